@@ -1,0 +1,284 @@
+#!/usr/bin/env python3
+"""Throughput of the NPCF hot path on one GB300 (or N, one process per GPU).
+
+Workload: 200,000 log-normal points in a periodic 1000 Mpc/h cube, 10 linear shells
+20-160 Mpc/h, lmax = 5, 4PCF + 3PCF (all parity-even multiplets). One step = one
+npcf_accumulate of the whole catalog: cell list, pair kernel (a_lm of every primary),
+3PCF and 4PCF contraction, FP64 reduction. Metric: primaries per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "primaries/sec for 4PCF (lmax=5, 10 shells); split-BF16 vs FP32 at stated error"
+WORKLOAD = "lognormal_200k_L1000_4pcf3pcf_lmax5_nr10_20-160"
+FOURPCF_ALG_FLOP_PER_PRIMARY = 405_360 + 126_240   # P-build + final contraction (lmax 5, N_r 10)
+PAIR_ALG_FLOP = 180                                  # per accepted pair at lmax 5
+N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+KERNELS_PER_STEP = 9   # k_sumw, 4 cell-list kernels, pair, contract3, contract4, reduce
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(wl, sample_n: int, seed: int = 77):
+    """The oracle as it stands (OpenMP over primaries), timed on a sample of primaries
+    against the full catalog. Returns (primaries/s, cores, sample description)."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(wl.n, sample_n, replace=False))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return sample_n / dt, cores, "%d seeded primaries of the 200k catalog against all 200k secondaries" % sample_n
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2105_08722_gb300 import catalogs
+    wl = catalogs.c2_lognormal_4pcf()
+    sample_n = args.ref_sample
+    times = []
+    for step in range(args.warmup + args.steps):
+        rate, cores, desc = cpu_oracle_rate(wl, sample_n, seed=1000 + step)
+        if step >= args.warmup:
+            times.append(sample_n / rate)
+    ms_per_primary = 1e3 * sum(times) / (sample_n * len(times))
+    value = 1e3 / ms_per_primary
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "primaries/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_points": wl.n, "lmax": wl.lmax, "nr": 10,
+                   "orders": [3, 4], "step": "%d primaries (bounded sample)" % sample_n},
+        "cpu_baseline": {"value": value, "unit": "primaries/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "primaries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32, SPLIT_BF16
+
+    wl = catalogs.c2_lognormal_4pcf()
+    prec = SPLIT_BF16 if args.precision == "bf16" else FP32
+    est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, prec)
+    pos = torch.from_numpy(wl.pos).to(dev)
+    w = torch.from_numpy(wl.w).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        est.accumulate(pos, w)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                      # evict the catalog and a_lm from L2 between steps
+        starts[k].record(stream)
+        est.accumulate(pos, w)
+        ends[k].record(stream)
+        stage_ms.append(est.timings())     # per-stage events of this step (same stream)
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    counts = est.pair_counts()
+
+    # end to end: host buffers through the C ABI, copies and result read-back inside
+    pos_h = np.ascontiguousarray(wl.pos)
+    w_h = np.ascontiguousarray(wl.w)
+    e2e_est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, prec)
+    e2e_est.accumulate_host(pos_h, w_h)
+    e2e_est.finalize()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_est.reset()
+        e2e_est.accumulate_host(pos_h, w_h)
+        e2e_est.finalize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    barrier()
+    clk = clocks.stop()
+
+    ms = float(np.mean(step_ms))
+    e2e_ms = e2e_s * 1e3
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    st = np.mean(np.array(stage_ms), axis=0)   # [cell list, pair, contraction, reduction]
+    npairs_per_step = float(counts.sum()) / (args.warmup + args.steps)
+    pair_tflops = npairs_per_step * PAIR_ALG_FLOP / (st[1] * 1e-3) / 1e12
+    con_tflops = wl.n * FOURPCF_ALG_FLOP_PER_PRIMARY / (st[2] * 1e-3) / 1e12
+    fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    dominant = "pair" if st[1] >= st[2] else "contraction"
+    achieved = pair_tflops if dominant == "pair" else con_tflops
+    line = {
+        "metric": METRIC,
+        "value": wl.n * world / (ms * 1e-3),
+        "unit": "primaries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == FP32 else "bf16x3",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_points": wl.n, "lmax": wl.lmax, "nr": 10, "orders": [3, 4],
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "e2e": {"value": wl.n * world / (e2e_ms * 1e-3), "unit": "primaries/s",
+                "h2d_bytes_per_step": int(wl.pos.nbytes + wl.w.nbytes),
+                "d2h_bytes_per_step": int(8 * e2e_est.size)},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
+                      "reduction": float(st[3])},
+        "pairs_per_step": npairs_per_step,
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        rate, cores, desc = cpu_oracle_rate(wl, args.cpu_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": "primaries/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line))
+    sys.stdout.flush()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--cpu-sample", type=int, default=1500)
+    ap.add_argument("--ref-sample", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

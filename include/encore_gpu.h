@@ -1,0 +1,151 @@
+/*
+ * encore_gpu.h -- C ABI of libencore_gpu, a single-GPU (sm_103a) implementation of
+ * the isotropic N-point correlation function estimator of Philcox, Slepian, Hou,
+ * Warner, Cahn & Eisenstein, "ENCORE: an O(N_g^2) estimator for galaxy N-point
+ * correlation functions" (arXiv:2105.08722).
+ *
+ * What one accumulate call computes (all of it on the GPU):
+ *   1. cell list: particles binned into a Cartesian grid for the neighbour search
+ *      (Sec. 5.1 / Fig. 5 "placing particles onto a Cartesian grid");
+ *   2. for every primary i, the binned harmonic coefficients
+ *         a^b_lm(s_i) = sum_j w_j Y_lm(unit(r_j - s_i)) Theta^b(|r_j - s_i|),
+ *      Eq. (binned-discrete-alm) without the 1/v_b factor, from Cartesian powers of
+ *      the unit separation (Algorithm 2);
+ *   3. the raw multiplets
+ *         zeta^B_L += sum_i u_i sum_M E(L) C^L_M prod_k a^{b_k}_{l_k m_k}(s_i),
+ *      Eq. (NPCF-mult-discrete-binned-estimator) without 1/V, summed with the
+ *      m_{N-1} >= 0 halving of App. B (Eq. simple-NPCF-summation), for N = 3, 4, 5.
+ *
+ * Conventions shared with the documentation:
+ *  - Y_lm orthonormal, Condon-Shortley phase (Sec. 2.1). Separation r_j - s_i.
+ *  - Neighbour/shell rule, evaluated in IEEE FP32 round-to-nearest without fused
+ *    multiply-add so that pair counts are exact and reproducible:
+ *      d = p_j - p_i per axis; periodic side L > 0: d > L/2 -> d - L,
+ *      d < -L/2 -> d + L; r2 = (dx*dx + dy*dy) + dz*dz; e2[k] = float(edge_k^2);
+ *      pair accepted iff r2 > 0 and e2[0] <= r2 < e2[nr]; shell b with
+ *      e2[b] <= r2 < e2[b+1]. Bins are distinct and ordered, b1 < b2 < ... (Sec. 3.2.1).
+ *  - Multiplets L: l1 outer, then l2, [l12], l3, [l4], last index fastest;
+ *    N=3: (l, l), l = 0..lmax; N=4: |l1-l2| <= l3 <= min(l1+l2, lmax);
+ *    N=5: |l1-l2| <= l12 <= l1+l2, |l12-l3| <= l4 <= min(l12+l3, lmax).
+ *    Parity-even only (sum of principal l even) unless allparity != 0 (Table 1).
+ *  - Output of npcf_finalize: orders ascending; for each order an array
+ *    [n_multiplets][n_bin_tuples], bin tuples lexicographic with the last index
+ *    fastest. Parity-even multiplets are real; parity-odd ones are purely imaginary
+ *    (Sec. 3.1) and their imaginary part is stored.
+ *
+ * Threading: a context is not thread-safe; use one context per host thread.
+ * Errors: every call returns an npcf_status and never aborts; npcf_last_error gives
+ * a message. Device-side waits are bounded and report NPCF_ETIMEOUT.
+ */
+#ifndef ENCORE_GPU_H
+#define ENCORE_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct npcf_ctx npcf_ctx;
+
+typedef enum {
+    NPCF_OK = 0,
+    NPCF_EINVAL = 1,        /* bad argument (null pointer, bad size, bad edges ...) */
+    NPCF_ENOMEM = 2,        /* device or host allocation failed */
+    NPCF_ECUDA = 3,         /* a CUDA runtime call failed */
+    NPCF_EUNSUPPORTED = 4,  /* valid request this build does not implement */
+    NPCF_ETIMEOUT = 5       /* a bounded device-side wait gave up */
+} npcf_status;
+
+/* Arithmetic of the contraction over primaries (step 3). FP32: CUDA-core FP32
+ * products and sums. SPLIT_BF16: tensor-core (tcgen05) products of bf16 hi/lo
+ * splits (hi*hi + hi*lo + lo*hi), FP32 accumulation. Cross-block sums are FP64. */
+typedef enum {
+    NPCF_FP32 = 0,
+    NPCF_SPLIT_BF16 = 1
+} npcf_precision;
+
+/* Create a context.
+ *   lmax        maximum l of every principal angular momentum, 0 <= lmax <= 10
+ *               (Sec. 3.1: the l_i <= lmax truncation).
+ *   order_mask  bit N set to compute the N-point function; N in {3, 4, 5}.
+ *   nr, edges   nr radial shells (1 <= nr <= 16) with host edges[nr+1] strictly
+ *               increasing, edges[0] >= 0 (the binning functions Theta^b, Sec. 3.2).
+ *   box         > 0: periodic cube of that side (Table 1 "periodic"); positions must
+ *               lie in [0, box) and edges[nr] < box / 3. 0: no periodicity.
+ *   prec        contraction arithmetic (npcf_precision).
+ *   allparity   non-zero: parity-odd multiplets too (Table 1 "allparity").
+ * The context owns every device buffer it needs; npcf_destroy frees them. On failure
+ * *out is NULL and npcf_last_error(NULL) describes the problem. */
+npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr,
+                        const double* edges, double box, int prec, int allparity);
+
+/* Accumulate the multiplets of one catalog into the context (adds to previous calls,
+ * so random-catalog splits co-add, Sec. 4.2).
+ *   d_pos   device float32 [n][3] positions (x, y, z), caller-owned
+ *   d_w     device float32 [n] weights w_j (secondaries, and primaries unless d_wprim)
+ *   d_wprim nullable device float32 [n] primary weights u_i; primaries with u_i == 0
+ *           are skipped (used to evaluate a sample of primaries)
+ *   n       number of particles, 0 <= n < 2^31
+ *   stream  cudaStream_t to enqueue on (0 = legacy default stream)
+ * Work is enqueued asynchronously; caller buffers must stay valid until the stream
+ * reaches it. For box == 0 the call reads the bounding box back to the host (one
+ * stream synchronisation). */
+npcf_status npcf_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n,
+                            void* stream);
+npcf_status npcf_accumulate_ex(npcf_ctx* ctx, const float* d_pos, const float* d_w,
+                               const float* d_wprim, int64_t n, void* stream);
+
+/* Same as npcf_accumulate, from HOST buffers: copies them to the device inside the
+ * call (stream-ordered) and synchronises the stream before returning. */
+npcf_status npcf_accumulate_host(npcf_ctx* ctx, const float* h_pos, const float* h_w,
+                                 int64_t n, void* stream);
+
+/* Number of doubles npcf_finalize writes. */
+npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len);
+
+/* Multiplet and bin-tuple tables of one order (N in the context's mask). lambdas
+ * (nullable) receives n_lambda x {2,3,5} ints, bins (nullable) n_bins x (N-1). */
+npcf_status npcf_layout(const npcf_ctx* ctx, int order, int* n_lambda, int* n_bins,
+                        int* lambdas, int* bins);
+
+/* Copy the FP64 multiplets accumulated so far to host out[out_len] (synchronises).
+ * normalize = 0: raw sums as defined above. normalize = 1 (periodic only): divide by
+ * V prod_k v_{b_k} (Eq. NPCF-mult-discrete-binned-estimator, Eq. alm-binned-def with
+ * v_b = 4 pi (r_{b+1}^3 - r_b^3) / 3, V = box^3) and by R_0 = (4pi)^{-(N-1)/2} nbar^N
+ * with nbar = sum w / V (Eq. R-periodic-form). */
+npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normalize);
+
+/* Per-shell pair counts accumulated so far (uint64 [nr], exact; synchronises). */
+npcf_status npcf_pair_counts(npcf_ctx* ctx, uint64_t* out);
+
+/* Zero every accumulator of the context. */
+npcf_status npcf_reset(npcf_ctx* ctx);
+
+/* Diagnostics: a^b_lm and per-shell neighbour counts of selected primaries from the
+ * LAST accumulate call (synchronises). idx: host int64 [k] input indices.
+ * alm: host float [k][nr][(lmax+1)(lmax+2)] as (re, im) pairs for l = 0..lmax,
+ * m = 0..l (index l(l+1)/2 + m); counts: host uint32 [k][nr] (nullable). */
+npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* alm,
+                           uint32_t* counts);
+
+/* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8),
+ * key 1 = pair-kernel warps per block (1..16), key 2 = contraction primaries per
+ * chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per warp
+ * (64..16384 entries; larger lists mean fewer passes for dense primaries). */
+npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);
+
+/* Device time in ms of the stages of the last accumulate call:
+ * [0] cell list, [1] pair kernel, [2] contraction, [3] FP64 reduction. */
+npcf_status npcf_get_timings(npcf_ctx* ctx, float* ms4);
+
+/* Message of the last failed call on ctx; with ctx == NULL, of the last failed
+ * npcf_create on this thread. */
+const char* npcf_last_error(const npcf_ctx* ctx);
+void npcf_destroy(npcf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

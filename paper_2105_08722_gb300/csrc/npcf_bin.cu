@@ -1,0 +1,152 @@
+// Cell-list construction (counting sort of particles into a Cartesian grid), the
+// neighbour-search structure of the pair kernel (Sec. 5.1 / Fig. 5: particles are
+// placed on a Cartesian grid before the pair search).
+//
+// Stages: per-point cell id + histogram -> exclusive scan -> scatter into cell order
+// as float4 (x, y, z, w) -> per-cell reorder by input index so the sorted order, and
+// every sum that follows it, is deterministic.
+#include "npcf_device.h"
+
+#include <cfloat>
+
+namespace npcf {
+
+namespace {
+
+__device__ __forceinline__ int cell_coord(float x, float o, float inv, int g) {
+    int c = (int)floorf((x - o) * inv);
+    return c < 0 ? 0 : (c >= g ? g - 1 : c);
+}
+
+__global__ void k_bbox(const float* __restrict__ pos, int n, float* __restrict__ part) {
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float v = pos[3 * i + a];
+            mn[a] = fminf(mn[a], v);
+            mx[a] = fmaxf(mx[a], v);
+        }
+    }
+    __shared__ float sh[6][32];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) { sh[a][warp] = mn[a]; sh[3 + a][warp] = mx[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int a = threadIdx.x;
+        float v = sh[a][0];
+        for (int k = 1; k < nw; ++k) v = (a < 3) ? fminf(v, sh[a][k]) : fmaxf(v, sh[a][k]);
+        part[blockIdx.x * 6 + a] = v;
+    }
+}
+
+__global__ void k_assign(BinArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float x = a.pos[3 * i], y = a.pos[3 * i + 1], z = a.pos[3 * i + 2];
+    bool bad = !(x == x && y == y && z == z);
+    if (a.g.periodic)
+        bad |= !(x >= 0.f && x < a.g.L && y >= 0.f && y < a.g.L && z >= 0.f && z < a.g.L);
+    if (bad) atomicOr(a.err, 1);
+    int cx = cell_coord(x, a.g.ox, a.g.inv_cell, a.g.gx);
+    int cy = cell_coord(y, a.g.oy, a.g.inv_cell, a.g.gy);
+    int cz = cell_coord(z, a.g.oz, a.g.inv_cell, a.g.gz);
+    uint32_t c = (uint32_t)((cz * a.g.gy + cy) * a.g.gx + cx);
+    a.cid[i] = c;
+    atomicAdd(&a.count[c], 1u);
+}
+
+// Single-block exclusive scan of the cell histogram (ncell is at most a few million).
+__global__ void k_scan(const uint32_t* __restrict__ count, uint32_t* __restrict__ start,
+                       uint32_t* __restrict__ cursor, int ncell) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < ncell; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < ncell ? count[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        uint32_t excl = carry + (warp > 0 ? warp_tot[warp - 1] : 0u) + x - v;
+        if (i < ncell) { start[i] = excl; cursor[i] = excl; }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[ncell] = carry;
+}
+
+__global__ void k_scatter(BinArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    uint32_t c = a.cid[i];
+    uint32_t k = atomicAdd(&a.cursor[c], 1u);
+    a.pts[k] = make_float4(a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2], a.w[i]);
+    a.wp[k] = a.wprim ? a.wprim[i] : a.w[i];
+    a.idx[k] = (uint32_t)i;
+    a.cell_of[k] = c;
+}
+
+// Order each cell's members by input index (insertion sort; cells hold tens of points).
+__global__ void k_cell_order(BinArgs a) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.g.ncell) return;
+    uint32_t s0 = a.start[c], s1 = a.start[c + 1];
+    if (s1 - s0 > 4096u) return;  // keep the quadratic sort bounded; order then follows the scatter
+    for (uint32_t k = s0 + 1; k < s1; ++k) {
+        uint32_t key = a.idx[k];
+        float4 p = a.pts[k];
+        float u = a.wp[k];
+        uint32_t j = k;
+        while (j > s0 && a.idx[j - 1] > key) {
+            a.idx[j] = a.idx[j - 1];
+            a.pts[j] = a.pts[j - 1];
+            a.wp[j] = a.wp[j - 1];
+            --j;
+        }
+        a.idx[j] = key;
+        a.pts[j] = p;
+        a.wp[j] = u;
+    }
+}
+
+}  // namespace
+
+void launch_bbox(const float* pos, int n, float* part, int nblocks, cudaStream_t s) {
+    k_bbox<<<nblocks, 256, 0, s>>>(pos, n, part);
+}
+
+void launch_bin(const BinArgs& a, cudaStream_t s) {
+    int nb = (a.n + 255) / 256;
+    if (a.n > 0) k_assign<<<nb, 256, 0, s>>>(a);
+    k_scan<<<1, 1024, 0, s>>>(a.count, a.start, a.cursor, a.g.ncell);
+    if (a.n > 0) k_scatter<<<nb, 256, 0, s>>>(a);
+    k_cell_order<<<(a.g.ncell + 127) / 128, 128, 0, s>>>(a);
+}
+
+}  // namespace npcf

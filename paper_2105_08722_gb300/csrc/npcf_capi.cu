@@ -1,0 +1,712 @@
+// C ABI of libencore_gpu (include/encore_gpu.h): context management and the
+// accumulate / finalize pipeline. Host code only enqueues work; every step of the
+// estimator runs in the kernels of npcf_bin.cu, npcf_pair.cu and npcf_contract.cu.
+#include "encore_gpu.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "npcf_device.h"
+#include "npcf_tables.h"
+
+using namespace npcf;
+
+namespace {
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t count) {
+        if (count <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) n = count;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct npcf_ctx {
+    int lmax = 0, nr = 0, prec = 0, allparity = 0;
+    unsigned mask = 0;
+    double box = 0.0;
+    std::vector<double> edges;
+    float e2[kMaxNr + 1] = {};
+    std::string err;
+
+    std::vector<OrderTable> orders;
+    std::vector<int> order_off;
+    int total = 0;
+    int nlm = 0;
+
+    // cell-list tuning and geometry
+    int cells_per_rmax = 4;
+    int pair_warps = 8;
+    int pair_cap = 4096;
+    int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
+    GridInfo grid{};
+    std::vector<int> rows_host;
+    float rows_cell = -1.f;
+
+    // device tables
+    DevBuf<float> kmat;
+    DevBuf<int4> rows;
+    DevBuf<int2> c3rows, c3pairs;
+    DevBuf<float> c3coef;
+    int c3nrows = 0;
+    DevBuf<int4> c4rows;
+    DevBuf<PairTerm> c4terms;
+    DevBuf<int> c4sb, c4se, c4lm3, c4lamseg0, c4odd;
+    DevBuf<float> c4fac;
+    int c4nrows = 0, c4nterms = 0, c4nseg = 0, c4nlam = 0;
+
+    // working buffers
+    DevBuf<float4> pts;
+    DevBuf<float> wp;
+    DevBuf<uint32_t> idx, cell_of, cid;
+    DevBuf<float2> alm;
+    DevBuf<uint32_t> cnt;
+    DevBuf<uint32_t> count, start, cursor;
+    DevBuf<double> partial, zeta, sumw;
+    DevBuf<unsigned long long> counts;
+    DevBuf<int> errflag, work;
+    DevBuf<float> bbox;
+    DevBuf<float> hpos_stage, hw_stage;
+    int nchunk = 0;
+    int64_t last_n = 0;
+    int nsm = 0;
+
+    cudaEvent_t ev[5] = {};
+    bool timed = false;
+};
+
+namespace {
+
+npcf_status fail(npcf_ctx* c, npcf_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? NPCF_ENOMEM : NPCF_ECUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                     \
+    } while (0)
+
+template <class T>
+cudaError_t upload(DevBuf<T>& b, const std::vector<T>& v) {
+    cudaError_t e = b.ensure(v.size());
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Neighbour rows (dy, dz, dx_lo, dx_hi) of cells that may hold a point within rmax of
+// some point of the centre cell. Cell-box gaps get a small slack so that points put in
+// a neighbouring cell by rounding are never missed.
+std::vector<int> make_rows(float cell, double rmax, int* reach) {
+    const double slack = 1e-3 * cell;
+    const double r2 = rmax * (1.0 + 1e-6) * rmax * (1.0 + 1e-6);
+    const int R = (int)std::ceil(rmax / cell) + 1;
+    auto gap = [&](int d) {
+        double gg = (std::abs(d) - 1) * (double)cell - slack;
+        return gg > 0 ? gg : 0.0;
+    };
+    std::vector<int> out;
+    int rmaxd = 0;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy) {
+            double gyz = gap(dy) * gap(dy) + gap(dz) * gap(dz);
+            if (gyz > r2) continue;
+            int X = 0;
+            while (X + 1 <= R && gyz + gap(X + 1) * gap(X + 1) <= r2) ++X;
+            out.insert(out.end(), {dy, dz, -X, X});
+            rmaxd = std::max(rmaxd, std::max(X, std::max(std::abs(dy), std::abs(dz))));
+        }
+    *reach = rmaxd;
+    return out;
+}
+
+npcf_status setup_tables(npcf_ctx* ctx) {
+    ctx->nlm = nlm(ctx->lmax);
+    // Y_lm conversion matrix
+    std::vector<double> K = ylm_power_matrix(ctx->lmax);
+    std::vector<float> Kf(K.begin(), K.end());
+    CU(upload(ctx->kmat, Kf));
+    ctx->total = 0;
+    for (int N = 3; N <= 5; ++N) {
+        if (!(ctx->mask & (1u << N))) continue;
+        ctx->orders.push_back(make_order(N, ctx->lmax, ctx->nr, ctx->allparity != 0));
+        ctx->order_off.push_back(ctx->total);
+        const OrderTable& o = ctx->orders.back();
+        ctx->total += o.n_lambda() * o.n_bins();
+    }
+    for (size_t k = 0; k < ctx->orders.size(); ++k) {
+        const OrderTable& o = ctx->orders[k];
+        const int off = ctx->order_off[k];
+        if (o.N == 3) {
+            std::vector<int2> rows, pairs;
+            std::vector<float> coef;
+            for (int b = 0; b < o.n_bins(); ++b) pairs.push_back(make_int2(o.bins[2 * b], o.bins[2 * b + 1]));
+            for (int l = 0; l <= ctx->lmax; ++l) {
+                // E(L) C^{ll}_{m,-m} (-1)^m = (l l 0; 0 0 0) for every m (Eq. N=3-coeff)
+                coef.push_back((float)wigner3j(l, l, 0, 0, 0, 0));
+                for (int b = 0; b < o.n_bins(); ++b) rows.push_back(make_int2(l, b));
+            }
+            ctx->c3nrows = (int)rows.size();
+            if (ctx->c3nrows > 1024)
+                return fail(ctx, NPCF_EUNSUPPORTED, "3PCF with %d outputs exceeds one block", ctx->c3nrows);
+            CU(upload(ctx->c3rows, rows));
+            CU(upload(ctx->c3pairs, pairs));
+            CU(upload(ctx->c3coef, coef));
+            (void)off;
+        } else if (o.N == 4) {
+            ContractTable4 t = make_contract4(o);
+            // rows (multiplet, b1, b2) with at least one b3 > b2, and their first output
+            std::vector<int4> rows;
+            const int nb = o.n_bins();
+            for (int a = 0; a < o.n_lambda(); ++a)
+                for (int b = 0; b < nb; ++b) {
+                    const int* B = &o.bins[3 * b];
+                    if (B[2] != B[1] + 1) continue;  // first b3 of this (b1, b2)
+                    rows.push_back(make_int4(a, B[0], B[1], off + a * nb + b));
+                }
+            std::vector<int> odd;
+            for (int a = 0; a < o.n_lambda(); ++a) odd.push_back(o.odd(a) ? 1 : 0);
+            ctx->c4nrows = (int)rows.size();
+            ctx->c4nterms = (int)t.terms.size();
+            {
+                const size_t need = (size_t)t.terms.size() * 20 + t.seg_begin.size() * 16 +
+                                    (size_t)8 * ctx->nr * ctx->nlm * 8 + 4096;
+                if (need > 200 * 1024)
+                    return fail(ctx, NPCF_EUNSUPPORTED, "4PCF coupling table (%zu terms) exceeds shared "
+                                "memory; use lmax <= 7", t.terms.size());
+            }
+            ctx->c4nseg = (int)t.seg_begin.size();
+            ctx->c4nlam = o.n_lambda();
+            CU(upload(ctx->c4rows, rows));
+            CU(upload(ctx->c4terms, t.terms));
+            CU(upload(ctx->c4sb, t.seg_begin));
+            CU(upload(ctx->c4se, t.seg_end));
+            CU(upload(ctx->c4lm3, t.seg_lm3));
+            CU(upload(ctx->c4fac, t.seg_factor));
+            CU(upload(ctx->c4lamseg0, t.lam_seg0));
+            CU(upload(ctx->c4odd, odd));
+        }
+    }
+    return NPCF_OK;
+}
+
+npcf_status check_ctx(npcf_ctx* ctx) {
+    if (!ctx) return NPCF_EINVAL;
+    return NPCF_OK;
+}
+
+// Grid and neighbour rows for the current geometry.
+npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s) {
+    const double rmax = ctx->edges[ctx->nr];
+    GridInfo g{};
+    int k = ctx->cells_per_rmax;
+    if (ctx->box > 0) {
+        const double L = ctx->box;
+        // the preferred cells per r_max first, then finer, then coarser grids: a grid is
+        // valid when no neighbour offset reaches the same cell twice (2 reach + 1 <= g)
+        std::vector<int> order;
+        for (int q = k; q <= 16; ++q) order.push_back(q);
+        for (int q = k - 1; q >= 1; --q) order.push_back(q);
+        bool found = false;
+        for (int q : order) {
+            int gg = (int)std::floor(L * q / rmax);
+            if (gg < 1) gg = 1;
+            gg = std::min(gg, 1024);
+            float cell = (float)(L / gg);
+            int reach = 0;
+            std::vector<int> rows = make_rows(cell, rmax, &reach);
+            if (2 * reach + 1 > gg) continue;
+            g.gx = g.gy = g.gz = gg;
+            g.ox = g.oy = g.oz = 0.f;
+            g.inv_cell = (float)(gg / L);
+            g.periodic = 1;
+            g.L = (float)L;
+            g.hL = (float)(0.5 * L);
+            if (rows != ctx->rows_host) {
+                ctx->rows_host = rows;
+                std::vector<int4> r4;
+                for (size_t i = 0; i < rows.size(); i += 4)
+                    r4.push_back(make_int4(rows[i], rows[i + 1], rows[i + 2], rows[i + 3]));
+                CU(upload(ctx->rows, r4));
+            }
+            found = true;
+            break;
+        }
+        if (!found) return fail(ctx, NPCF_EINVAL, "box %.6g too small for r_max %.6g", L, rmax);
+    } else {
+        // bounding box of the catalog (one stream synchronisation)
+        const int nb = 256;
+        CU(ctx->bbox.ensure(nb * 6));
+        launch_bbox(d_pos, n, ctx->bbox.p, nb, s);
+        CU(cudaGetLastError());
+        std::vector<float> part(nb * 6);
+        CU(cudaMemcpyAsync(part.data(), ctx->bbox.p, nb * 6 * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        float mn[3], mx[3];
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = part[a];
+            mx[a] = part[3 + a];
+            for (int b = 1; b < nb; ++b) {
+                mn[a] = std::min(mn[a], part[b * 6 + a]);
+                mx[a] = std::max(mx[a], part[b * 6 + 3 + a]);
+            }
+            if (!std::isfinite(mn[a]) || !std::isfinite(mx[a]))
+                return fail(ctx, NPCF_EINVAL, "non-finite positions");
+        }
+        float cell = (float)(rmax / k);
+        int dims[3];
+        double ncell = 1;
+        for (int a = 0; a < 3; ++a) {
+            dims[a] = std::max(1, (int)std::floor((mx[a] - mn[a]) / cell) + 1);
+            ncell *= dims[a];
+        }
+        while (ncell > (1 << 24)) {  // keep the grid bounded for sparse, extended catalogs
+            cell *= 1.25f;
+            ncell = 1;
+            for (int a = 0; a < 3; ++a) {
+                dims[a] = std::max(1, (int)std::floor((mx[a] - mn[a]) / cell) + 1);
+                ncell *= dims[a];
+            }
+        }
+        g.gx = dims[0];
+        g.gy = dims[1];
+        g.gz = dims[2];
+        g.ox = mn[0];
+        g.oy = mn[1];
+        g.oz = mn[2];
+        g.inv_cell = 1.0f / cell;
+        g.periodic = 0;
+        g.L = 0.f;
+        g.hL = 0.f;
+        int reach = 0;
+        std::vector<int> rows = make_rows(cell, rmax, &reach);
+        if (rows != ctx->rows_host) {
+            ctx->rows_host = rows;
+            std::vector<int4> r4;
+            for (size_t i = 0; i < rows.size(); i += 4)
+                r4.push_back(make_int4(rows[i], rows[i + 1], rows[i + 2], rows[i + 3]));
+            CU(upload(ctx->rows, r4));
+        }
+    }
+    g.ncell = g.gx * g.gy * g.gz;
+    ctx->grid = g;
+    return NPCF_OK;
+}
+
+__global__ void k_sumw(const float* __restrict__ w, int n, double* out) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim,
+                           int64_t n64, cudaStream_t s) {
+    if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", (long long)n64);
+    if (n64 == 0) return NPCF_OK;
+    if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+    const int n = (int)n64;
+    npcf_status st = setup_grid(ctx, d_pos, n, s);
+    if (st != NPCF_OK) return st;
+    const GridInfo& g = ctx->grid;
+
+    CU(ctx->pts.ensure(n));
+    CU(ctx->wp.ensure(n));
+    CU(ctx->idx.ensure(n));
+    CU(ctx->cell_of.ensure(n));
+    CU(ctx->cid.ensure(n));
+    CU(ctx->alm.ensure((size_t)n * ctx->nr * ctx->nlm));
+    CU(ctx->cnt.ensure((size_t)n * ctx->nr));
+    CU(ctx->count.ensure(g.ncell));
+    CU(ctx->start.ensure(g.ncell + 1));
+    CU(ctx->cursor.ensure(g.ncell));
+    CU(ctx->work.ensure(1));
+
+    if (ctx->timed) CU(cudaEventRecord(ctx->ev[0], s));
+    CU(cudaMemsetAsync(ctx->count.p, 0, g.ncell * sizeof(uint32_t), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, sizeof(int), s));
+    k_sumw<<<64, 256, 0, s>>>(d_w, n, ctx->sumw.p);
+
+    BinArgs b{};
+    b.pos = d_pos;
+    b.w = d_w;
+    b.wprim = d_wprim;
+    b.n = n;
+    b.g = g;
+    b.cid = ctx->cid.p;
+    b.count = ctx->count.p;
+    b.start = ctx->start.p;
+    b.cursor = ctx->cursor.p;
+    b.pts = ctx->pts.p;
+    b.wp = ctx->wp.p;
+    b.idx = ctx->idx.p;
+    b.cell_of = ctx->cell_of.p;
+    b.err = ctx->errflag.p;
+    launch_bin(b, s);
+    CU(cudaGetLastError());
+    if (ctx->timed) CU(cudaEventRecord(ctx->ev[1], s));
+
+    PairArgs pa{};
+    pa.pts = ctx->pts.p;
+    pa.wp = ctx->wp.p;
+    pa.cell_of = ctx->cell_of.p;
+    pa.cell_start = ctx->start.p;
+    pa.rows = ctx->rows.p;
+    pa.nrows = (int)(ctx->rows_host.size() / 4);
+    pa.g = g;
+    for (int i = 0; i <= ctx->nr; ++i) pa.e2[i] = ctx->e2[i];
+    pa.nr = ctx->nr;
+    pa.lmax = ctx->lmax;
+    pa.kmat = ctx->kmat.p;
+    pa.alm = ctx->alm.p;
+    pa.cnt = ctx->cnt.p;
+    pa.counts = ctx->counts.p;
+    pa.n = n;
+    pa.work = ctx->work.p;
+    pa.cap = ctx->pair_cap;
+    pa.warps = ctx->pair_warps;
+    {
+        int dev = 0, optin = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const size_t need = (size_t)pa.nrows * sizeof(int4) + pair_smem_bytes(pa.warps, pa.cap) + 16384;
+        if (need > (size_t)optin)
+            return fail(ctx, NPCF_EINVAL, "pair kernel needs %zu B of shared memory (limit %d): lower "
+                        "the warps or the list capacity", need, optin);
+    }
+    const int pair_blocks_per_sm = 1;
+    launch_pair(pa, ctx->nsm * pair_blocks_per_sm, s);
+    CU(cudaGetLastError());
+    if (ctx->timed) CU(cudaEventRecord(ctx->ev[2], s));
+
+    // contraction over primaries: chunks of cell-sorted primaries
+    int nchunk = ctx->chunk_target > 0 ? (n + ctx->chunk_target - 1) / ctx->chunk_target
+                                       : std::min(std::max(1, n / 64), 4 * ctx->nsm);
+    nchunk = std::max(1, nchunk);
+    const int chunk = (n + nchunk - 1) / nchunk;
+    nchunk = (n + chunk - 1) / chunk;
+    CU(ctx->partial.ensure((size_t)nchunk * ctx->total));
+    for (size_t k = 0; k < ctx->orders.size(); ++k) {
+        const OrderTable& o = ctx->orders[k];
+        if (o.N == 3) {
+            if (ctx->c3nrows == 0) continue;
+            Contract3Args c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.lmax = ctx->lmax;
+            c.nchunk = nchunk;
+            c.chunk = chunk;
+            c.rows = ctx->c3rows.p;
+            c.pairs = ctx->c3pairs.p;
+            c.coef = ctx->c3coef.p;
+            c.nrows = ctx->c3nrows;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            c.out_off = ctx->order_off[k];
+            c.nbins = o.n_bins();
+            launch_contract3(c, s);
+        } else if (o.N == 4) {
+            if (ctx->c4nrows == 0) continue;
+            Contract4Args c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.nchunk = nchunk;
+            c.chunk = chunk;
+            c.rows = ctx->c4rows.p;
+            c.nrows = ctx->c4nrows;
+            c.terms = ctx->c4terms.p;
+            c.nterms = ctx->c4nterms;
+            c.seg_begin = ctx->c4sb.p;
+            c.seg_end = ctx->c4se.p;
+            c.seg_lm3 = ctx->c4lm3.p;
+            c.seg_factor = ctx->c4fac.p;
+            c.lam_seg0 = ctx->c4lamseg0.p;
+            c.lam_odd = ctx->c4odd.p;
+            c.nseg = ctx->c4nseg;
+            c.nlam = ctx->c4nlam;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            launch_contract4(c, s);
+        }
+        CU(cudaGetLastError());
+    }
+    if (ctx->timed) CU(cudaEventRecord(ctx->ev[3], s));
+    if (ctx->total > 0) launch_reduce(ctx->partial.p, nchunk, ctx->total, ctx->zeta.p, s);
+    CU(cudaGetLastError());
+    if (ctx->timed) CU(cudaEventRecord(ctx->ev[4], s));
+    ctx->nchunk = nchunk;
+    ctx->last_n = n;
+    return NPCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr, const double* edges,
+                        double box, int prec, int allparity) {
+    if (!out) return NPCF_EINVAL;
+    *out = nullptr;
+    npcf_ctx* ctx = new (std::nothrow) npcf_ctx();
+    if (!ctx) return NPCF_ENOMEM;
+    auto bad = [&](npcf_status s) {
+        // the message stays readable through npcf_last_error(NULL)
+        g_create_error = ctx->err;
+        delete ctx;
+        return s;
+    };
+    if (lmax < 0 || lmax > kMaxL) return bad(fail(ctx, NPCF_EINVAL, "lmax %d outside [0, %d]", lmax, kMaxL));
+    if (nr < 1 || nr > kMaxNr) return bad(fail(ctx, NPCF_EINVAL, "nr %d outside [1, %d]", nr, kMaxNr));
+    if (!edges) return bad(fail(ctx, NPCF_EINVAL, "edges is null"));
+    if ((order_mask & ~((1u << 3) | (1u << 4) | (1u << 5))) || order_mask == 0)
+        return bad(fail(ctx, NPCF_EINVAL, "order_mask 0x%x must select orders among 3, 4, 5", order_mask));
+    if (order_mask & (1u << 5))
+        return bad(fail(ctx, NPCF_EUNSUPPORTED, "the 5PCF contraction is not built yet"));
+    if (prec != NPCF_FP32 && prec != NPCF_SPLIT_BF16)
+        return bad(fail(ctx, NPCF_EINVAL, "unknown precision %d", prec));
+    if (prec == NPCF_SPLIT_BF16)
+        return bad(fail(ctx, NPCF_EUNSUPPORTED, "split-BF16 contraction is not built yet"));
+    for (int i = 0; i <= nr; ++i)
+        if (!std::isfinite(edges[i]) || edges[i] < 0 || (i > 0 && !(edges[i] > edges[i - 1])))
+            return bad(fail(ctx, NPCF_EINVAL, "edges must be finite, >= 0 and strictly increasing"));
+    if (!(box >= 0) || !std::isfinite(box)) return bad(fail(ctx, NPCF_EINVAL, "box must be >= 0"));
+    if (box > 0 && !(edges[nr] * 3.0 < box))
+        return bad(fail(ctx, NPCF_EINVAL, "periodic box %.6g must exceed 3 r_max (%.6g)", box, edges[nr]));
+    ctx->lmax = lmax;
+    ctx->nr = nr;
+    ctx->mask = order_mask;
+    ctx->box = box;
+    ctx->prec = prec;
+    ctx->allparity = allparity ? 1 : 0;
+    ctx->edges.assign(edges, edges + nr + 1);
+    for (int i = 0; i <= nr; ++i) ctx->e2[i] = (float)(edges[i] * edges[i]);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bad(fail(ctx, NPCF_ECUDA, "no CUDA device"));
+    npcf_status st = setup_tables(ctx);
+    if (st != NPCF_OK) return bad(st);
+    if (ctx->zeta.ensure(ctx->total) != cudaSuccess || ctx->counts.ensure(nr) != cudaSuccess ||
+        ctx->errflag.ensure(1) != cudaSuccess || ctx->sumw.ensure(1) != cudaSuccess)
+        return bad(fail(ctx, NPCF_ENOMEM, "device allocation failed"));
+    for (auto& e : ctx->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bad(fail(ctx, NPCF_ECUDA, "event creation failed"));
+    ctx->timed = true;
+    st = npcf_reset(ctx);
+    if (st != NPCF_OK) return bad(st);
+    *out = ctx;
+    return NPCF_OK;
+}
+
+npcf_status npcf_reset(npcf_ctx* ctx) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, ctx->total * sizeof(double)));
+    CU(cudaMemset(ctx->counts.p, 0, ctx->nr * sizeof(unsigned long long)));
+    CU(cudaMemset(ctx->errflag.p, 0, sizeof(int)));
+    CU(cudaMemset(ctx->sumw.p, 0, sizeof(double)));
+    return NPCF_OK;
+}
+
+npcf_status npcf_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    return run_accumulate(ctx, d_pos, d_w, nullptr, n, (cudaStream_t)stream);
+}
+
+npcf_status npcf_accumulate_ex(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim,
+                               int64_t n, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    return run_accumulate(ctx, d_pos, d_w, d_wprim, n, (cudaStream_t)stream);
+}
+
+npcf_status npcf_accumulate_host(npcf_ctx* ctx, const float* h_pos, const float* h_w, int64_t n,
+                                 void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n out of range");
+    if (n == 0) return NPCF_OK;
+    if (!h_pos || !h_w) return fail(ctx, NPCF_EINVAL, "null host pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(ctx->hpos_stage.ensure((size_t)n * 3));
+    CU(ctx->hw_stage.ensure((size_t)n));
+    CU(cudaMemcpyAsync(ctx->hpos_stage.p, h_pos, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ctx->hw_stage.p, h_w, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s));
+    npcf_status st = run_accumulate(ctx, ctx->hpos_stage.p, ctx->hw_stage.p, nullptr, n, s);
+    if (st != NPCF_OK) return st;
+    CU(cudaStreamSynchronize(s));
+    return NPCF_OK;
+}
+
+npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len) {
+    if (!ctx || !len) return NPCF_EINVAL;
+    *len = (size_t)ctx->total;
+    return NPCF_OK;
+}
+
+npcf_status npcf_layout(const npcf_ctx* ctx, int order, int* n_lambda, int* n_bins, int* lambdas, int* bins) {
+    if (!ctx) return NPCF_EINVAL;
+    for (const OrderTable& o : ctx->orders) {
+        if (o.N != order) continue;
+        if (n_lambda) *n_lambda = o.n_lambda();
+        if (n_bins) *n_bins = o.n_bins();
+        if (lambdas) std::memcpy(lambdas, o.lam.data(), o.lam.size() * sizeof(int));
+        if (bins) std::memcpy(bins, o.bins.data(), o.bins.size() * sizeof(int));
+        return NPCF_OK;
+    }
+    return NPCF_EINVAL;
+}
+
+npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normalize) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if ((!out && ctx->total > 0) || out_len < (size_t)ctx->total)
+        return fail(ctx, NPCF_EINVAL, "output buffer too small");
+    CU(cudaDeviceSynchronize());
+    int errbits = 0;
+    CU(cudaMemcpy(&errbits, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errbits & 1) return fail(ctx, NPCF_EINVAL, "positions outside [0, box) or not finite");
+    if (ctx->total > 0)
+        CU(cudaMemcpy(out, ctx->zeta.p, ctx->total * sizeof(double), cudaMemcpyDeviceToHost));
+    if (normalize) {
+        if (!(ctx->box > 0)) return fail(ctx, NPCF_EUNSUPPORTED, "normalisation needs a periodic box");
+        double sumw = 0;
+        CU(cudaMemcpy(&sumw, ctx->sumw.p, sizeof(double), cudaMemcpyDeviceToHost));
+        const double V = ctx->box * ctx->box * ctx->box;
+        const double nbar = sumw / V;
+        const double fourpi = 4.0 * M_PI;
+        std::vector<double> vb(ctx->nr);
+        for (int b = 0; b < ctx->nr; ++b)
+            vb[b] = fourpi / 3.0 * (std::pow(ctx->edges[b + 1], 3) - std::pow(ctx->edges[b], 3));
+        for (size_t k = 0; k < ctx->orders.size(); ++k) {
+            const OrderTable& o = ctx->orders[k];
+            const int N = o.N, nb = o.n_bins();
+            const double R0 = std::pow(fourpi, -(N - 1) / 2.0) * std::pow(nbar, N);
+            for (int a = 0; a < o.n_lambda(); ++a)
+                for (int b = 0; b < nb; ++b) {
+                    double vB = V;
+                    for (int q = 0; q < N - 1; ++q) vB *= vb[o.bins[(size_t)b * (N - 1) + q]];
+                    out[ctx->order_off[k] + a * nb + b] /= vB * R0;
+                }
+        }
+    }
+    return NPCF_OK;
+}
+
+npcf_status npcf_pair_counts(npcf_ctx* ctx, uint64_t* out) {
+    if (check_ctx(ctx) != NPCF_OK || !out) return NPCF_EINVAL;
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(out, ctx->counts.p, ctx->nr * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return NPCF_OK;
+}
+
+npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* alm, uint32_t* counts) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (k < 0 || (k > 0 && (!idx || !alm))) return fail(ctx, NPCF_EINVAL, "bad arguments");
+    if (k == 0) return NPCF_OK;
+    const int n = (int)ctx->last_n;
+    if (n == 0) return fail(ctx, NPCF_EINVAL, "no accumulate call yet");
+    CU(cudaDeviceSynchronize());
+    std::vector<uint32_t> sidx(n);
+    CU(cudaMemcpy(sidx.data(), ctx->idx.p, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    std::vector<int> inv(n, -1);
+    for (int q = 0; q < n; ++q) inv[sidx[q]] = q;
+    const int per = ctx->nr * ctx->nlm;
+    for (int64_t q = 0; q < k; ++q) {
+        if (idx[q] < 0 || idx[q] >= n) return fail(ctx, NPCF_EINVAL, "index out of range");
+        const int sp = inv[idx[q]];
+        CU(cudaMemcpy(alm + q * per * 2, ctx->alm.p + (size_t)sp * per, per * sizeof(float2),
+                      cudaMemcpyDeviceToHost));
+        if (counts)
+            CU(cudaMemcpy(counts + q * ctx->nr, ctx->cnt.p + (size_t)sp * ctx->nr, ctx->nr * sizeof(uint32_t),
+                          cudaMemcpyDeviceToHost));
+    }
+    return NPCF_OK;
+}
+
+npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    switch (key) {
+        case 0:
+            if (value < 1 || value > 8) return fail(ctx, NPCF_EINVAL, "cells per r_max in [1, 8]");
+            ctx->cells_per_rmax = value;
+            return NPCF_OK;
+        case 1:
+            if (value < 1 || value > 16) return fail(ctx, NPCF_EINVAL, "pair warps in [1, 16]");
+            ctx->pair_warps = value;
+            return NPCF_OK;
+        case 2:
+            if (value < 0) return fail(ctx, NPCF_EINVAL, "chunk must be >= 0");
+            ctx->chunk_target = value;
+            return NPCF_OK;
+        case 3:
+            if (value < 64 || value > 16384) return fail(ctx, NPCF_EINVAL, "pair capacity in [64, 16384]");
+            ctx->pair_cap = value;
+            return NPCF_OK;
+        default:
+            return fail(ctx, NPCF_EINVAL, "unknown tuning key %d", key);
+    }
+}
+
+npcf_status npcf_get_timings(npcf_ctx* ctx, float* ms4) {
+    if (check_ctx(ctx) != NPCF_OK || !ms4) return NPCF_EINVAL;
+    for (int i = 0; i < 4; ++i) {
+        ms4[i] = 0.f;
+        CU(cudaEventSynchronize(ctx->ev[i + 1]));
+        CU(cudaEventElapsedTime(&ms4[i], ctx->ev[i], ctx->ev[i + 1]));
+    }
+    return NPCF_OK;
+}
+
+const char* npcf_last_error(const npcf_ctx* ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+void npcf_destroy(npcf_ctx* ctx) {
+    if (!ctx) return;
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;  // device buffers are released by their destructors
+}
+
+}  // extern "C"

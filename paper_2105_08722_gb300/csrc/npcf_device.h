@@ -1,0 +1,109 @@
+// Argument blocks and launch wrappers shared by the kernels of libencore_gpu.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "npcf_tables.h"
+
+namespace npcf {
+
+// Cartesian cell grid of the neighbour search (cells sorted x fastest, then y, z).
+struct GridInfo {
+    int gx, gy, gz, ncell;
+    float ox, oy, oz;      // origin of cell (0,0,0)
+    float inv_cell;        // 1 / cell side
+    int periodic;
+    float L, hL;           // periodic side and float(L/2)
+};
+
+// ---------------------------------------------------------------- cell list (a1)
+struct BinArgs {
+    const float* pos;      // [n][3] input order
+    const float* w;        // [n]
+    const float* wprim;    // [n] or nullptr (= w)
+    int n;
+    GridInfo g;
+    uint32_t* cid;         // [n] cell of each input point
+    uint32_t* count;       // [ncell] histogram (zeroed by caller)
+    uint32_t* start;       // [ncell + 1] exclusive scan
+    uint32_t* cursor;      // [ncell] scatter cursors
+    float4* pts;           // [n] sorted (x, y, z, w)
+    float* wp;             // [n] sorted primary weights
+    uint32_t* idx;         // [n] sorted -> input index
+    uint32_t* cell_of;     // [n] sorted -> cell
+    int* err;              // error bits (1: position outside the periodic box / NaN)
+    float* bbox_part;      // [nblocks][6] partial min/max (non-periodic)
+};
+
+void launch_bbox(const float* pos, int n, float* part, int nblocks, cudaStream_t s);
+void launch_bin(const BinArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- pair kernel (a2 + a3)
+struct PairArgs {
+    const float4* pts;
+    const float* wp;
+    const uint32_t* cell_of;
+    const uint32_t* cell_start;
+    const int4* rows;          // (dy, dz, dx_lo, dx_hi) neighbour rows
+    int nrows;
+    GridInfo g;
+    float e2[kMaxNr + 1];
+    int nr;
+    int lmax;
+    const float* kmat;         // [nlm][lmax + 1] Y_lm conversion matrix
+    float2* alm;               // [n][nr][nlm]
+    uint32_t* cnt;             // [n][nr]
+    unsigned long long* counts;// [nr]
+    int n;
+    int* work;                 // dynamic primary counter (zeroed by caller)
+    int cap;                   // entries per warp buffer
+    int warps;                 // warps per block
+};
+
+void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s);
+size_t pair_smem_bytes(int warps, int cap);
+
+// ---------------------------------------------------------------- contraction (a4 + a5)
+struct Contract3Args {
+    const float2* alm;
+    const float* wp;
+    int n, nr, nlm, lmax;
+    int nchunk, chunk;         // primaries per chunk
+    const int2* rows;          // (l, pair index) rows
+    const int2* pairs;         // (b1, b2)
+    const float* coef;         // per l
+    int nrows;
+    double* partial;           // [nchunk][total]
+    int total, out_off;        // entries of the whole output, first entry of this order
+    int nbins;
+};
+
+struct Contract4Args {
+    const float2* alm;
+    const float* wp;
+    int n, nr, nlm;
+    int nchunk, chunk;
+    const int4* rows;          // (multiplet, b1, b2, first output entry)
+    int nrows;
+    const PairTerm* terms;
+    int nterms;
+    const int* seg_begin;
+    const int* seg_end;
+    const int* seg_lm3;
+    const float* seg_factor;
+    const int* lam_seg0;
+    const int* lam_odd;
+    int nseg, nlam;
+    double* partial;
+    int total;
+};
+
+void launch_contract3(const Contract3Args& a, cudaStream_t s);
+void launch_contract4(const Contract4Args& a, cudaStream_t s);
+size_t contract4_smem_bytes(const Contract4Args& a);
+
+// ---------------------------------------------------------------- FP64 reduction (a6)
+void launch_reduce(const double* partial, int nchunk, int total, double* zeta, cudaStream_t s);
+
+}  // namespace npcf

@@ -1,0 +1,165 @@
+// Host-side tables of libencore_gpu (see npcf_tables.h).
+#include "npcf_tables.h"
+
+#include <cmath>
+#include <cstdlib>
+
+namespace npcf {
+
+namespace {
+
+// n! for n <= 63 in long double (exact to 25! and within a few ulp beyond).
+struct FactTable {
+    long double f[64];
+    FactTable() {
+        f[0] = 1.0L;
+        for (int i = 1; i < 64; ++i) f[i] = f[i - 1] * (long double)i;
+    }
+};
+const FactTable& facts() {
+    static FactTable t;
+    return t;
+}
+
+inline int neg1pow(int k) { return (k & 1) ? -1 : 1; }
+
+}  // namespace
+
+double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3) {
+    if (m1 + m2 + m3 != 0) return 0.0;
+    if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
+    if (j3 > j1 + j2 || j3 < std::abs(j1 - j2)) return 0.0;
+    const long double* f = facts().f;
+    // triangle coefficient and the m-dependent square root, then the alternating sum
+    long double delta = f[j1 + j2 - j3] * f[j1 - j2 + j3] * f[-j1 + j2 + j3] / f[j1 + j2 + j3 + 1];
+    long double root = std::sqrt(delta * f[j1 + m1] * f[j1 - m1] * f[j2 + m2] * f[j2 - m2] *
+                                 f[j3 + m3] * f[j3 - m3]);
+    int lo = 0;
+    if (j2 - j3 - m1 > lo) lo = j2 - j3 - m1;
+    if (j1 - j3 + m2 > lo) lo = j1 - j3 + m2;
+    int hi = j1 + j2 - j3;
+    if (j1 - m1 < hi) hi = j1 - m1;
+    if (j2 + m2 < hi) hi = j2 + m2;
+    long double sum = 0.0L;
+    for (int t = lo; t <= hi; ++t) {
+        long double d = f[t] * f[j3 - j2 + t + m1] * f[j3 - j1 + t - m2] * f[j1 + j2 - j3 - t] *
+                        f[j1 - t - m1] * f[j2 - t + m2];
+        sum += neg1pow(t) / d;
+    }
+    return (double)(neg1pow(j1 - j2 - m3) * root * sum);
+}
+
+bool OrderTable::odd(int a) const {
+    const int* L = &lam[(size_t)a * width];
+    int s = (N == 5) ? L[0] + L[1] + L[3] + L[4] : (N == 4 ? L[0] + L[1] + L[2] : 2 * L[0]);
+    return (s & 1) != 0;
+}
+
+OrderTable make_order(int N, int lmax, int nr, bool allparity) {
+    OrderTable o;
+    o.N = N;
+    o.width = (N == 3) ? 2 : (N == 4 ? 3 : 5);
+    if (N == 3) {
+        for (int l = 0; l <= lmax; ++l) { o.lam.push_back(l); o.lam.push_back(l); }
+    } else if (N == 4) {
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = 0; l2 <= lmax; ++l2) {
+                int top = l1 + l2 < lmax ? l1 + l2 : lmax;
+                for (int l3 = std::abs(l1 - l2); l3 <= top; ++l3) {
+                    if (!allparity && ((l1 + l2 + l3) & 1)) continue;
+                    o.lam.insert(o.lam.end(), {l1, l2, l3});
+                }
+            }
+    } else if (N == 5) {
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = 0; l2 <= lmax; ++l2)
+                for (int l12 = std::abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                    for (int l3 = 0; l3 <= lmax; ++l3) {
+                        int top = l12 + l3 < lmax ? l12 + l3 : lmax;
+                        for (int l4 = std::abs(l12 - l3); l4 <= top; ++l4) {
+                            if (!allparity && ((l1 + l2 + l3 + l4) & 1)) continue;
+                            o.lam.insert(o.lam.end(), {l1, l2, l12, l3, l4});
+                        }
+                    }
+    }
+    // strictly increasing bin tuples, lexicographic, last index fastest
+    int k = N - 1;
+    std::vector<int> b(k);
+    if (nr >= k) {
+        for (int i = 0; i < k; ++i) b[i] = i;
+        while (true) {
+            o.bins.insert(o.bins.end(), b.begin(), b.end());
+            int i = k - 1;
+            while (i >= 0 && b[i] == nr - k + i) --i;
+            if (i < 0) break;
+            ++b[i];
+            for (int j = i + 1; j < k; ++j) b[j] = b[j - 1] + 1;
+        }
+    }
+    return o;
+}
+
+std::vector<double> ylm_power_matrix(int lmax) {
+    const long double* f = facts().f;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double> K((size_t)nlm(lmax) * (lmax + 1), 0.0);
+    for (int l = 0; l <= lmax; ++l) {
+        // power-series coefficients of P_l: c[n] z^n, n = l - 2j
+        std::vector<long double> c(l + 1, 0.0L);
+        for (int j = 0; 2 * j <= l; ++j)
+            c[l - 2 * j] = neg1pow(j) * f[2 * l - 2 * j] /
+                           (std::pow(2.0L, l) * f[j] * f[l - j] * f[l - 2 * j]);
+        for (int m = 0; m <= l; ++m) {
+            long double norm = std::sqrt((2.0L * l + 1.0L) / (4.0L * pi) * f[l - m] / f[l + m]);
+            for (int kk = 0; kk + m <= l; ++kk) {
+                // coefficient of z^k in N_lm (-1)^m d^m P_l / dz^m
+                long double v = norm * neg1pow(m) * c[kk + m] * f[kk + m] / f[kk];
+                K[(size_t)lm_index(l, m) * (lmax + 1) + kk] = (double)v;
+            }
+        }
+    }
+    return K;
+}
+
+PairTerm make_pair_term(double c, int l1, int m1, int l2, int m2) {
+    double s1 = (m1 < 0) ? neg1pow(m1) : 1.0, g1 = (m1 < 0) ? -1.0 : 1.0;
+    double s2 = (m2 < 0) ? neg1pow(m2) : 1.0, g2 = (m2 < 0) ? -1.0 : 1.0;
+    double cc = c * s1 * s2;
+    PairTerm t;
+    t.cA = (float)cc;
+    t.cB = (float)(-cc * g1 * g2);
+    t.cC = (float)(cc * g1);
+    t.cD = (float)(cc * g2);
+    t.lm1 = (uint16_t)lm_index(l1, std::abs(m1));
+    t.lm2 = (uint16_t)lm_index(l2, std::abs(m2));
+    return t;
+}
+
+ContractTable4 make_contract4(const OrderTable& o) {
+    ContractTable4 t;
+    int na = o.n_lambda();
+    for (int a = 0; a < na; ++a) {
+        const int* L = &o.lam[(size_t)a * 3];
+        int l1 = L[0], l2 = L[1], l3 = L[2];
+        int E = neg1pow(l1 + l2 + l3);
+        t.lam_seg0.push_back((int)t.seg_begin.size());
+        for (int m3 = 0; m3 <= l3; ++m3) {
+            t.seg_begin.push_back((int)t.terms.size());
+            for (int m1 = -l1; m1 <= l1; ++m1) {
+                int m2 = -m1 - m3;
+                if (std::abs(m2) > l2) continue;
+                // E(L) C^L_M with C^L_M = E(L) (l1 l2 l3; m1 m2 m3)  (Eq. N=4-coeff)
+                double c = E * (E * wigner3j(l1, l2, l3, m1, m2, m3));
+                if (std::fabs(c) < 1e-14) continue;
+                t.terms.push_back(make_pair_term(c, l1, m1, l2, m2));
+            }
+            t.seg_end.push_back((int)t.terms.size());
+            t.seg_lm3.push_back(lm_index(l3, m3));
+            t.seg_factor.push_back(m3 == 0 ? 1.0f : 2.0f);
+        }
+    }
+    t.lam_seg0.push_back((int)t.seg_begin.size());
+    return t;
+}
+
+}  // namespace npcf

@@ -1,0 +1,66 @@
+// Host-side tables of libencore_gpu: multiplet and bin enumerations, coupling
+// coefficients and the spherical-harmonic conversion matrix. Built once per
+// context and uploaded to the device.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace npcf {
+
+constexpr int kMaxL = 10;    // largest lmax of the pair kernel
+constexpr int kMaxNr = 16;   // largest number of radial shells
+
+// Wigner 3-j symbol (Racah's closed form, DLMF 34.2.4).
+double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
+
+// Number of complex slots per shell in the a_lm layout: l <= lmax, 0 <= m <= l.
+inline int nlm(int lmax) { return (lmax + 1) * (lmax + 2) / 2; }
+inline int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
+
+// One order N of the statistic: its multiplets L and bin tuples B.
+struct OrderTable {
+    int N = 0;
+    int width = 0;                  // ints per multiplet: 2 (N=3), 3 (N=4), 5 (N=5)
+    std::vector<int> lam;           // n_lambda x width
+    std::vector<int> bins;          // n_bins x (N-1)
+    int n_lambda() const { return width ? (int)lam.size() / width : 0; }
+    int n_bins() const { return N > 1 ? (int)bins.size() / (N - 1) : 0; }
+    bool odd(int a) const;          // parity-odd multiplet (odd sum of principal l)
+};
+
+OrderTable make_order(int N, int lmax, int nr, bool allparity);
+
+// a_lm from the sums S_{m,k} = sum_j w_j (x + i y)^m z^k over unit separations,
+// m + k <= lmax: a_lm = sum_k K[lm_index(l,m)][k] S_{m,k}. Derived from
+// Y_lm = N_lm (-1)^m (x+iy)^m d^m P_l(z)/dz^m (Condon-Shortley phase, unit vectors)
+// and the power series of the Legendre polynomial P_l.
+std::vector<double> ylm_power_matrix(int lmax);
+
+// One product term c * a^{b1}_{l1 m1} * a^{b2}_{l2 m2} with m1, m2 of either sign,
+// written on the stored m >= 0 coefficients (x1 + i y1), (x2 + i y2) using
+// a_{l,-m} = (-1)^m conj(a_{l m}):
+//   re += cA x1 x2 + cB y1 y2 ;  im += cC y1 x2 + cD x1 y2.
+struct PairTerm {
+    float cA, cB, cC, cD;
+    uint16_t lm1, lm2;
+};
+
+PairTerm make_pair_term(double c, int l1, int m1, int l2, int m2);
+
+// 4PCF contraction table (Eq. simple-NPCF-summation at N=4): for multiplet a and
+// m3 = 0..l3 one segment of terms over m1, with m2 = -m1 - m3,
+//   P^{a,m3}(b1,b2) = sum_{m1} E(L) C^L_{m1 m2 m3} a^{b1}_{l1 m1} a^{b2}_{l2 m2},
+// and zeta += u * 2 S(m3) * Q_L[P^{a,m3} a^{b3}_{l3 m3}].
+struct ContractTable4 {
+    std::vector<PairTerm> terms;
+    std::vector<int> seg_begin;     // per segment: [begin, end) into terms
+    std::vector<int> seg_end;
+    std::vector<int> seg_lm3;       // lm index of a_{l3 m3}
+    std::vector<float> seg_factor;  // 2 S(m3)
+    std::vector<int> lam_seg0;      // first segment of multiplet a (n_lambda + 1 entries)
+};
+
+ContractTable4 make_contract4(const OrderTable& o);
+
+}  // namespace npcf

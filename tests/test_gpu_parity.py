@@ -1,0 +1,267 @@
+"""GPU path (libencore_gpu through its C ABI) against the FP64 oracle.
+
+Bars: neighbour counts bit-exact; every multiplet within 1e-5 of its order's RMS on
+the FP32 path (within 3e-5 on the split-BF16 path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_08722_gb300 import catalogs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_08722_gb300 import build
+    build()
+    oracle.build()
+    return torch, torch.device("cuda:0")
+
+
+def gpu_run(torch_dev, pos, w, orders, lmax, edges, box=0.0, allparity=False, wprim=None,
+            prec=0, tuning=None):
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    est = NPCF(lmax, orders, edges, box, prec, allparity)
+    for k, v in (tuning or {}).items():
+        est.set_tuning(k, v)
+    tp = torch.from_numpy(np.ascontiguousarray(pos, np.float32)).to(dev)
+    tw = torch.from_numpy(np.ascontiguousarray(w, np.float32)).to(dev)
+    twp = None if wprim is None else torch.from_numpy(np.ascontiguousarray(wprim, np.float32)).to(dev)
+    est.accumulate(tp, tw, wprim=twp)
+    return est, est.finalize(), est.pair_counts()
+
+
+def assert_orders_close(got, want, orders, lmax, nr, allparity=False, tol=TOL_FP32):
+    g = oracle.split_orders(got, orders, lmax, nr, allparity)
+    o = oracle.split_orders(want, orders, lmax, nr, allparity)
+    for N in orders:
+        rms = math.sqrt(float(np.mean(o[N] ** 2)))
+        assert rms > 0
+        err = float(np.max(np.abs(g[N] - o[N]))) / rms
+        assert err <= tol, "order %d: max |gpu - oracle| / rms = %.3e" % (N, err)
+
+
+def _catalog(n, side, seed, weights=True):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0, side, size=(n, 3)).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, size=n).astype(np.float32) if weights else np.ones(n, np.float32)
+    return pos, w
+
+
+# ------------------------------------------------------------------ neighbour counts
+
+@pytest.mark.parametrize("n,box,edges", [
+    (1, 50.0, [0.0, 5.0, 10.0]),
+    (2, 50.0, [0.0, 5.0, 10.0]),
+    (33, 60.0, [1.0, 4.0, 9.0, 15.0]),
+    (1000, 100.0, list(np.linspace(0.0, 30.0, 11))),
+    (5003, 200.0, list(np.linspace(5.0, 50.0, 16))),
+    (777, 0.0, list(np.linspace(2.0, 20.0, 7))),
+])
+def test_pair_counts_bit_exact(torch_dev, n, box, edges):
+    pos, w = _catalog(n, box if box > 0 else 80.0, 100 + n)
+    for k in (1, 3, 4):   # several cell sizes must give the same neighbour sets
+        est, _, counts = gpu_run(torch_dev, pos, w, (3,), 2, edges, box, tuning={0: k})
+        assert np.array_equal(counts, oracle.pair_counts(pos, edges, box)), k
+        est.close()
+
+
+def test_pair_counts_on_exact_edges_and_duplicates(torch_dev):
+    # secondaries placed at exactly representable distances equal to the shell edges,
+    # coincident points and points at |d| = L/2 in a periodic box
+    edges = [0.0, 2.0, 4.0, 8.0]
+    base = np.array([20.0, 20.0, 20.0], np.float32)
+    pts = [base, base.copy()]                                  # coincident pair
+    for e in edges:
+        for ax in range(3):
+            p = base.copy()
+            p[ax] += np.float32(e)
+            pts.append(p)
+            q = base.copy()
+            q[ax] -= np.float32(e)
+            pts.append(q)
+    pts.append(np.array([0.0, 20.0, 20.0], np.float32))
+    pts.append(np.array([39.5, 20.0, 20.0], np.float32))        # 0.5 apart through the wall
+    pos = np.array(pts, np.float32)
+    w = np.ones(len(pos), np.float32)
+    for box in (0.0, 40.0):
+        _, _, counts = gpu_run(torch_dev, pos, w, (3,), 1, edges, box)
+        assert np.array_equal(counts, oracle.pair_counts(pos, edges, box)), box
+
+
+# ------------------------------------------------------------------ a_lm
+
+def test_alm_of_sampled_primaries(torch_dev):
+    pos, w = _catalog(4000, 150.0, 7)
+    edges = np.linspace(5.0, 40.0, 8)
+    lmax = 6
+    est, _, _ = gpu_run(torch_dev, pos, w, (3,), lmax, edges, 150.0)
+    sample = np.array([0, 1, 17, 500, 1999, 3998, 3999])
+    a_gpu, c_gpu = est.debug_alm(sample)
+    a_orc, c_orc = oracle.alm(pos, w, sample, lmax, edges, 150.0)
+    assert np.array_equal(c_gpu, c_orc)
+    for l in range(lmax + 1):
+        for m in range(l + 1):
+            g = a_gpu[:, :, l * (l + 1) // 2 + m]
+            o = a_orc[:, :, l * l + l + m]
+            scale = np.sqrt(np.mean(np.abs(a_orc) ** 2))
+            assert np.max(np.abs(g - o)) <= 1e-5 * scale, (l, m)
+
+
+# ------------------------------------------------------------------ multiplets
+
+def test_3pcf_uniform_4096_box250_full(torch_dev):
+    wl = catalogs.c1_uniform_3pcf()
+    _, got, counts = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box)
+    want, wcounts = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
+
+
+def test_4pcf_3pcf_periodic_lmax5_10_shells(torch_dev):
+    pos = catalogs.lognormal_box(2500, 300.0, 64, seed=31)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(8.0, 60.0, 11)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 5, edges, 300.0)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 5, edges, 300.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4), 5, 10)
+
+
+def test_4pcf_all_parity_non_periodic_weighted(torch_dev):
+    pos, w = _catalog(1500, 120.0, 41)
+    w = w - np.float32(0.9)          # mixed-sign weights, like data minus randoms
+    edges = np.linspace(6.0, 36.0, 7)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 0.0, allparity=True)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 4, edges, 0.0, allparity=True)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4), 4, 6, allparity=True)
+
+
+def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
+    for n in (0, 1, 5):
+        pos, w = _catalog(max(n, 1), 30.0, 50 + n)
+        pos, w = pos[:n], w[:n]
+        edges = [1.0, 12.0]
+        if n == 0:
+            from paper_2105_08722_gb300._lib import NPCF
+            est = NPCF(0, (3,), edges, 0.0)
+            assert np.all(est.finalize() == 0)
+            continue
+        _, got, counts = gpu_run(torch_dev, pos, w, (3,), 0, edges, 0.0)
+        want, wcounts = oracle.npcf(pos, w, (3,), 0, edges, 0.0)
+        assert np.array_equal(counts, wcounts)
+        assert got.shape == want.shape and np.all(got == 0) and np.all(want == 0)
+
+
+def test_dense_primaries_need_several_list_slices(torch_dev):
+    # a small per-warp list forces the multi-slice path of the pair kernel
+    pos, w = _catalog(3000, 60.0, 61)
+    edges = np.linspace(2.0, 18.0, 5)
+    _, got_small, c_small = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0, tuning={3: 64})
+    _, got_big, c_big = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 3, edges, 60.0)
+    assert np.array_equal(c_small, wcounts) and np.array_equal(c_big, wcounts)
+    assert_orders_close(got_small, want, (3, 4), 3, 4)
+    assert_orders_close(got_big, want, (3, 4), 3, 4)
+
+
+def test_accumulate_coadds_and_reset(torch_dev):
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    a_pos, a_w = _catalog(800, 100.0, 71)
+    b_pos, b_w = _catalog(900, 100.0, 72)
+    edges = np.linspace(4.0, 30.0, 6)
+    est = NPCF(3, (3, 4), edges, 100.0)
+    for p, ww in ((a_pos, a_w), (b_pos, b_w)):
+        est.accumulate(torch.from_numpy(p).to(dev), torch.from_numpy(ww).to(dev))
+    got = est.finalize()
+    za, _ = oracle.npcf(a_pos, a_w, (3, 4), 3, edges, 100.0)
+    zb, _ = oracle.npcf(b_pos, b_w, (3, 4), 3, edges, 100.0)
+    assert_orders_close(got, za + zb, (3, 4), 3, 5)
+    est.reset()
+    assert np.all(est.finalize() == 0) and np.all(est.pair_counts() == 0)
+
+
+def test_host_entry_point_matches_device_entry_point(torch_dev):
+    from paper_2105_08722_gb300._lib import NPCF
+    pos, w = _catalog(1200, 90.0, 81)
+    edges = np.linspace(3.0, 25.0, 6)
+    _, dev_out, dev_counts = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 90.0)
+    est = NPCF(4, (3, 4), edges, 90.0)
+    est.accumulate_host(pos, w)
+    assert np.array_equal(est.finalize(), dev_out)
+    assert np.array_equal(est.pair_counts(), dev_counts)
+
+
+def test_primary_weights_select_a_sample(torch_dev):
+    pos, w = _catalog(2000, 120.0, 91)
+    edges = np.linspace(4.0, 30.0, 7)
+    rng = np.random.default_rng(92)
+    sample = np.sort(rng.choice(len(pos), 50, replace=False))
+    wp = np.zeros(len(pos), np.float32)
+    wp[sample] = w[sample]
+    _, got, _ = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 120.0, wprim=wp)
+    want, _ = oracle.npcf(pos, w, (3, 4), 4, edges, 120.0, prim=sample)
+    assert_orders_close(got, want, (3, 4), 4, 6)
+
+
+def test_periodic_normalisation(torch_dev):
+    pos, w = _catalog(1500, 100.0, 95, weights=False)
+    edges = np.linspace(5.0, 30.0, 6)
+    est, raw, _ = gpu_run(torch_dev, pos, w, (3, 4), 2, edges, 100.0)
+    norm = est.finalize(normalize=True)
+    V = 100.0 ** 3
+    nbar = len(pos) / V
+    vb = 4 * math.pi / 3 * (edges[1:] ** 3 - edges[:-1] ** 3)
+    parts_raw = est.split(raw)
+    parts = est.split(norm)
+    for N in (3, 4):
+        _, bins = est.layout(N)
+        vB = V * np.prod(vb[bins], axis=1)
+        R0 = (4 * math.pi) ** (-(N - 1) / 2) * nbar ** N
+        assert np.allclose(parts[N], parts_raw[N] / (vB * R0), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ full-size workload
+
+@pytest.fixture(scope="module")
+def c2_workload():
+    return catalogs.c2_lognormal_4pcf()
+
+
+def test_lognormal_200k_4pcf_sampled_primaries(torch_dev, c2_workload):
+    """The 200k log-normal 4PCF+3PCF workload at full size, in the bench's launch
+    configuration; the oracle evaluates a seeded sample of primaries one by one."""
+    wl = c2_workload
+    rng = np.random.default_rng(2024)
+    sample = np.sort(rng.choice(wl.n, 48, replace=False))
+    wp = np.zeros(wl.n, np.float32)
+    wp[sample] = wl.w[sample]
+    est, got, _ = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wp)
+    a_gpu, c_gpu = est.debug_alm(sample)
+    a_orc, c_orc = oracle.alm(wl.pos, wl.w, sample, wl.lmax, wl.edges, wl.box)
+    assert np.array_equal(c_gpu, c_orc)
+    want, _ = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample)
+    assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
+
+
+def test_lognormal_200k_full_run_is_sum_of_complementary_samples(torch_dev, c2_workload):
+    wl = c2_workload
+    _, full, cfull = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box)
+    mask = (np.arange(wl.n) % 3 == 0).astype(np.float32)
+    _, a, ca = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wl.w * mask)
+    _, b, cb = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box,
+                       wprim=wl.w * (1 - mask))
+    assert np.array_equal(ca + cb, cfull)
+    assert_orders_close(a + b, full, wl.orders, wl.lmax, len(wl.edges) - 1, tol=1e-6)
