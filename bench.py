@@ -220,13 +220,14 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
 
-    st = np.mean(np.array(stage_ms), axis=0)   # [cell list, pair, contraction, reduction]
+    st = np.mean(np.array(stage_ms, dtype=np.float64), axis=0)   # [cell list, pair, contraction, reduction]
     npairs_per_step = float(counts.sum()) / (args.warmup + args.steps)
     pair_tflops = npairs_per_step * PAIR_ALG_FLOP / (st[1] * 1e-3) / 1e12
     con_tflops = wl.n * FOURPCF_ALG_FLOP_PER_PRIMARY / (st[2] * 1e-3) / 1e12
     fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     dominant = "pair" if st[1] >= st[2] else "contraction"
     achieved = pair_tflops if dominant == "pair" else con_tflops
+    achieved = float(achieved)
     line = {
         "metric": METRIC,
         "value": wl.n * world / (ms * 1e-3),

@@ -130,10 +130,13 @@ npcf_status npcf_reset(npcf_ctx* ctx);
 npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* alm,
                            uint32_t* counts);
 
-/* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8),
- * key 1 = pair-kernel warps per block (1..16), key 2 = contraction primaries per
- * chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per warp
- * (64..16384 entries; larger lists mean fewer passes for dense primaries). */
+/* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8; the cell
+ * side of the neighbour grid is about r_max / key0), key 2 = contraction primaries
+ * per chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per warp
+ * (even, 64..8192 entries; larger lists mean fewer passes for dense primaries, smaller
+ * ones leave more shared memory for staging neighbour cells), key 4 = cap on the
+ * neighbour points staged in shared memory per cell (0 = as many as fit; cells with
+ * more neighbours read them from global memory instead). */
 npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);
 
 /* Device time in ms of the stages of the last accumulate call:

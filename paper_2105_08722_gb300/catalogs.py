@@ -62,7 +62,7 @@ def gaussian_field(mesh: int, box: float, rng, slope: float = -1.5, kcut: float 
     psum = float((pk * wz[None, None, :]).sum())
     # E|noise_k|^2 = mesh^3, so Var(G) = (c^2 / mesh^3) sum_k P(k); pick c for sigma_g.
     c2 = sigma_g ** 2 * mesh ** 3 / psum
-    g = np.fft.irfftn(nk * np.sqrt(pk * c2), s=(mesh, mesh, mesh))
+    g = np.fft.irfftn(nk * np.sqrt(pk * c2), s=(mesh, mesh, mesh), axes=(0, 1, 2))
     return g
 
 

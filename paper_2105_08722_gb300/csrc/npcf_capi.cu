@@ -62,8 +62,8 @@ struct npcf_ctx {
 
     // cell-list tuning and geometry
     int cells_per_rmax = 4;
-    int pair_warps = 8;
     int pair_cap = 4096;
+    int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -160,7 +160,7 @@ std::vector<int> make_rows(float cell, double rmax, int* reach) {
 npcf_status setup_tables(npcf_ctx* ctx) {
     ctx->nlm = nlm(ctx->lmax);
     // Y_lm conversion matrix
-    std::vector<double> K = ylm_power_matrix(ctx->lmax);
+    std::vector<double> K = ylm_chebyshev_matrix(ctx->lmax);
     std::vector<float> Kf(K.begin(), K.end());
     CU(upload(ctx->kmat, Kf));
     ctx->total = 0;
@@ -246,7 +246,8 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s)
         for (int q = k - 1; q >= 1; --q) order.push_back(q);
         bool found = false;
         for (int q : order) {
-            int gg = (int)std::floor(L * q / rmax);
+            // 0.999: r_max / cell never an integer, so rows at exactly r_max drop out
+            int gg = (int)std::floor(L * q / rmax * 0.999);
             if (gg < 1) gg = 1;
             gg = std::min(gg, 1024);
             float cell = (float)(L / gg);
@@ -290,7 +291,7 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s)
             if (!std::isfinite(mn[a]) || !std::isfinite(mx[a]))
                 return fail(ctx, NPCF_EINVAL, "non-finite positions");
         }
-        float cell = (float)(rmax / k);
+        float cell = (float)(rmax / k * 1.001);
         int dims[3];
         double ncell = 1;
         for (int a = 0; a < 3; ++a) {
@@ -401,18 +402,20 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     pa.n = n;
     pa.work = ctx->work.p;
     pa.cap = ctx->pair_cap;
-    pa.warps = ctx->pair_warps;
+    pa.err = ctx->errflag.p;
     {
         int dev = 0, optin = 0;
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const size_t need = (size_t)pa.nrows * sizeof(int4) + pair_smem_bytes(pa.warps, pa.cap) + 16384;
-        if (need > (size_t)optin)
-            return fail(ctx, NPCF_EINVAL, "pair kernel needs %zu B of shared memory (limit %d): lower "
-                        "the warps or the list capacity", need, optin);
+        pa.cand_cap = 0;
+        const long long room = (long long)optin - kPairStaticSmem - (long long)pair_dynamic_smem(pa);
+        if (room < 16 * 256)
+            return fail(ctx, NPCF_EINVAL, "pair kernel: neighbour-list capacity %d leaves no room for "
+                        "staging (shared memory limit %d B)", pa.cap, optin);
+        pa.cand_cap = (int)std::min<long long>(room / 16, 65535);
+        if (ctx->stage_limit > 0) pa.cand_cap = std::min(pa.cand_cap, ctx->stage_limit);
     }
-    const int pair_blocks_per_sm = 1;
-    launch_pair(pa, ctx->nsm * pair_blocks_per_sm, s);
+    launch_pair(pa, ctx->nsm, s);   // persistent: one block per SM, cells taken dynamically
     CU(cudaGetLastError());
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[2], s));
 
@@ -605,6 +608,7 @@ npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normal
     int errbits = 0;
     CU(cudaMemcpy(&errbits, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (errbits & 1) return fail(ctx, NPCF_EINVAL, "positions outside [0, box) or not finite");
+    if (errbits & 2) return fail(ctx, NPCF_ETIMEOUT, "a bounded device wait gave up; results are incomplete");
     if (ctx->total > 0)
         CU(cudaMemcpy(out, ctx->zeta.p, ctx->total * sizeof(double), cudaMemcpyDeviceToHost));
     if (normalize) {
@@ -670,17 +674,18 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             if (value < 1 || value > 8) return fail(ctx, NPCF_EINVAL, "cells per r_max in [1, 8]");
             ctx->cells_per_rmax = value;
             return NPCF_OK;
-        case 1:
-            if (value < 1 || value > 16) return fail(ctx, NPCF_EINVAL, "pair warps in [1, 16]");
-            ctx->pair_warps = value;
-            return NPCF_OK;
         case 2:
             if (value < 0) return fail(ctx, NPCF_EINVAL, "chunk must be >= 0");
             ctx->chunk_target = value;
             return NPCF_OK;
         case 3:
-            if (value < 64 || value > 16384) return fail(ctx, NPCF_EINVAL, "pair capacity in [64, 16384]");
+            if (value < 64 || value > 8192 || (value & 1))
+                return fail(ctx, NPCF_EINVAL, "pair list capacity must be even and in [64, 8192]");
             ctx->pair_cap = value;
+            return NPCF_OK;
+        case 4:
+            if (value < 0) return fail(ctx, NPCF_EINVAL, "staging limit must be >= 0");
+            ctx->stage_limit = value;
             return NPCF_OK;
         default:
             return fail(ctx, NPCF_EINVAL, "unknown tuning key %d", key);

@@ -56,13 +56,16 @@ struct PairArgs {
     uint32_t* cnt;             // [n][nr]
     unsigned long long* counts;// [nr]
     int n;
-    int* work;                 // dynamic primary counter (zeroed by caller)
-    int cap;                   // entries per warp buffer
-    int warps;                 // warps per block
+    int* work;                 // dynamic cell counter (zeroed by caller)
+    int* err;                  // error bits (2: a bounded wait gave up)
+    int cap;                   // 16-bit entries per warp neighbour list
+    int cand_cap;              // points the staging buffer holds
 };
 
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s);
-size_t pair_smem_bytes(int warps, int cap);
+// dynamic shared memory of the pair kernel for a given capacity setting
+size_t pair_dynamic_smem(const PairArgs& a);
+constexpr int kPairStaticSmem = 16 * 1024;   // upper bound of its static shared memory
 
 // ---------------------------------------------------------------- contraction (a4 + a5)
 struct Contract3Args {

@@ -99,9 +99,16 @@ OrderTable make_order(int N, int lmax, int nr, bool allparity) {
     return o;
 }
 
-std::vector<double> ylm_power_matrix(int lmax) {
+std::vector<double> ylm_chebyshev_matrix(int lmax) {
     const long double* f = facts().f;
     const long double pi = 3.141592653589793238462643383279502884L;
+    // power-series coefficients of the Chebyshev polynomials T_k, k <= lmax
+    std::vector<std::vector<long double>> T(lmax + 1, std::vector<long double>(lmax + 1, 0.0L));
+    T[0][0] = 1.0L;
+    if (lmax >= 1) T[1][1] = 1.0L;
+    for (int k = 2; k <= lmax; ++k)
+        for (int n = 0; n <= k; ++n)
+            T[k][n] = (n > 0 ? 2.0L * T[k - 1][n - 1] : 0.0L) - T[k - 2][n];
     std::vector<double> K((size_t)nlm(lmax) * (lmax + 1), 0.0);
     for (int l = 0; l <= lmax; ++l) {
         // power-series coefficients of P_l: c[n] z^n, n = l - 2j
@@ -111,10 +118,14 @@ std::vector<double> ylm_power_matrix(int lmax) {
                            (std::pow(2.0L, l) * f[j] * f[l - j] * f[l - 2 * j]);
         for (int m = 0; m <= l; ++m) {
             long double norm = std::sqrt((2.0L * l + 1.0L) / (4.0L * pi) * f[l - m] / f[l + m]);
-            for (int kk = 0; kk + m <= l; ++kk) {
-                // coefficient of z^k in N_lm (-1)^m d^m P_l / dz^m
-                long double v = norm * neg1pow(m) * c[kk + m] * f[kk + m] / f[kk];
-                K[(size_t)lm_index(l, m) * (lmax + 1) + kk] = (double)v;
+            // q(z) = N_lm (-1)^m d^m P_l / dz^m in powers of z
+            std::vector<long double> q(l - m + 1, 0.0L);
+            for (int kk = 0; kk + m <= l; ++kk) q[kk] = norm * neg1pow(m) * c[kk + m] * f[kk + m] / f[kk];
+            // rewrite q in the Chebyshev basis, highest degree first
+            for (int d = l - m; d >= 0; --d) {
+                long double coef = q[d] / T[d][d];
+                K[(size_t)lm_index(l, m) * (lmax + 1) + d] = (double)coef;
+                for (int n = 0; n <= d; ++n) q[n] -= coef * T[d][n];
             }
         }
     }

@@ -31,11 +31,13 @@ struct OrderTable {
 
 OrderTable make_order(int N, int lmax, int nr, bool allparity);
 
-// a_lm from the sums S_{m,k} = sum_j w_j (x + i y)^m z^k over unit separations,
-// m + k <= lmax: a_lm = sum_k K[lm_index(l,m)][k] S_{m,k}. Derived from
-// Y_lm = N_lm (-1)^m (x+iy)^m d^m P_l(z)/dz^m (Condon-Shortley phase, unit vectors)
-// and the power series of the Legendre polynomial P_l.
-std::vector<double> ylm_power_matrix(int lmax);
+// a_lm from the sums S_{m,k} = sum_j w_j (x + i y)^m T_k(z) over unit separations,
+// m + k <= lmax, T_k the Chebyshev polynomials: a_lm = sum_k K[lm_index(l,m)][k] S_{m,k}.
+// Derived from Y_lm = N_lm (-1)^m (x+iy)^m d^m P_l(z)/dz^m (Condon-Shortley phase,
+// unit vectors): the polynomial factor is rewritten in the Chebyshev basis, whose
+// coefficients stay O(1) where the plain powers z^k would alternate in sign and grow,
+// so the FP32 sums lose little to cancellation.
+std::vector<double> ylm_chebyshev_matrix(int lmax);
 
 // One product term c * a^{b1}_{l1 m1} * a^{b2}_{l2 m2} with m1, m2 of either sign,
 // written on the stored m >= 0 coefficients (x1 + i y1), (x2 + i y2) using
