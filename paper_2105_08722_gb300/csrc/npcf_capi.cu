@@ -47,6 +47,10 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace npcf {
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace npcf
+
 struct npcf_ctx {
     int lmax = 0, nr = 0, prec = 0, allparity = 0;
     unsigned mask = 0;
@@ -131,32 +135,6 @@ cudaError_t upload(DevBuf<T>& b, const std::vector<T>& v) {
     return e;
 }
 
-// Neighbour rows (dy, dz, dx_lo, dx_hi) of cells that may hold a point within rmax of
-// some point of the centre cell. Cell-box gaps get a small slack so that points put in
-// a neighbouring cell by rounding are never missed.
-std::vector<int> make_rows(float cell, double rmax, int* reach) {
-    const double slack = 1e-3 * cell;
-    const double r2 = rmax * (1.0 + 1e-6) * rmax * (1.0 + 1e-6);
-    const int R = (int)std::ceil(rmax / cell) + 1;
-    auto gap = [&](int d) {
-        double gg = (std::abs(d) - 1) * (double)cell - slack;
-        return gg > 0 ? gg : 0.0;
-    };
-    std::vector<int> out;
-    int rmaxd = 0;
-    for (int dz = -R; dz <= R; ++dz)
-        for (int dy = -R; dy <= R; ++dy) {
-            double gyz = gap(dy) * gap(dy) + gap(dz) * gap(dz);
-            if (gyz > r2) continue;
-            int X = 0;
-            while (X + 1 <= R && gyz + gap(X + 1) * gap(X + 1) <= r2) ++X;
-            out.insert(out.end(), {dy, dz, -X, X});
-            rmaxd = std::max(rmaxd, std::max(X, std::max(std::abs(dy), std::abs(dz))));
-        }
-    *reach = rmaxd;
-    return out;
-}
-
 npcf_status setup_tables(npcf_ctx* ctx) {
     ctx->nlm = nlm(ctx->lmax);
     // Y_lm conversion matrix
@@ -236,41 +214,10 @@ npcf_status check_ctx(npcf_ctx* ctx) {
 npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s) {
     const double rmax = ctx->edges[ctx->nr];
     GridInfo g{};
-    int k = ctx->cells_per_rmax;
+    std::vector<int> rows;
     if (ctx->box > 0) {
-        const double L = ctx->box;
-        // the preferred cells per r_max first, then finer, then coarser grids: a grid is
-        // valid when no neighbour offset reaches the same cell twice (2 reach + 1 <= g)
-        std::vector<int> order;
-        for (int q = k; q <= 16; ++q) order.push_back(q);
-        for (int q = k - 1; q >= 1; --q) order.push_back(q);
-        bool found = false;
-        for (int q : order) {
-            // 0.999: r_max / cell never an integer, so rows at exactly r_max drop out
-            int gg = (int)std::floor(L * q / rmax * 0.999);
-            if (gg < 1) gg = 1;
-            gg = std::min(gg, 1024);
-            float cell = (float)(L / gg);
-            int reach = 0;
-            std::vector<int> rows = make_rows(cell, rmax, &reach);
-            if (2 * reach + 1 > gg) continue;
-            g.gx = g.gy = g.gz = gg;
-            g.ox = g.oy = g.oz = 0.f;
-            g.inv_cell = (float)(gg / L);
-            g.periodic = 1;
-            g.L = (float)L;
-            g.hL = (float)(0.5 * L);
-            if (rows != ctx->rows_host) {
-                ctx->rows_host = rows;
-                std::vector<int4> r4;
-                for (size_t i = 0; i < rows.size(); i += 4)
-                    r4.push_back(make_int4(rows[i], rows[i + 1], rows[i + 2], rows[i + 3]));
-                CU(upload(ctx->rows, r4));
-            }
-            found = true;
-            break;
-        }
-        if (!found) return fail(ctx, NPCF_EINVAL, "box %.6g too small for r_max %.6g", L, rmax);
+        if (!plan_periodic_grid(ctx->box, rmax, ctx->cells_per_rmax, 1 << 27, &g, &rows))
+            return fail(ctx, NPCF_EINVAL, "box %.6g too small for r_max %.6g", ctx->box, rmax);
     } else {
         // bounding box of the catalog (one stream synchronisation)
         const int nb = 256;
@@ -291,42 +238,15 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s)
             if (!std::isfinite(mn[a]) || !std::isfinite(mx[a]))
                 return fail(ctx, NPCF_EINVAL, "non-finite positions");
         }
-        float cell = (float)(rmax / k * 1.001);
-        int dims[3];
-        double ncell = 1;
-        for (int a = 0; a < 3; ++a) {
-            dims[a] = std::max(1, (int)std::floor((mx[a] - mn[a]) / cell) + 1);
-            ncell *= dims[a];
-        }
-        while (ncell > (1 << 24)) {  // keep the grid bounded for sparse, extended catalogs
-            cell *= 1.25f;
-            ncell = 1;
-            for (int a = 0; a < 3; ++a) {
-                dims[a] = std::max(1, (int)std::floor((mx[a] - mn[a]) / cell) + 1);
-                ncell *= dims[a];
-            }
-        }
-        g.gx = dims[0];
-        g.gy = dims[1];
-        g.gz = dims[2];
-        g.ox = mn[0];
-        g.oy = mn[1];
-        g.oz = mn[2];
-        g.inv_cell = 1.0f / cell;
-        g.periodic = 0;
-        g.L = 0.f;
-        g.hL = 0.f;
-        int reach = 0;
-        std::vector<int> rows = make_rows(cell, rmax, &reach);
-        if (rows != ctx->rows_host) {
-            ctx->rows_host = rows;
-            std::vector<int4> r4;
-            for (size_t i = 0; i < rows.size(); i += 4)
-                r4.push_back(make_int4(rows[i], rows[i + 1], rows[i + 2], rows[i + 3]));
-            CU(upload(ctx->rows, r4));
-        }
+        plan_open_grid(mn, mx, rmax, ctx->cells_per_rmax, 1 << 24, &g, &rows);
     }
-    g.ncell = g.gx * g.gy * g.gz;
+    if (rows != ctx->rows_host) {
+        ctx->rows_host = rows;
+        std::vector<int4> r4;
+        for (size_t i = 0; i < rows.size(); i += 4)
+            r4.push_back(make_int4(rows[i], rows[i + 1], rows[i + 2], rows[i + 3]));
+        CU(upload(ctx->rows, r4));
+    }
     ctx->grid = g;
     return NPCF_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "npcf_tables.h"
@@ -16,6 +17,13 @@ struct GridInfo {
     int periodic;
     float L, hL;           // periodic side and float(L/2)
 };
+
+// Host: neighbour-grid planning (npcf_grid.cpp). Rows are (dy, dz, dx_lo, dx_hi).
+std::vector<int> neighbour_rows(float cell, double rmax, int* reach);
+bool plan_periodic_grid(double L, double rmax, int cells_per_rmax, int max_cells, GridInfo* g,
+                        std::vector<int>* rows);
+void plan_open_grid(const float mn[3], const float mx[3], double rmax, int cells_per_rmax,
+                    int max_cells, GridInfo* g, std::vector<int>* rows);
 
 // ---------------------------------------------------------------- cell list (a1)
 struct BinArgs {

@@ -22,6 +22,7 @@
 //           S_{m,k} in registers; a shuffle transpose-reduction gives the per-shell
 //           sums, which are converted to a_lm and written once per (primary, shell).
 #include "npcf_device.h"
+#include "npcf_rules.cuh"
 
 namespace npcf {
 namespace {
@@ -34,23 +35,6 @@ __host__ __device__ constexpr int nlmc(int L) { return (L + 1) * (L + 2) / 2; }
 // position of Re S_{m,k} in the accumulator array (Im S_{m,k} follows for m > 0)
 __host__ __device__ constexpr int s_index(int L, int m, int k) {
     return m == 0 ? k : (L + 1) + (m - 1) * (2 * L + 2 - m) + 2 * k;
-}
-
-// The neighbour/shell rule in IEEE FP32 round-to-nearest, never fused; (sx,sy,sz)
-// is the periodic image shift of the cell row (0 or +-L), applied as d - s exactly
-// as the rule's d - L / d + L.
-__device__ __forceinline__ int shell_of(const float4 pj, const float4 pi, float sx, float sy,
-                                        float sz, const float* e2, int nr) {
-    float dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
-    float dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
-    float dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
-    float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    if (!(r2 > 0.f) || !(r2 >= e2[0]) || !(r2 < e2[nr])) return -1;
-    int b = 0;
-#pragma unroll
-    for (int step = 8; step >= 1; step >>= 1)
-        if (b + step < nr && r2 >= e2[b + step]) b += step;
-    return b;
 }
 
 template <int L>
@@ -148,10 +132,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     for (int it = 0; it < (1 << 21); ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
-}
-
-__device__ __forceinline__ float shift_of(int code, float L) {
-    return code == 1 ? L : (code == 2 ? -L : 0.f);
 }
 
 // The neighbour rows of one cell as segments of the cell-sorted point array:
