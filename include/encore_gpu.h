@@ -143,8 +143,28 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);
  * [0] cell list, [1] pair kernel, [2] contraction, [3] FP64 reduction. */
 npcf_status npcf_get_timings(npcf_ctx* ctx, float* ms4);
 
+/* Exact per-shell pair counts of one catalog, computed without allocating any device
+ * memory. The paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc: code running while a CUDA graph is captured, processes whose device memory
+ * belongs to another allocator, plug-ins that must not grow their memory footprint.
+ *   d_pos    device float32 [n][3] positions, caller-owned; in [0, box) when periodic
+ *   n        0 <= n <= 262144 (larger catalogs are rejected with NPCF_EINVAL)
+ *   nr, edges, box   as in npcf_create (host edges[nr+1]; box > 3 edges[nr] or 0)
+ *   d_counts device uint64 [nr], caller-owned; overwritten with the counts of this call
+ *   stream   cudaStream_t the work is enqueued on
+ * Counts are the same as npcf_accumulate + npcf_pair_counts give for the catalog (the
+ * same FP32 neighbour rule). All scratch lives in one fixed device array of about 13 MiB
+ * that every GPU loading the library keeps until the process exits. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make it before
+ * any stream capture. Calls share the array: each clears what must start at zero, and
+ * calls that overlap on the GPU race. With box == 0 the call reads the bounding box back
+ * to the host (one stream synchronisation); with box > 0 it is fully asynchronous.
+ * Errors are reported through npcf_last_error(NULL). */
+npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, int nr, const double* edges,
+                                     double box, uint64_t* d_counts, void* stream);
+
 /* Message of the last failed call on ctx; with ctx == NULL, of the last failed
- * npcf_create on this thread. */
+ * npcf_create or npcf_pair_counts_noalloc on this thread. */
 const char* npcf_last_error(const npcf_ctx* ctx);
 void npcf_destroy(npcf_ctx* ctx);
 

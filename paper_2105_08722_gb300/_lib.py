@@ -34,6 +34,7 @@ SIGNATURES = {
     "npcf_debug_alm": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "npcf_set_tuning": (_i, [_vp, _i, _i]),
     "npcf_get_timings": (_i, [_vp, _vp]),
+    "npcf_pair_counts_noalloc": (_i, [_vp, _i64, _i, _vp, _d, _vp, _vp]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
 }
@@ -55,6 +56,17 @@ def load(path: str = LIB_PATH):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def pair_counts_noalloc(pos, edges, box: float, out, stream=None):
+    """Exact per-shell pair counts into the CUDA uint64 tensor ``out`` [nr] without any
+    device allocation by the library (npcf_pair_counts_noalloc)."""
+    lib = load()
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    st = lib.npcf_pair_counts_noalloc(_ptr(pos), int(pos.shape[0]), len(e) - 1, e.ctypes.data, float(box),
+                                      _ptr(out), _stream_handle(stream))
+    if st != NPCF_OK:
+        raise NPCFError(st, lib.npcf_last_error(None).decode())
 
 
 class NPCFError(RuntimeError):
