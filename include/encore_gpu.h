@@ -132,11 +132,12 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
 
 /* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8; the cell
  * side of the neighbour grid is about r_max / key0), key 2 = contraction primaries
- * per chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per warp
- * (even, 64..8192 entries; larger lists mean fewer passes for dense primaries, smaller
- * ones leave more shared memory for staging neighbour cells), key 4 = cap on the
+ * per chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per block
+ * (multiple of 256 in 512..16384 entries; larger lists mean fewer slices for dense
+ * primaries, smaller ones leave more shared memory for staging), key 4 = cap on the
  * neighbour points staged in shared memory per cell (0 = as many as fit; cells with
- * more neighbours read them from global memory instead). */
+ * more neighbours read them from global memory instead), key 5 = x-adjacent cells
+ * per pair-kernel work unit (1..4). */
 npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);
 
 /* Device time in ms of the stages of the last accumulate call:

@@ -65,8 +65,9 @@ struct npcf_ctx {
     int nlm = 0;
 
     // cell-list tuning and geometry
-    int cells_per_rmax = 4;
-    int pair_cap = 4096;
+    int cells_per_rmax = 5;
+    int cell_run = 2;          // x-adjacent cells per pair-kernel work unit
+    int pair_cap = 8192;
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
@@ -324,15 +325,33 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     pa.cap = ctx->pair_cap;
     pa.err = ctx->errflag.p;
     {
+        // a run of cells must not make the periodic neighbour span wrap onto itself
+        int reach = 0;
+        for (size_t i = 0; i < ctx->rows_host.size(); i += 4)
+            reach = std::max({reach, std::abs(ctx->rows_host[i]), std::abs(ctx->rows_host[i + 1]),
+                              std::abs(ctx->rows_host[i + 2]), std::abs(ctx->rows_host[i + 3])});
+        pa.run = std::max(1, ctx->cell_run);
+        if (g.periodic) pa.run = std::max(1, std::min(pa.run, g.gx - 2 * reach));
+        // linear shell edges allow a direct shell estimate (corrected exactly on the device)
+        const double r0 = ctx->edges[0], w = (ctx->edges[ctx->nr] - r0) / ctx->nr;
+        bool lin = w > 0;
+        for (int i = 0; i <= ctx->nr && lin; ++i)
+            lin = std::fabs(ctx->edges[i] - (r0 + i * w)) <= 1e-9 * ctx->edges[ctx->nr];
+        pa.linear = lin ? 1 : 0;
+        pa.lin_r0 = (float)r0;
+        pa.lin_inv_w = lin ? (float)(1.0 / w) : 0.f;
+    }
+    {
         int dev = 0, optin = 0;
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         pa.cand_cap = 0;
-        const long long room = (long long)optin - kPairStaticSmem - (long long)pair_dynamic_smem(pa);
-        if (room < 16 * 256)
+        // each staged point takes 16 B plus a 1-byte periodic shift code
+        const long long room = (long long)optin - kPairStaticSmem - (long long)pair_dynamic_smem(pa) - 256;
+        if (room < 17 * 256)
             return fail(ctx, NPCF_EINVAL, "pair kernel: neighbour-list capacity %d leaves no room for "
                         "staging (shared memory limit %d B)", pa.cap, optin);
-        pa.cand_cap = (int)std::min<long long>(room / 16, 65535);
+        pa.cand_cap = (int)std::min<long long>(room / 17, 65535);
         if (ctx->stage_limit > 0) pa.cand_cap = std::min(pa.cand_cap, ctx->stage_limit);
     }
     launch_pair(pa, ctx->nsm, s);   // persistent: one block per SM, cells taken dynamically
@@ -599,13 +618,17 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             ctx->chunk_target = value;
             return NPCF_OK;
         case 3:
-            if (value < 64 || value > 8192 || (value & 1))
-                return fail(ctx, NPCF_EINVAL, "pair list capacity must be even and in [64, 8192]");
+            if (value < 512 || value > 16384 || (value % 256))
+                return fail(ctx, NPCF_EINVAL, "pair list capacity must be a multiple of 256 in [512, 16384]");
             ctx->pair_cap = value;
             return NPCF_OK;
         case 4:
             if (value < 0) return fail(ctx, NPCF_EINVAL, "staging limit must be >= 0");
             ctx->stage_limit = value;
+            return NPCF_OK;
+        case 5:
+            if (value < 1 || value > 4) return fail(ctx, NPCF_EINVAL, "cells per work unit in [1, 4]");
+            ctx->cell_run = value;
             return NPCF_OK;
         default:
             return fail(ctx, NPCF_EINVAL, "unknown tuning key %d", key);

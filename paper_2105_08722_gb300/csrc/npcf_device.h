@@ -68,6 +68,9 @@ struct PairArgs {
     int* err;                  // error bits (2: a bounded wait gave up)
     int cap;                   // 16-bit entries per warp neighbour list
     int cand_cap;              // points the staging buffer holds
+    int run;                   // cells per work unit (x-adjacent)
+    int linear;                // edges are linear in r: shell estimated from sqrt(r2)
+    float lin_r0, lin_inv_w;   // first edge and 1 / shell width of linear edges
 };
 
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s);

@@ -134,10 +134,42 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// The neighbour rows of one cell as segments of the cell-sorted point array:
-// (global start, count, offset in the staging buffer, shift code 2 bits per axis).
-// Computed by one warp; returns (number of segments, total points) via shared memory.
-__device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int cy, int cz,
+// Shell of an accepted pair. For linear bins the shell is estimated from sqrt(r2) and then
+// corrected against the exact squared edges, so the decision stays the rule's
+// e2[b] <= r2 < e2[b+1]; other edges use a binary search.
+__device__ __forceinline__ int shell_index(float r2, const float* e2, int nr, int linear, float r0,
+                                           float inv_w) {
+    int b;
+    if (linear) {
+        b = (int)((r2 * rsqrtf(r2) - r0) * inv_w);
+        b = b < 0 ? 0 : (b >= nr ? nr - 1 : b);
+        while (b > 0 && r2 < e2[b]) --b;
+        while (b + 1 < nr && r2 >= e2[b + 1]) ++b;
+    } else {
+        b = 0;
+#pragma unroll
+        for (int step = 8; step >= 1; step >>= 1)
+            if (b + step < nr && r2 >= e2[b + step]) b += step;
+    }
+    return b;
+}
+
+// The exact FP32 neighbour rule (same operations as shell_of in npcf_rules.cuh) followed
+// by the shell lookup above; -1 for a rejected pair.
+__device__ __forceinline__ int pair_shell(const float4 pj, const float4 pi, float sx, float sy, float sz,
+                                          const float* e2, int nr, int linear, float r0, float inv_w) {
+    const float dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
+    const float dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
+    const float dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    if (!(r2 > 0.f) || !(r2 >= e2[0]) || !(r2 < e2[nr])) return -1;
+    return shell_index(r2, e2, nr, linear, r0, inv_w);
+}
+
+// The neighbour rows of a run of cells (x-adjacent, same y and z) as segments of the
+// cell-sorted point array: (global start, count, offset in the staging buffer, shift code
+// 2 bits per axis). Computed by one warp; the totals go to shared memory.
+__device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int cy, int cz, int run,
                                int4* segs, int* out_nseg, int* out_total, int lane) {
     const GridInfo& g = a.g;
     int nseg = 0, total = 0;
@@ -156,7 +188,7 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int 
             }
             if (ok) {
                 const int base = (zz * g.gy + yy) * g.gx;
-                int x0 = cx + rw.z, x1 = cx + rw.w;
+                int x0 = cx + rw.z, x1 = cx + run - 1 + rw.w;
                 if (g.periodic) {
                     if (x0 < 0) {
                         beg[ns] = (int)a.cell_start[base + x0 + g.gx];
@@ -201,35 +233,266 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int 
     if (lane == 0) { *out_nseg = nseg; *out_total = total; }
 }
 
-// Per-warp state for the primary loop (shared memory).
-struct WarpState {
-    uint32_t hist[kMaxNr];
-    uint32_t cur[kMaxNr];
-    int rlo[kMaxNr], rhi[kMaxNr], gofs[kMaxNr];
-    int next[4];
+constexpr int kW = 8;             // warps per block of the pair kernel
+constexpr int kShiftCodes = 64;   // 2 bits per axis
+
+// Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
+struct PairLayout {
+    size_t cand, scode, segs, rows, ulist, slist, ushell, part, total;
 };
 
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int cap, int nr, int nc) {
+    PairLayout l;
+    l.cand = 0;
+    l.scode = align16(l.cand + (size_t)cand_cap * 16);
+    l.segs = align16(l.scode + (size_t)cand_cap);
+    l.rows = align16(l.segs + (size_t)2 * nrows * 16);
+    l.ulist = align16(l.rows + (size_t)nrows * 16);
+    l.slist = align16(l.ulist + (size_t)cap * 2);
+    l.ushell = align16(l.slist + (size_t)cap * 2);
+    l.part = align16(l.ushell + (size_t)cap);
+    l.total = align16(l.part + (size_t)kW * nr * nc * 4);
+    return l;
+}
+
 template <int L>
-__global__ void __launch_bounds__(256, 1) k_pair(const PairArgs a) {
+struct PairShared {
+    float4 shift[kShiftCodes];     // (sx, sy, sz) of each periodic shift code
+    float kmat[nlmc(L) * (L + 1)];
+    float e2[kMaxNr + 1];
+    uint32_t hist[kW][kMaxNr];     // per-warp shell counts of the current slice
+    uint32_t base[kW][kMaxNr];     // where each warp scatters each shell
+    uint32_t off[kMaxNr + 1];      // shell offsets of the sorted slice
+    uint32_t tot[kMaxNr];          // shell totals of the current primary
+    int unit[4];
+};
+
+// One primary, processed by the whole block. Neighbours are split evenly over the warps
+// (flat staged range, or segments round-robin for the global-memory path); each warp
+// appends accepted neighbours (index, shell) to its own sub-list; a ballot counting sort
+// orders the slice by shell; the sorted slice is cut into kW equal chunks whose per-shell
+// sums go to per-warp partials; the partials give a_lm at the end. Sub-lists that fill up
+// end the slice early, and the scan resumes where it stopped.
+template <int L, bool STAGED>
+__device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
+                                            const uint8_t* scode, const int4* segs, int nseg, int total,
+                                            uint16_t* ulist, uint16_t* slist, uint8_t* ushell, float* part,
+                                            int p, int warp, int lane, const int* slot_org) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
     using R = TR<NC>;
-    constexpr int kW = 8;  // warps per block
-    extern __shared__ __align__(128) unsigned char dsm[];
-    float4* cand = reinterpret_cast<float4*>(dsm);                       // staged neighbour points
-    int4* segs = reinterpret_cast<int4*>(cand + a.cand_cap);             // segment table
-    int4* rows = segs + 2 * a.nrows;                                      // neighbour rows
-    uint16_t* lists = reinterpret_cast<uint16_t*>(rows + a.nrows);       // per-warp neighbour lists
-    __shared__ WarpState ws[kW];
-    __shared__ float red[kW][NC];
-    __shared__ float kmat[NLM * (L + 1)];
-    __shared__ float e2[kMaxNr + 1];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int unit[4];   // cell, nseg, total, overflow
+    const int nr = a.nr;
+    const int tid = threadIdx.x;
+    const GridInfo& g = a.g;
+    float2* out = a.alm + (size_t)p * nr * NLM;
+    const float u = a.wp[p];
+    if (u == 0.f) {  // primary not evaluated
+        for (int i = tid; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
+        if (tid < nr) a.cnt[(size_t)p * nr + tid] = 0u;
+        return;
+    }
+    const float4 pi = a.pts[p];
+    for (int i = tid; i < kW * nr * NC; i += kW * 32) part[i] = 0.f;
+    if (tid < kMaxNr) sh.tot[tid] = 0u;
 
+    // this warp's share of the neighbours and its sub-list
+    const int capw = STAGED ? a.cap / kW : a.cap / (2 * kW);
+    uint16_t* ul16 = ulist + (size_t)warp * (a.cap / kW);
+    uint32_t* ul32 = reinterpret_cast<uint32_t*>(ul16);
+    uint8_t* us = ushell + (size_t)warp * (a.cap / kW);
+    uint32_t* sl32 = reinterpret_cast<uint32_t*>(slist);
+    const int per = (total + kW - 1) / kW;
+    int cursor = STAGED ? min(total, warp * per) : 0;
+    const int kend = STAGED ? min(total, cursor + per) : 0;
+    int seg = warp, segpos = 0;   // global-memory path: segments warp, warp + kW, ...
+    const unsigned lt = (1u << lane) - 1u;
+    __syncthreads();   // partials zeroed before any warp adds to them
+
+    for (;;) {
+        // ---- scan: append accepted neighbours while the sub-list has room
+        int cw = 0;
+        if (STAGED) {
+            const int iters = min((kend - cursor + 31) / 32, capw / 32);
+#pragma unroll 2
+            for (int it = 0; it < iters; ++it) {
+                const int k = cursor + it * 32 + lane;
+                int b = -1;
+                if (k < kend) {
+                    const float4 sf = sh.shift[scode[k]];
+                    b = pair_shell(cand[k], pi, sf.x, sf.y, sf.z, sh.e2, nr, a.linear, a.lin_r0, a.lin_inv_w);
+                }
+                const unsigned m = __ballot_sync(kFull, b >= 0);
+                if (b >= 0) {
+                    const int pos = cw + __popc(m & lt);
+                    ul16[pos] = (uint16_t)k;
+                    us[pos] = (uint8_t)b;
+                }
+                cw += __popc(m);
+            }
+            cursor = min(kend, cursor + iters * 32);
+        } else {
+            while (seg < nseg && cw + 32 <= capw) {
+                const int4 sg = segs[seg];
+                const float4 sf = sh.shift[sg.w];
+                const int k = segpos + lane;
+                int b = -1;
+                if (k < sg.y)
+                    b = pair_shell(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.e2, nr, a.linear, a.lin_r0,
+                                   a.lin_inv_w);
+                const unsigned m = __ballot_sync(kFull, b >= 0);
+                if (b >= 0) {
+                    const int pos = cw + __popc(m & lt);
+                    ul32[pos] = (uint32_t)(sg.x + k);
+                    us[pos] = (uint8_t)b;
+                }
+                cw += __popc(m);
+                segpos += 32;
+                if (segpos >= sg.y) { seg += kW; segpos = 0; }
+            }
+        }
+        const bool done = STAGED ? (cursor >= kend) : (seg >= nseg);
+
+        // ---- shell histogram of this warp's sub-list (lane t counts shell t)
+        uint32_t h = 0u;
+        for (int k0 = 0; k0 < cw; k0 += 32) {
+            const int shk = (k0 + lane < cw) ? (int)us[k0 + lane] : -1;
+            for (int t = 0; t < nr; ++t) {
+                const unsigned m = __ballot_sync(kFull, shk == t);
+                if (lane == t) h += (uint32_t)__popc(m);
+            }
+        }
+        if (lane < kMaxNr) sh.hist[warp][lane] = h;
+        const int all_done = __syncthreads_and(done ? 1 : 0);
+
+        // ---- shell offsets of the slice and each warp's scatter bases
+        if (warp == 0) {
+            uint32_t tsum = 0u;
+            if (lane < nr)
+                for (int w = 0; w < kW; ++w) tsum += sh.hist[w][lane];
+            uint32_t incl = tsum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane < nr) {
+                uint32_t bw = incl - tsum;
+                sh.off[lane] = bw;
+                for (int w = 0; w < kW; ++w) { sh.base[w][lane] = bw; bw += sh.hist[w][lane]; }
+                sh.tot[lane] += tsum;
+            }
+            if (lane == nr - 1) sh.off[nr] = incl;
+        }
+        __syncthreads();
+
+        // ---- scatter the sub-list into shell order (stable within a warp)
+        {
+            uint32_t myb = lane < nr ? sh.base[warp][lane] : 0u;
+            for (int k0 = 0; k0 < cw; k0 += 32) {
+                const bool ok = k0 + lane < cw;
+                const int shk = ok ? (int)us[k0 + lane] : -1;
+                const uint32_t idx = ok ? (STAGED ? (uint32_t)ul16[k0 + lane] : ul32[k0 + lane]) : 0u;
+                for (int t = 0; t < nr; ++t) {
+                    const unsigned m = __ballot_sync(kFull, shk == t);
+                    const uint32_t bt = __shfl_sync(kFull, myb, t);
+                    if (shk == t) {
+                        const uint32_t pos = bt + (uint32_t)__popc(m & lt);
+                        if (STAGED) slist[pos] = (uint16_t)idx;
+                        else sl32[pos] = idx;
+                    }
+                    if (lane == t) myb += (uint32_t)__popc(m);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- accumulate an equal chunk of the sorted slice, per shell
+        {
+            const int ns = (int)sh.off[nr];
+            const int chunk = (ns + kW - 1) / kW;
+            const int c0 = min(ns, warp * chunk), c1 = min(ns, c0 + chunk);
+            for (int t = 0; t < nr; ++t) {
+                const int lo = max(c0, (int)sh.off[t]), hi = min(c1, (int)sh.off[t + 1]);
+                if (lo >= hi) continue;
+                float acc[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) acc[i] = 0.f;
+                for (int k = lo + lane; k < hi; k += 32) {
+                    const float4 pj = STAGED ? cand[slist[k]] : a.pts[sl32[k]];
+                    float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    if (g.periodic) {
+                        dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
+                        dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
+                        dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
+                    }
+                    const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, pj.w);
+                }
+                R::run(acc, lane);
+                float* pw = part + ((size_t)warp * nr + t) * NC;
+#pragma unroll
+                for (int i = 0; i < R::F; ++i)
+                    if (slot_org[i] >= 0) pw[slot_org[i]] += acc[i];
+            }
+        }
+        __syncthreads();   // lists are rewritten by the next slice
+        if (all_done) break;
+    }
+
+    // ---- combine the per-warp partials and convert to a_lm
+    for (int i = tid; i < nr * NLM; i += kW * 32) {
+        const int t = i / NLM, q = i % NLM;
+        int l = 0, m = q;
+        while (m > l) { m -= l + 1; ++l; }
+        float re = 0.f, im = 0.f;
+        for (int k = l - m; k >= 0; k -= 2) {
+            const int si = s_index(L, m, k);
+            float sr = 0.f, sim = 0.f;
+            for (int w = 0; w < kW; ++w) {
+                const float* pw = part + ((size_t)w * nr + t) * NC;
+                sr += pw[si];
+                if (m > 0) sim += pw[si + 1];
+            }
+            const float kk = sh.kmat[q * (L + 1) + k];
+            re = fmaf(kk, sr, re);
+            im = fmaf(kk, sim, im);
+        }
+        out[i] = make_float2(re, im);
+    }
+    if (tid < nr) {
+        const uint32_t c = sh.tot[tid];
+        a.cnt[(size_t)p * nr + tid] = c;
+        if (c) atomicAdd(&a.counts[tid], (unsigned long long)c);
+    }
+    __syncthreads();   // partials and totals are reset by the next primary
+}
+
+template <int L>
+__global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
+    using R = TR<ncomp(L)>;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const PairLayout lay = pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(L));
+    float4* cand = reinterpret_cast<float4*>(dsm + lay.cand);
+    uint8_t* scode = dsm + lay.scode;
+    int4* segs = reinterpret_cast<int4*>(dsm + lay.segs);
+    int4* rows = reinterpret_cast<int4*>(dsm + lay.rows);
+    uint16_t* ulist = reinterpret_cast<uint16_t*>(dsm + lay.ulist);
+    uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist);
+    uint8_t* ushell = dsm + lay.ushell;
+    float* part = reinterpret_cast<float*>(dsm + lay.part);
+    __shared__ PairShared<L> sh;
+    __shared__ __align__(8) uint64_t bar;
+
+    const GridInfo& g = a.g;
     for (int i = threadIdx.x; i < a.nrows; i += blockDim.x) rows[i] = a.rows[i];
-    for (int i = threadIdx.x; i < NLM * (L + 1); i += blockDim.x) kmat[i] = a.kmat[i];
-    if (threadIdx.x <= a.nr) e2[threadIdx.x] = a.e2[threadIdx.x];
+    for (int i = threadIdx.x; i < nlmc(L) * (L + 1); i += blockDim.x) sh.kmat[i] = a.kmat[i];
+    if (threadIdx.x <= a.nr) sh.e2[threadIdx.x] = a.e2[threadIdx.x];
+    if (threadIdx.x < kShiftCodes) {
+        const int c = threadIdx.x;
+        sh.shift[c] = make_float4(shift_of(c & 3, g.L), shift_of((c >> 2) & 3, g.L),
+                                  shift_of((c >> 4) & 3, g.L), 0.f);
+    }
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -237,31 +500,30 @@ __global__ void __launch_bounds__(256, 1) k_pair(const PairArgs a) {
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nr = a.nr;
-    const GridInfo& g = a.g;
-    WarpState& W = ws[warp];
-    uint16_t* list16 = lists + (size_t)warp * a.cap;
-    uint32_t* list32 = reinterpret_cast<uint32_t*>(list16);
-
     int slot_org[R::F];
 #pragma unroll
     for (int i = 0; i < R::F; ++i) slot_org[i] = R::origin(i, lane);
     uint32_t parity = 0;
+    const int upr = (g.gx + a.run - 1) / a.run;   // units per row of cells
+    const int nunits = upr * g.gy * g.gz;
 
     for (;;) {
-        if (threadIdx.x == 0) unit[0] = atomicAdd(a.work, 1);
+        if (threadIdx.x == 0) sh.unit[0] = atomicAdd(a.work, 1);
         __syncthreads();
-        const int cell = unit[0];
-        if (cell >= g.ncell) break;
-        const int pbeg = (int)a.cell_start[cell], pend = (int)a.cell_start[cell + 1];
+        const int u = sh.unit[0];
+        if (u >= nunits) break;
+        const int row = u / upr, cx = (u % upr) * a.run;
+        const int run = min(a.run, g.gx - cx);
+        const int cy = row % g.gy, cz = row / g.gy;
+        const int c0 = (cz * g.gy + cy) * g.gx + cx;
+        const int pbeg = (int)a.cell_start[c0], pend = (int)a.cell_start[c0 + run];
         if (pbeg == pend) {
             __syncthreads();
             continue;
         }
-        const int cx = cell % g.gx, cy = (cell / g.gx) % g.gy, cz = cell / (g.gx * g.gy);
-        if (warp == 0) build_segments(a, rows, cx, cy, cz, segs, &unit[1], &unit[2], lane);
+        if (warp == 0) build_segments(a, rows, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], lane);
         __syncthreads();
-        const int nseg = unit[1], total = unit[2];
+        const int nseg = sh.unit[1], total = sh.unit[2];
         const bool staged = total <= a.cand_cap;
         if (staged && total > 0) {
             // stage the neighbour points with bulk asynchronous copies (one mbarrier)
@@ -280,6 +542,11 @@ __global__ void __launch_bounds__(256, 1) k_pair(const PairArgs a) {
                         : "memory");
                 }
             }
+            // periodic shift code of every staged point
+            for (int s = warp; s < nseg; s += kW) {
+                const int4 sg = segs[s];
+                for (int k = lane; k < sg.y; k += 32) scode[sg.z + k] = (uint8_t)sg.w;
+            }
             const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
             // the whole block leaves together if any thread's wait gave up
             if (__syncthreads_or(ok ? 0 : 1)) {
@@ -289,148 +556,15 @@ __global__ void __launch_bounds__(256, 1) k_pair(const PairArgs a) {
             }
             parity ^= 1u;
         }
-        const int cap = staged ? a.cap : a.cap / 2;   // 16-bit staged or 32-bit global indices
-
-        for (int p = pbeg + warp; p < pend; p += kW) {
-            float2* out = a.alm + (size_t)p * nr * NLM;
-            const float u = a.wp[p];
-            if (u == 0.f) {  // primary not evaluated
-                for (int i = lane; i < nr * NLM; i += 32) out[i] = make_float2(0.f, 0.f);
-                if (lane < nr) a.cnt[(size_t)p * nr + lane] = 0u;
-                continue;
-            }
-            const float4 pi = a.pts[p];
-
-            // ---- pass 0: neighbour counts per shell
-            if (lane < kMaxNr) W.hist[lane] = 0u;
-            __syncwarp();
-            for (int s = 0; s < nseg; ++s) {
-                const int4 sg = segs[s];
-                const float sx = shift_of(sg.w & 3, g.L), sy = shift_of((sg.w >> 2) & 3, g.L),
-                            sz = shift_of((sg.w >> 4) & 3, g.L);
-                for (int j = lane; j < sg.y; j += 32) {
-                    const float4 pj = staged ? cand[sg.z + j] : a.pts[sg.x + j];
-                    const int b = shell_of(pj, pi, sx, sy, sz, e2, nr);
-                    if (b >= 0) atomicAdd(&W.hist[b], 1u);
-                }
-            }
-            __syncwarp();
-            if (lane < nr) {
-                const uint32_t c = W.hist[lane];
-                a.cnt[(size_t)p * nr + lane] = c;
-                if (c) atomicAdd(&a.counts[lane], (unsigned long long)c);
-            }
-
-            float acc[NC];
-#pragma unroll
-            for (int i = 0; i < NC; ++i) acc[i] = 0.f;
-
-            int s_next = 0, r_next = 0;
-            while (s_next < nr) {
-                // ---- slice of the shell-ordered list: shells [g_first, g_last]
-                if (lane == 0) {
-                    for (int q = 0; q < kMaxNr; ++q) { W.rlo[q] = 0; W.rhi[q] = -1; W.cur[q] = 0u; }
-                    int used = 0, t = s_next, r = r_next, last = s_next;
-                    while (t < nr) {
-                        const int avail = (int)W.hist[t] - r;
-                        const int take = avail < cap - used ? avail : cap - used;
-                        W.rlo[t] = r;
-                        W.rhi[t] = r + take;
-                        W.gofs[t] = used;
-                        used += take;
-                        last = t;
-                        if (take < avail) { r += take; break; }  // shell t continues in the next slice
-                        ++t;
-                        r = 0;
-                        if (used >= cap) break;
-                    }
-                    W.next[0] = used;
-                    W.next[1] = last;
-                    W.next[2] = t;
-                    W.next[3] = r;
-                }
-                __syncwarp();
-                const int g_first = s_next;
-                const int used = W.next[0];
-                const int g_last = W.next[1];
-                s_next = W.next[2];
-                r_next = W.next[3];
-
-                // ---- pass 1: write the slice's neighbour indices in shell order
-                if (used > 0) {
-                    for (int s = 0; s < nseg; ++s) {
-                        const int4 sg = segs[s];
-                        const float sx = shift_of(sg.w & 3, g.L), sy = shift_of((sg.w >> 2) & 3, g.L),
-                                    sz = shift_of((sg.w >> 4) & 3, g.L);
-                        for (int j0 = 0; j0 < sg.y; j0 += 32) {
-                            const int j = j0 + lane;
-                            int key = -1;
-                            if (j < sg.y) {
-                                const float4 pj = staged ? cand[sg.z + j] : a.pts[sg.x + j];
-                                const int b = shell_of(pj, pi, sx, sy, sz, e2, nr);
-                                if (b >= g_first && b <= g_last) key = b;
-                            }
-                            if (__ballot_sync(kFull, key >= 0) == 0u) continue;
-                            const unsigned m = __match_any_sync(kFull, key);
-                            const int leader = __ffs(m) - 1;
-                            uint32_t b0 = 0u;
-                            if (key >= 0 && lane == leader) b0 = atomicAdd(&W.cur[key], (uint32_t)__popc(m));
-                            b0 = __shfl_sync(kFull, b0, leader);
-                            if (key >= 0) {
-                                const int rank = (int)b0 + __popc(m & ((1u << lane) - 1u));
-                                if (rank >= W.rlo[key] && rank < W.rhi[key]) {
-                                    const int slot = W.gofs[key] + rank - W.rlo[key];
-                                    if (staged) list16[slot] = (uint16_t)(sg.z + j);
-                                    else list32[slot] = (uint32_t)(sg.x + j);
-                                }
-                            }
-                        }
-                    }
-                }
-                __syncwarp();
-
-                // ---- accumulate the slice, finish the shells it completes
-                for (int t = g_first; t <= g_last; ++t) {
-                    const int k0 = W.gofs[t];
-                    const int kn = W.rhi[t] - W.rlo[t];
-                    for (int k = lane; k < kn; k += 32) {
-                        const float4 pj = staged ? cand[list16[k0 + k]] : a.pts[list32[k0 + k]];
-                        float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                        if (g.periodic) {
-                            dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
-                            dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
-                            dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
-                        }
-                        const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                        harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, pj.w);
-                    }
-                    if (W.rhi[t] == (int)W.hist[t]) {
-                        R::run(acc, lane);
-#pragma unroll
-                        for (int i = 0; i < R::F; ++i)
-                            if (slot_org[i] >= 0) red[warp][slot_org[i]] = acc[i];
-                        __syncwarp();
-                        for (int q = lane; q < NLM; q += 32) {
-                            int l = 0, m = q;
-                            while (m > l) { m -= l + 1; ++l; }
-                            float re = 0.f, im = 0.f;
-                            for (int k = l - m; k >= 0; k -= 2) {
-                                const float kk = kmat[q * (L + 1) + k];
-                                const int si = s_index(L, m, k);
-                                re = fmaf(kk, red[warp][si], re);
-                                if (m > 0) im = fmaf(kk, red[warp][si + 1], im);
-                            }
-                            out[t * NLM + q] = make_float2(re, im);
-                        }
-#pragma unroll
-                        for (int i = 0; i < NC; ++i) acc[i] = 0.f;
-                        __syncwarp();
-                    }
-                }
-                __syncwarp();
-            }
+        for (int p = pbeg; p < pend; ++p) {
+            if (staged)
+                one_primary<L, true>(a, sh, cand, scode, segs, nseg, total, ulist, slist, ushell, part, p,
+                                     warp, lane, slot_org);
+            else
+                one_primary<L, false>(a, sh, cand, scode, segs, nseg, total, ulist, slist, ushell, part, p,
+                                      warp, lane, slot_org);
         }
-        __syncthreads();   // every warp is done with the staged points of this cell
+        __syncthreads();   // every warp is done with the staged points of this unit
     }
 }
 
@@ -438,14 +572,13 @@ template <int L>
 void launch_L(const PairArgs& a, int nblocks, cudaStream_t s) {
     const size_t smem = pair_dynamic_smem(a);
     cudaFuncSetAttribute(k_pair<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pair<L><<<nblocks, 8 * 32, smem, s>>>(a);
+    k_pair<L><<<nblocks, kW * 32, smem, s>>>(a);
 }
 
 }  // namespace
 
 size_t pair_dynamic_smem(const PairArgs& a) {
-    return (size_t)a.cand_cap * sizeof(float4) + (size_t)3 * a.nrows * sizeof(int4) +
-           (size_t)8 * a.cap * sizeof(uint16_t);
+    return pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(a.lmax)).total;
 }
 
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s) {

@@ -166,9 +166,9 @@ def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
 
 @pytest.mark.parametrize("tuning", [
     {},                 # staged neighbour cells, one list slice per primary
-    {3: 64},            # staged, several list slices per primary
+    {3: 512},           # staged, several list slices per primary
     {4: 256},           # neighbour cells too large to stage: global-memory path
-    {3: 64, 4: 256},    # global-memory path with several list slices
+    {3: 512, 4: 256},   # global-memory path with several list slices
 ])
 def test_dense_primaries_staged_and_global_paths(torch_dev, tuning):
     pos, w = _catalog(3000, 60.0, 61)
