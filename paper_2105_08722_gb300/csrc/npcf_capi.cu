@@ -67,7 +67,7 @@ struct npcf_ctx {
     // cell-list tuning and geometry
     int cells_per_rmax = 5;
     int cell_run = 2;          // x-adjacent cells per pair-kernel work unit
-    int pair_cap = 8192;
+    int pair_cap = 4096;       // per group of the pair kernel
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};

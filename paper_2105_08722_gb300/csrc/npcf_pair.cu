@@ -40,7 +40,9 @@ __host__ __device__ constexpr int s_index(int L, int m, int k) {
 template <int L>
 __device__ __forceinline__ void harm_accumulate(float (&acc)[ncomp(L)], float x, float y, float z,
                                                 float w) {
-    float c[L + 1], s[L + 1], wz[L + 1];
+    // c_m + i s_m = (x + i y)^m ; wt_k = w T_k(z) with T_0 = 1, T_1 = z,
+    // T_{k+1} = 2 z T_k - T_{k-1} (the weight rides along the recurrence)
+    float c[L + 1], s[L + 1], wt[L + 1];
     c[0] = 1.f;
     s[0] = 0.f;
 #pragma unroll
@@ -48,24 +50,19 @@ __device__ __forceinline__ void harm_accumulate(float (&acc)[ncomp(L)], float x,
         c[m] = fmaf(c[m - 1], x, -s[m - 1] * y);
         s[m] = fmaf(s[m - 1], x, c[m - 1] * y);
     }
-    // w T_k(z): T_0 = 1, T_1 = z, T_{k+1} = 2 z T_k - T_{k-1}
-    float t[L + 1];
-    t[0] = 1.f;
-    if (L >= 1) t[1] = z;
+    wt[0] = w;
+    if (L >= 1) wt[1] = w * z;
     const float z2 = z + z;
 #pragma unroll
-    for (int k = 2; k <= L; ++k) t[k] = fmaf(z2, t[k - 1], -t[k - 2]);
-    wz[0] = w;
+    for (int k = 2; k <= L; ++k) wt[k] = fmaf(z2, wt[k - 1], -wt[k - 2]);
 #pragma unroll
-    for (int k = 1; k <= L; ++k) wz[k] = w * t[k];
-#pragma unroll
-    for (int k = 0; k <= L; ++k) acc[k] += wz[k];
+    for (int k = 0; k <= L; ++k) acc[k] += wt[k];
 #pragma unroll
     for (int m = 1; m <= L; ++m) {
 #pragma unroll
         for (int k = 0; k + m <= L; ++k) {
-            acc[s_index(L, m, k)] = fmaf(c[m], wz[k], acc[s_index(L, m, k)]);
-            acc[s_index(L, m, k) + 1] = fmaf(s[m], wz[k], acc[s_index(L, m, k) + 1]);
+            acc[s_index(L, m, k)] = fmaf(c[m], wt[k], acc[s_index(L, m, k)]);
+            acc[s_index(L, m, k) + 1] = fmaf(s[m], wt[k], acc[s_index(L, m, k) + 1]);
         }
     }
 }
@@ -233,10 +230,12 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int 
     if (lane == 0) { *out_nseg = nseg; *out_total = total; }
 }
 
-constexpr int kW = 8;             // warps per block of the pair kernel
+constexpr int kW = 8;             // warps per group; a group works on one primary
+constexpr int kG = 2;             // groups per block
 constexpr int kShiftCodes = 64;   // 2 bits per axis
 
 // Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
+// cap is the neighbour-list capacity of one group in 16-bit entries.
 struct PairLayout {
     size_t cand, scode, segs, rows, ulist, slist, ushell, part, total;
 };
@@ -250,52 +249,64 @@ __host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int c
     l.segs = align16(l.scode + (size_t)cand_cap);
     l.rows = align16(l.segs + (size_t)2 * nrows * 16);
     l.ulist = align16(l.rows + (size_t)nrows * 16);
-    l.slist = align16(l.ulist + (size_t)cap * 2);
-    l.ushell = align16(l.slist + (size_t)cap * 2);
-    l.part = align16(l.ushell + (size_t)cap);
-    l.total = align16(l.part + (size_t)kW * nr * nc * 4);
+    l.slist = align16(l.ulist + (size_t)kG * cap * 2);
+    l.ushell = align16(l.slist + (size_t)kG * cap * 2);
+    l.part = align16(l.ushell + (size_t)kG * cap);
+    l.total = align16(l.part + (size_t)kG * kW * nr * nc * 4);
     return l;
 }
+
+// Shared state of one group.
+struct GroupShared {
+    uint32_t hist[kW][kMaxNr];     // per-warp shell counts of the current slice
+    uint32_t base[kW][kMaxNr];     // where each warp scatters each shell
+    uint32_t off[kMaxNr + 1];      // shell offsets of the sorted slice
+    uint32_t tot[kMaxNr];          // shell totals of the current primary
+    int done[kW];
+};
 
 template <int L>
 struct PairShared {
     float4 shift[kShiftCodes];     // (sx, sy, sz) of each periodic shift code
     float kmat[nlmc(L) * (L + 1)];
     float e2[kMaxNr + 1];
-    uint32_t hist[kW][kMaxNr];     // per-warp shell counts of the current slice
-    uint32_t base[kW][kMaxNr];     // where each warp scatters each shell
-    uint32_t off[kMaxNr + 1];      // shell offsets of the sorted slice
-    uint32_t tot[kMaxNr];          // shell totals of the current primary
+    GroupShared grp[kG];
     int unit[4];
 };
 
-// One primary, processed by the whole block. Neighbours are split evenly over the warps
-// (flat staged range, or segments round-robin for the global-memory path); each warp
-// appends accepted neighbours (index, shell) to its own sub-list; a ballot counting sort
-// orders the slice by shell; the sorted slice is cut into kW equal chunks whose per-shell
-// sums go to per-warp partials; the partials give a_lm at the end. Sub-lists that fill up
-// end the slice early, and the scan resumes where it stopped.
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kW * 32) : "memory");
+}
+
+// One primary, processed by one group of kW warps. Neighbours are split evenly over the
+// warps (flat staged range, or segments round-robin for the global-memory path); each
+// warp appends accepted neighbours (index, shell) to its own sub-list; a counting sort
+// orders the slice by shell (ranks from __match_any_sync); the sorted slice is cut into
+// kW equal chunks whose per-shell sums go to per-warp partials; the partials give a_lm
+// at the end. Sub-lists that fill up end the slice early, and the scan resumes where it
+// stopped.
 template <int L, bool STAGED>
 __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
                                             const uint8_t* scode, const int4* segs, int nseg, int total,
                                             uint16_t* ulist, uint16_t* slist, uint8_t* ushell, float* part,
-                                            int p, int warp, int lane, const int* slot_org) {
+                                            int p, int grp, int warp, int lane, const int* slot_org) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
     using R = TR<NC>;
+    GroupShared& G = sh.grp[grp];
     const int nr = a.nr;
-    const int tid = threadIdx.x;
+    const int gt = warp * 32 + lane;   // thread index in the group
     const GridInfo& g = a.g;
     float2* out = a.alm + (size_t)p * nr * NLM;
     const float u = a.wp[p];
     if (u == 0.f) {  // primary not evaluated
-        for (int i = tid; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
-        if (tid < nr) a.cnt[(size_t)p * nr + tid] = 0u;
+        for (int i = gt; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
+        if (gt < nr) a.cnt[(size_t)p * nr + gt] = 0u;
         return;
     }
     const float4 pi = a.pts[p];
-    for (int i = tid; i < kW * nr * NC; i += kW * 32) part[i] = 0.f;
-    if (tid < kMaxNr) sh.tot[tid] = 0u;
+    for (int i = gt; i < kW * nr * NC; i += kW * 32) part[i] = 0.f;
+    if (gt < kMaxNr) G.tot[gt] = 0u;
 
     // this warp's share of the neighbours and its sub-list
     const int capw = STAGED ? a.cap / kW : a.cap / (2 * kW);
@@ -308,7 +319,7 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     const int kend = STAGED ? min(total, cursor + per) : 0;
     int seg = warp, segpos = 0;   // global-memory path: segments warp, warp + kW, ...
     const unsigned lt = (1u << lane) - 1u;
-    __syncthreads();   // partials zeroed before any warp adds to them
+    group_sync(grp);   // partials zeroed before any warp adds to them
 
     for (;;) {
         // ---- scan: append accepted neighbours while the sub-list has room
@@ -354,23 +365,26 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         }
         const bool done = STAGED ? (cursor >= kend) : (seg >= nseg);
 
-        // ---- shell histogram of this warp's sub-list (lane t counts shell t)
-        uint32_t h = 0u;
+        // ---- shell histogram of this warp's sub-list
+        if (lane < kMaxNr) G.hist[warp][lane] = 0u;
+        __syncwarp();
         for (int k0 = 0; k0 < cw; k0 += 32) {
-            const int shk = (k0 + lane < cw) ? (int)us[k0 + lane] : -1;
-            for (int t = 0; t < nr; ++t) {
-                const unsigned m = __ballot_sync(kFull, shk == t);
-                if (lane == t) h += (uint32_t)__popc(m);
-            }
+            const bool ok = k0 + lane < cw;
+            const int shk = ok ? (int)us[k0 + lane] : -1;
+            const unsigned m = __match_any_sync(kFull, shk);
+            if (ok && lane == __ffs(m) - 1) G.hist[warp][shk] += (uint32_t)__popc(m);
+            __syncwarp();
         }
-        if (lane < kMaxNr) sh.hist[warp][lane] = h;
-        const int all_done = __syncthreads_and(done ? 1 : 0);
+        if (lane == 0) G.done[warp] = done ? 1 : 0;
+        group_sync(grp);
+        int all_done = 1;
+        for (int w = 0; w < kW; ++w) all_done &= G.done[w];
 
         // ---- shell offsets of the slice and each warp's scatter bases
         if (warp == 0) {
             uint32_t tsum = 0u;
             if (lane < nr)
-                for (int w = 0; w < kW; ++w) tsum += sh.hist[w][lane];
+                for (int w = 0; w < kW; ++w) tsum += G.hist[w][lane];
             uint32_t incl = tsum;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(kFull, incl, o);
@@ -378,56 +392,67 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
             }
             if (lane < nr) {
                 uint32_t bw = incl - tsum;
-                sh.off[lane] = bw;
-                for (int w = 0; w < kW; ++w) { sh.base[w][lane] = bw; bw += sh.hist[w][lane]; }
-                sh.tot[lane] += tsum;
+                G.off[lane] = bw;
+                for (int w = 0; w < kW; ++w) { G.base[w][lane] = bw; bw += G.hist[w][lane]; }
+                G.tot[lane] += tsum;
             }
-            if (lane == nr - 1) sh.off[nr] = incl;
+            if (lane == nr - 1) G.off[nr] = incl;
         }
-        __syncthreads();
+        group_sync(grp);
 
         // ---- scatter the sub-list into shell order (stable within a warp)
-        {
-            uint32_t myb = lane < nr ? sh.base[warp][lane] : 0u;
-            for (int k0 = 0; k0 < cw; k0 += 32) {
-                const bool ok = k0 + lane < cw;
-                const int shk = ok ? (int)us[k0 + lane] : -1;
-                const uint32_t idx = ok ? (STAGED ? (uint32_t)ul16[k0 + lane] : ul32[k0 + lane]) : 0u;
-                for (int t = 0; t < nr; ++t) {
-                    const unsigned m = __ballot_sync(kFull, shk == t);
-                    const uint32_t bt = __shfl_sync(kFull, myb, t);
-                    if (shk == t) {
-                        const uint32_t pos = bt + (uint32_t)__popc(m & lt);
-                        if (STAGED) slist[pos] = (uint16_t)idx;
-                        else sl32[pos] = idx;
-                    }
-                    if (lane == t) myb += (uint32_t)__popc(m);
-                }
+        for (int k0 = 0; k0 < cw; k0 += 32) {
+            const bool ok = k0 + lane < cw;
+            const int shk = ok ? (int)us[k0 + lane] : -1;
+            const uint32_t idx = ok ? (STAGED ? (uint32_t)ul16[k0 + lane] : ul32[k0 + lane]) : 0u;
+            const unsigned m = __match_any_sync(kFull, shk);
+            const uint32_t b0 = ok ? G.base[warp][shk] : 0u;
+            __syncwarp();
+            if (ok) {
+                const uint32_t pos = b0 + (uint32_t)__popc(m & lt);
+                if (STAGED) slist[pos] = (uint16_t)idx;
+                else sl32[pos] = idx;
+                if (lane == __ffs(m) - 1) G.base[warp][shk] = b0 + (uint32_t)__popc(m);
             }
+            __syncwarp();
         }
-        __syncthreads();
+        group_sync(grp);
 
         // ---- accumulate an equal chunk of the sorted slice, per shell
         {
-            const int ns = (int)sh.off[nr];
+            const int ns = (int)G.off[nr];
             const int chunk = (ns + kW - 1) / kW;
             const int c0 = min(ns, warp * chunk), c1 = min(ns, c0 + chunk);
             for (int t = 0; t < nr; ++t) {
-                const int lo = max(c0, (int)sh.off[t]), hi = min(c1, (int)sh.off[t + 1]);
+                const int lo = max(c0, (int)G.off[t]), hi = min(c1, (int)G.off[t + 1]);
                 if (lo >= hi) continue;
                 float acc[NC];
 #pragma unroll
                 for (int i = 0; i < NC; ++i) acc[i] = 0.f;
                 for (int k = lo + lane; k < hi; k += 32) {
-                    const float4 pj = STAGED ? cand[slist[k]] : a.pts[sl32[k]];
-                    float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                    if (g.periodic) {
-                        dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
-                        dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
-                        dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
+                    float dx, dy, dz, wj;
+                    if (STAGED) {
+                        const int q = slist[k];
+                        const float4 pj = cand[q];
+                        const float4 sf = sh.shift[scode[q]];
+                        dx = (pj.x - pi.x) - sf.x;
+                        dy = (pj.y - pi.y) - sf.y;
+                        dz = (pj.z - pi.z) - sf.z;
+                        wj = pj.w;
+                    } else {
+                        const float4 pj = a.pts[sl32[k]];
+                        dx = pj.x - pi.x;
+                        dy = pj.y - pi.y;
+                        dz = pj.z - pi.z;
+                        wj = pj.w;
+                        if (g.periodic) {
+                            dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
+                            dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
+                            dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
+                        }
                     }
                     const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, pj.w);
+                    harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, wj);
                 }
                 R::run(acc, lane);
                 float* pw = part + ((size_t)warp * nr + t) * NC;
@@ -436,12 +461,12 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                     if (slot_org[i] >= 0) pw[slot_org[i]] += acc[i];
             }
         }
-        __syncthreads();   // lists are rewritten by the next slice
+        group_sync(grp);   // lists are rewritten by the next slice
         if (all_done) break;
     }
 
     // ---- combine the per-warp partials and convert to a_lm
-    for (int i = tid; i < nr * NLM; i += kW * 32) {
+    for (int i = gt; i < nr * NLM; i += kW * 32) {
         const int t = i / NLM, q = i % NLM;
         int l = 0, m = q;
         while (m > l) { m -= l + 1; ++l; }
@@ -460,16 +485,16 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         }
         out[i] = make_float2(re, im);
     }
-    if (tid < nr) {
-        const uint32_t c = sh.tot[tid];
-        a.cnt[(size_t)p * nr + tid] = c;
-        if (c) atomicAdd(&a.counts[tid], (unsigned long long)c);
+    if (gt < nr) {
+        const uint32_t c = G.tot[gt];
+        a.cnt[(size_t)p * nr + gt] = c;
+        if (c) atomicAdd(&a.counts[gt], (unsigned long long)c);
     }
-    __syncthreads();   // partials and totals are reset by the next primary
+    group_sync(grp);   // partials and totals are reset by the next primary
 }
 
 template <int L>
-__global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
+__global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     using R = TR<ncomp(L)>;
     extern __shared__ __align__(128) unsigned char dsm[];
     const PairLayout lay = pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(L));
@@ -477,10 +502,6 @@ __global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
     uint8_t* scode = dsm + lay.scode;
     int4* segs = reinterpret_cast<int4*>(dsm + lay.segs);
     int4* rows = reinterpret_cast<int4*>(dsm + lay.rows);
-    uint16_t* ulist = reinterpret_cast<uint16_t*>(dsm + lay.ulist);
-    uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist);
-    uint8_t* ushell = dsm + lay.ushell;
-    float* part = reinterpret_cast<float*>(dsm + lay.part);
     __shared__ PairShared<L> sh;
     __shared__ __align__(8) uint64_t bar;
 
@@ -499,7 +520,12 @@ __global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
     }
     __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wblk = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = wblk / kW, warp = wblk % kW;
+    uint16_t* ulist = reinterpret_cast<uint16_t*>(dsm + lay.ulist) + (size_t)grp * a.cap;
+    uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist) + (size_t)grp * a.cap;
+    uint8_t* ushell = dsm + lay.ushell + (size_t)grp * a.cap;
+    float* part = reinterpret_cast<float*>(dsm + lay.part) + (size_t)grp * kW * a.nr * ncomp(L);
     int slot_org[R::F];
 #pragma unroll
     for (int i = 0; i < R::F; ++i) slot_org[i] = R::origin(i, lane);
@@ -521,7 +547,7 @@ __global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
             __syncthreads();
             continue;
         }
-        if (warp == 0) build_segments(a, rows, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], lane);
+        if (wblk == 0) build_segments(a, rows, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], lane);
         __syncthreads();
         const int nseg = sh.unit[1], total = sh.unit[2];
         const bool staged = total <= a.cand_cap;
@@ -543,7 +569,7 @@ __global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
                 }
             }
             // periodic shift code of every staged point
-            for (int s = warp; s < nseg; s += kW) {
+            for (int s = wblk; s < nseg; s += kG * kW) {
                 const int4 sg = segs[s];
                 for (int k = lane; k < sg.y; k += 32) scode[sg.z + k] = (uint8_t)sg.w;
             }
@@ -556,15 +582,15 @@ __global__ void __launch_bounds__(kW * 32, 1) k_pair(const PairArgs a) {
             }
             parity ^= 1u;
         }
-        for (int p = pbeg; p < pend; ++p) {
+        for (int p = pbeg + grp; p < pend; p += kG) {
             if (staged)
                 one_primary<L, true>(a, sh, cand, scode, segs, nseg, total, ulist, slist, ushell, part, p,
-                                     warp, lane, slot_org);
+                                     grp, warp, lane, slot_org);
             else
                 one_primary<L, false>(a, sh, cand, scode, segs, nseg, total, ulist, slist, ushell, part, p,
-                                      warp, lane, slot_org);
+                                      grp, warp, lane, slot_org);
         }
-        __syncthreads();   // every warp is done with the staged points of this unit
+        __syncthreads();   // both groups are done with the staged points of this unit
     }
 }
 
@@ -572,7 +598,7 @@ template <int L>
 void launch_L(const PairArgs& a, int nblocks, cudaStream_t s) {
     const size_t smem = pair_dynamic_smem(a);
     cudaFuncSetAttribute(k_pair<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pair<L><<<nblocks, kW * 32, smem, s>>>(a);
+    k_pair<L><<<nblocks, kG * kW * 32, smem, s>>>(a);
 }
 
 }  // namespace
