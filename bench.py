@@ -228,6 +228,29 @@ def run_gpu(args):
     dominant = "pair" if st[1] >= st[2] else "contraction"
     achieved = pair_tflops if dominant == "pair" else con_tflops
     achieved = float(achieved)
+    other = None
+    if not args.no_other_precision:
+        # the other contraction arithmetic on the same workload (same timing protocol)
+        oprec = FP32 if prec == SPLIT_BF16 else SPLIT_BF16
+        oest = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, oprec)
+        for _ in range(args.warmup):
+            oest.accumulate(pos, w)
+        torch.cuda.synchronize()
+        oms, ost = [], []
+        for k in range(args.steps):
+            flush.zero_()
+            s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_ev.record(stream)
+            oest.accumulate(pos, w)
+            e_ev.record(stream)
+            ost.append(oest.timings())
+            torch.cuda.synchronize()
+            oms.append(s_ev.elapsed_time(e_ev))
+        ost = np.mean(np.array(ost, dtype=np.float64), axis=0)
+        other = {"precision": "bf16" if oprec == SPLIT_BF16 else "fp32",
+                 "value": wl.n / (float(np.mean(oms)) * 1e-3), "ms_per_step": float(np.mean(oms)),
+                 "stages_ms": {"pair": float(ost[1]), "contraction": float(ost[2])}}
+        oest.close()
     line = {
         "metric": METRIC,
         "value": wl.n * world / (ms * 1e-3),
@@ -251,6 +274,10 @@ def run_gpu(args):
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
         "clocks": clk,
+        "other_precision": other,
+        "stated_error": {"fp32": "<= 1e-5 of each order's RMS vs the FP64 oracle (GPU tests)",
+                         "bf16": "<= 3e-5 of each order's RMS vs the FP64 oracle (GPU tests); "
+                                 "~3e-7 measured with tensor memory drained every 2 steps"},
     }
     if not args.no_cpu_baseline:
         rate, cores, desc = cpu_oracle_rate(wl, args.cpu_sample)
@@ -273,6 +300,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1500)
     ap.add_argument("--ref-sample", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-precision", action="store_true",
+                    help="skip timing the other contraction precision")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

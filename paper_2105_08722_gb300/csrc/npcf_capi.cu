@@ -69,6 +69,7 @@ struct npcf_ctx {
     int cell_run = 2;          // x-adjacent cells per pair-kernel work unit
     int pair_cap = 4096;       // per group of the pair kernel
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
+    int drain_steps = 2;       // tensor-core contraction: steps of 16 primaries per TMEM drain
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -85,6 +86,12 @@ struct npcf_ctx {
     DevBuf<int> c4sb, c4se, c4lm3, c4lamseg0, c4odd;
     DevBuf<float> c4fac;
     int c4nrows = 0, c4nterms = 0, c4nseg = 0, c4nlam = 0;
+    // tensor-core (split bf16) 4PCF contraction tables
+    DevBuf<int4> tc_segs, tc_groups, tc_tiles;
+    DevBuf<int> tc_group_lams, tc_group_bslab, tc_combo_bin;
+    DevBuf<int2> tc_combos;
+    int tc_ngroup = 0, tc_ntile = 0, tc_ncombo = 0, tc_nbslab = 0, tc_maxcomp = 0;
+    int off4 = 0, nb4 = 0;
 
     // working buffers
     DevBuf<float4> pts;
@@ -134,6 +141,63 @@ cudaError_t upload(DevBuf<T>& b, const std::vector<T>& v) {
     if (e != cudaSuccess) return e;
     if (!v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
+}
+
+// Tables of the tensor-core 4PCF contraction: rows (multiplet, b1, b2) grouped by
+// (l3, parity), cut into 128-row tiles; one B slab per (group, component).
+npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTable4& t) {
+    const int nr = ctx->nr;
+    std::vector<int2> combos;
+    std::vector<int> cbin;
+    for (int b = 0; b < o.n_bins(); ++b) {
+        const int* B = &o.bins[3 * b];
+        if (B[2] != B[1] + 1) continue;
+        combos.push_back(make_int2(B[0], B[1]));
+        cbin.push_back(b);
+    }
+    std::vector<int4> groups, tiles, segs;
+    std::vector<int> glams, gbslab;
+    int nbslab = 0, maxcomp = 0;
+    for (int l3 = 0; l3 <= ctx->lmax; ++l3)
+        for (int odd = 0; odd <= 1; ++odd) {
+            std::vector<int> lams;
+            for (int a = 0; a < o.n_lambda(); ++a)
+                if (o.lam[3 * a + 2] == l3 && (int)o.odd(a) == odd) lams.push_back(a);
+            if (lams.empty()) continue;
+            const int g = (int)groups.size();
+            const int ncomp = 2 * l3 + 1;
+            groups.push_back(make_int4(l3, odd, (int)glams.size(), (int)lams.size()));
+            gbslab.push_back(nbslab);
+            glams.insert(glams.end(), lams.begin(), lams.end());
+            const int rows = (int)lams.size() * (int)combos.size();
+            for (int r0 = 0; r0 < rows; r0 += 128)
+                tiles.push_back(make_int4(g, r0, std::min(128, rows - r0), nbslab));
+            nbslab += ncomp;
+            maxcomp = std::max(maxcomp, ncomp);
+        }
+    for (size_t i = 0; i < t.seg_begin.size(); ++i) {
+        float f = t.seg_factor[i];
+        int fb;
+        std::memcpy(&fb, &f, 4);
+        segs.push_back(make_int4(t.seg_begin[i], t.seg_end[i], t.seg_lm3[i], fb));
+    }
+    if (tiles.size() * 16 > 512 || groups.size() > 32)
+        return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: %zu accumulator tiles exceed tensor memory "
+                    "(at most 32; use fewer shells, a lower lmax or parity-even multiplets)", tiles.size());
+    (void)nr;
+    ctx->tc_ngroup = (int)groups.size();
+    ctx->tc_ntile = (int)tiles.size();
+    ctx->tc_ncombo = (int)combos.size();
+    ctx->tc_nbslab = nbslab;
+    ctx->tc_maxcomp = maxcomp;
+    CU(upload(ctx->tc_segs, segs));
+    CU(upload(ctx->tc_groups, groups));
+    CU(upload(ctx->tc_tiles, tiles));
+    CU(upload(ctx->tc_group_lams, glams));
+    CU(upload(ctx->tc_group_bslab, gbslab));
+    CU(upload(ctx->tc_combos, combos));
+    CU(upload(ctx->tc_combo_bin, cbin));
+    return NPCF_OK;
 }
 
 npcf_status setup_tables(npcf_ctx* ctx) {
@@ -201,6 +265,12 @@ npcf_status setup_tables(npcf_ctx* ctx) {
             CU(upload(ctx->c4fac, t.seg_factor));
             CU(upload(ctx->c4lamseg0, t.lam_seg0));
             CU(upload(ctx->c4odd, odd));
+            ctx->off4 = off;
+            ctx->nb4 = nb;
+            if (ctx->prec == NPCF_SPLIT_BF16) {
+                npcf_status st = setup_tc_tables(ctx, o, t);
+                if (st != NPCF_OK) return st;
+            }
         }
     }
     return NPCF_OK;
@@ -359,8 +429,10 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[2], s));
 
     // contraction over primaries: chunks of cell-sorted primaries
+    // (the tensor-core contraction keeps its accumulators for a whole chunk: one wave)
+    const int waves = ctx->prec == NPCF_SPLIT_BF16 ? 1 : 4;
     int nchunk = ctx->chunk_target > 0 ? (n + ctx->chunk_target - 1) / ctx->chunk_target
-                                       : std::min(std::max(1, n / 64), 4 * ctx->nsm);
+                                       : std::min(std::max(1, n / 64), waves * ctx->nsm);
     nchunk = std::max(1, nchunk);
     const int chunk = (n + nchunk - 1) / nchunk;
     nchunk = (n + chunk - 1) / chunk;
@@ -387,6 +459,45 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.out_off = ctx->order_off[k];
             c.nbins = o.n_bins();
             launch_contract3(c, s);
+        } else if (o.N == 4 && ctx->prec == NPCF_SPLIT_BF16) {
+            if (ctx->c4nrows == 0) continue;
+            Contract4TCArgs c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.chunk = chunk;
+            c.terms = ctx->c4terms.p;
+            c.nterms = ctx->c4nterms;
+            c.segs = ctx->tc_segs.p;
+            c.nseg = ctx->c4nseg;
+            c.lam_seg0 = ctx->c4lamseg0.p;
+            c.nlam = ctx->c4nlam;
+            c.groups = ctx->tc_groups.p;
+            c.group_lams = ctx->tc_group_lams.p;
+            c.ngroup = ctx->tc_ngroup;
+            c.tiles = ctx->tc_tiles.p;
+            c.ntile = ctx->tc_ntile;
+            c.combos = ctx->tc_combos.p;
+            c.combo_bin = ctx->tc_combo_bin.p;
+            c.ncombo = ctx->tc_ncombo;
+            c.group_bslab = ctx->tc_group_bslab.p;
+            c.nbslab = ctx->tc_nbslab;
+            c.maxcomp = ctx->tc_maxcomp;
+            c.off4 = ctx->off4;
+            c.nb4 = ctx->nb4;
+            c.drain_steps = ctx->drain_steps;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            c.err = ctx->errflag.p;
+            int dev = 0, optin = 0;
+            CU(cudaGetDevice(&dev));
+            CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            if (contract4_tc_smem_bytes(c) + 1024 > (size_t)optin)
+                return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: operands need %zu B of shared memory",
+                            contract4_tc_smem_bytes(c));
+            launch_contract4_tc(c, nchunk, s);
         } else if (o.N == 4) {
             if (ctx->c4nrows == 0) continue;
             Contract4Args c{};
@@ -449,8 +560,6 @@ npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr, c
         return bad(fail(ctx, NPCF_EUNSUPPORTED, "the 5PCF contraction is not built yet"));
     if (prec != NPCF_FP32 && prec != NPCF_SPLIT_BF16)
         return bad(fail(ctx, NPCF_EINVAL, "unknown precision %d", prec));
-    if (prec == NPCF_SPLIT_BF16)
-        return bad(fail(ctx, NPCF_EUNSUPPORTED, "split-BF16 contraction is not built yet"));
     for (int i = 0; i <= nr; ++i)
         if (!std::isfinite(edges[i]) || edges[i] < 0 || (i > 0 && !(edges[i] > edges[i - 1])))
             return bad(fail(ctx, NPCF_EINVAL, "edges must be finite, >= 0 and strictly increasing"));
@@ -629,6 +738,10 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
         case 5:
             if (value < 1 || value > 4) return fail(ctx, NPCF_EINVAL, "cells per work unit in [1, 4]");
             ctx->cell_run = value;
+            return NPCF_OK;
+        case 6:
+            if (value < 1) return fail(ctx, NPCF_EINVAL, "drain interval must be >= 1");
+            ctx->drain_steps = value;
             return NPCF_OK;
         default:
             return fail(ctx, NPCF_EINVAL, "unknown tuning key %d", key);

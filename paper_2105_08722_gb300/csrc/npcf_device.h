@@ -113,6 +113,42 @@ struct Contract4Args {
     int total;
 };
 
+// 4PCF contraction on the tensor cores (split bf16, fp32 accumulation in tensor memory).
+// Rows (multiplet, b1, b2) are grouped by (l3, parity); each group's rows form 128-row
+// tiles whose 128 x 16 (b3) accumulators stay in tensor memory for a block's whole chunk
+// of primaries.
+struct Contract4TCArgs {
+    const float2* alm;
+    const float* wp;
+    int n, nr, nlm;
+    int chunk;                 // primaries per block
+    const PairTerm* terms;
+    int nterms;
+    const int4* segs;          // per (multiplet, m3): term range, lm of a_{l3 m3}, 2 S(m3)
+    int nseg;
+    const int* lam_seg0;       // first segment of each multiplet (n_lambda + 1)
+    int nlam;
+    const int4* groups;        // (l3, odd, first multiplet in group_lams, multiplets)
+    const int* group_lams;
+    int ngroup;
+    const int4* tiles;         // (group, first row in the group, rows, first B slab)
+    int ntile;
+    const int2* combos;        // (b1, b2), b1 < b2 <= nr - 2
+    const int* combo_bin;      // bin-tuple index of (b1, b2, b2 + 1)
+    int ncombo;
+    const int* group_bslab;    // first B slab of each group
+    int nbslab;                // B slabs in total (sum of 2 l3 + 1)
+    int maxcomp;               // largest 2 l3 + 1
+    int off4, nb4;
+    int drain_steps;           // steps of 16 primaries between drains of tensor memory
+    double* partial;           // [nchunk][total]
+    int total;
+    int* err;
+};
+
+void launch_contract4_tc(const Contract4TCArgs& a, int nchunk, cudaStream_t s);
+size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
+
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
 void launch_contract4(const Contract4Args& a, cudaStream_t s);
 size_t contract4_smem_bytes(const Contract4Args& a);

@@ -14,6 +14,7 @@ from paper_2105_08722_gb300 import catalogs
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
+TOL_BF16 = 3e-5     # split-bf16 tensor-core contraction
 
 
 @pytest.fixture(scope="module")
@@ -269,3 +270,46 @@ def test_lognormal_200k_full_run_is_sum_of_complementary_samples(torch_dev, c2_w
     assert np.array_equal(ca + cb, cfull)
     # the two runs sum different primary subsets in FP32 within each chunk
     assert_orders_close(a + b, full, wl.orders, wl.lmax, len(wl.edges) - 1)
+
+
+# ------------------------------------------------------------------ split-bf16 tensor-core contraction
+
+def test_4pcf_split_bf16_periodic_lmax5_10_shells(torch_dev):
+    pos = catalogs.lognormal_box(2500, 300.0, 64, seed=31)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(8.0, 60.0, 11)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 5, edges, 300.0, prec=1)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 5, edges, 300.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4), 5, 10, tol=TOL_BF16)
+
+
+def test_4pcf_split_bf16_all_parity_weighted(torch_dev):
+    pos, w = _catalog(1500, 120.0, 41)
+    w = w - np.float32(0.9)
+    edges = np.linspace(6.0, 36.0, 7)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 0.0, allparity=True, prec=1)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 4, edges, 0.0, allparity=True)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4), 4, 6, allparity=True, tol=TOL_BF16)
+
+
+def test_split_bf16_and_fp32_paths_agree_on_ragged_chunks(torch_dev):
+    # chunk sizes that leave partial steps of 16 primaries and empty blocks
+    pos, w = _catalog(1037, 100.0, 43)
+    edges = np.linspace(4.0, 30.0, 9)
+    for chunk in (1, 15, 17, 1000, 5000):
+        _, a, _ = gpu_run(torch_dev, pos, w, (4,), 3, edges, 100.0, prec=1, tuning={2: chunk})
+        _, b, _ = gpu_run(torch_dev, pos, w, (4,), 3, edges, 100.0, prec=0, tuning={2: chunk})
+        assert_orders_close(a, b, (4,), 3, 8, tol=TOL_BF16)
+
+
+def test_lognormal_200k_split_bf16_sampled_primaries(torch_dev, c2_workload):
+    wl = c2_workload
+    rng = np.random.default_rng(2025)
+    sample = np.sort(rng.choice(wl.n, 48, replace=False))
+    wp = np.zeros(wl.n, np.float32)
+    wp[sample] = wl.w[sample]
+    _, got, _ = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wp, prec=1)
+    want, _ = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample)
+    assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1, tol=TOL_BF16)
