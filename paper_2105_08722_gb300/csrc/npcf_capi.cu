@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -92,6 +93,14 @@ struct npcf_ctx {
     DevBuf<int2> tc_combos;
     int tc_ngroup = 0, tc_ntile = 0, tc_ncombo = 0, tc_nbslab = 0, tc_maxcomp = 0;
     int off4 = 0, nb4 = 0;
+    // 5PCF contraction tables
+    DevBuf<PairTerm> c5terms12, c5terms34;
+    DevBuf<int2> c5segs12, c5segs34, c5pairs;
+    DevBuf<int> c5t12seg0, c5t34seg0, c5t34l12, c5blkt34;
+    DevBuf<int4> c5rowsA, c5rowsB, c5blocks;
+    DevBuf<float2> c5rowsC;
+    int c5nrows = 0, c5nblocks = 0, c5npairs = 0, c5l12max = 0;
+    int c5nt12 = 0, c5nt34 = 0, c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
 
     // working buffers
     DevBuf<float4> pts;
@@ -100,7 +109,7 @@ struct npcf_ctx {
     DevBuf<float2> alm;
     DevBuf<uint32_t> cnt;
     DevBuf<uint32_t> count, start, cursor;
-    DevBuf<double> partial, zeta, sumw;
+    DevBuf<double> partial, zeta, sumw, zscale;
     DevBuf<unsigned long long> counts;
     DevBuf<int> errflag, work;
     DevBuf<float> bbox;
@@ -200,6 +209,94 @@ npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTa
     return NPCF_OK;
 }
 
+// Tables of the 5PCF contraction: rows (multiplet, b1, b2), b2 <= nr - 3, sorted by the
+// (l12 l3 l4) triple, cut into blocks of <= 256 rows using <= kMaxT34 distinct triples.
+npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
+    const int nr = ctx->nr;
+    if (nr > 10)
+        return fail(ctx, NPCF_EUNSUPPORTED, "the 5PCF contraction supports at most 10 shells");
+    ContractTable5 t = make_contract5(o);
+    std::vector<int2> pairs;
+    for (int b3 = 0; b3 < nr; ++b3)
+        for (int b4 = b3 + 1; b4 < nr; ++b4) pairs.push_back(make_int2(b3, b4));
+    auto pair_index = [&](int b3, int b4) {
+        for (size_t i = 0; i < pairs.size(); ++i)
+            if (pairs[i].x == b3 && pairs[i].y == b4) return (int)i;
+        return -1;
+    };
+    auto bin_index = [&](int b1, int b2, int b3, int b4) {
+        for (int b = 0; b < o.n_bins(); ++b) {
+            const int* B = &o.bins[4 * b];
+            if (B[0] == b1 && B[1] == b2 && B[2] == b3 && B[3] == b4) return b;
+        }
+        return -1;
+    };
+    struct Row { int t34, t12, lam, b1, b2; };
+    std::vector<Row> rows;
+    for (int a = 0; a < o.n_lambda(); ++a)
+        for (int b1 = 0; b1 < nr; ++b1)
+            for (int b2 = b1 + 1; b2 <= nr - 3; ++b2)
+                rows.push_back({t.lam_t34[a], t.lam_t12[a], a, b1, b2});
+    std::stable_sort(rows.begin(), rows.end(), [](const Row& x, const Row& y) {
+        if (x.t34 != y.t34) return x.t34 < y.t34;
+        return x.t12 < y.t12;
+    });
+    std::vector<int4> rowsA, rowsB, blocks;
+    std::vector<float2> rowsC;
+    std::vector<int> blk_t34;
+    size_t r = 0;
+    while (r < rows.size()) {
+        const int first = (int)r;
+        std::vector<int> trip;
+        while (r < rows.size() && (int)(r - first) < 256) {
+            int loc = -1;
+            for (size_t q = 0; q < trip.size(); ++q)
+                if (trip[q] == rows[r].t34) loc = (int)q;
+            if (loc < 0) {
+                if ((int)trip.size() == kMaxT34) break;
+                trip.push_back(rows[r].t34);
+                loc = (int)trip.size() - 1;
+            }
+            const Row& R = rows[r];
+            const int* L = &o.lam[(size_t)R.lam * 5];
+            const int np = (nr - 1 - R.b2) * (nr - 2 - R.b2) / 2;
+            rowsA.push_back(make_int4(R.lam, R.b1, R.b2, off + R.lam * o.n_bins() + bin_index(R.b1, R.b2, R.b2 + 1, R.b2 + 2)));
+            rowsB.push_back(make_int4(R.t12, loc, pair_index(R.b2 + 1, R.b2 + 2), np));
+            rowsC.push_back(make_float2((float)std::sqrt(2.0 * L[2] + 1.0), o.odd(R.lam) ? 1.f : 0.f));
+            ++r;
+        }
+        blocks.push_back(make_int4(first, (int)r - first, (int)trip.size(), 0));
+        for (int q = 0; q < kMaxT34; ++q) blk_t34.push_back(q < (int)trip.size() ? trip[q] : 0);
+    }
+    std::vector<int2> s12, s34;
+    for (size_t i = 0; i < t.seg12_begin.size(); ++i) s12.push_back(make_int2(t.seg12_begin[i], t.seg12_end[i]));
+    for (size_t i = 0; i < t.seg34_begin.size(); ++i) s34.push_back(make_int2(t.seg34_begin[i], t.seg34_end[i]));
+    ctx->c5nrows = (int)rowsA.size();
+    ctx->c5nblocks = (int)blocks.size();
+    ctx->c5npairs = (int)pairs.size();
+    ctx->c5l12max = t.l12max;
+    ctx->c5nt12 = (int)t.t12_seg0.size() - 1;
+    ctx->c5nt34 = (int)t.t34_seg0.size() - 1;
+    ctx->c5nterms12 = (int)t.terms12.size();
+    ctx->c5nterms34 = (int)t.terms34.size();
+    ctx->c5nseg12 = (int)s12.size();
+    ctx->c5nseg34 = (int)s34.size();
+    CU(upload(ctx->c5terms12, t.terms12));
+    CU(upload(ctx->c5terms34, t.terms34));
+    CU(upload(ctx->c5segs12, s12));
+    CU(upload(ctx->c5segs34, s34));
+    CU(upload(ctx->c5pairs, pairs));
+    CU(upload(ctx->c5t12seg0, t.t12_seg0));
+    CU(upload(ctx->c5t34seg0, t.t34_seg0));
+    CU(upload(ctx->c5t34l12, t.t34_l12));
+    CU(upload(ctx->c5blkt34, blk_t34));
+    CU(upload(ctx->c5rowsA, rowsA));
+    CU(upload(ctx->c5rowsB, rowsB));
+    CU(upload(ctx->c5rowsC, rowsC));
+    CU(upload(ctx->c5blocks, blocks));
+    return NPCF_OK;
+}
+
 npcf_status setup_tables(npcf_ctx* ctx) {
     ctx->nlm = nlm(ctx->lmax);
     // Y_lm conversion matrix
@@ -214,6 +311,18 @@ npcf_status setup_tables(npcf_ctx* ctx) {
         const OrderTable& o = ctx->orders.back();
         ctx->total += o.n_lambda() * o.n_bins();
     }
+    // per output entry: the harmonic normalisation of its multiplet's N-1 factors
+    std::vector<double> zs;
+    zs.reserve(ctx->total);
+    for (const OrderTable& o : ctx->orders)
+        for (int L = 0; L < o.n_lambda(); ++L) {
+            const int* l = &o.lam[(size_t)L * o.width];
+            double f = 1.0;
+            for (int k = 0; k < o.width; ++k)
+                if (!(o.N == 5 && k == 2)) f *= ylm_l_norm(l[k]);   // l12 couples, it is no harmonic
+            zs.insert(zs.end(), o.n_bins(), f);
+        }
+    CU(upload(ctx->zscale, zs));
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
         const int off = ctx->order_off[k];
@@ -271,6 +380,9 @@ npcf_status setup_tables(npcf_ctx* ctx) {
                 npcf_status st = setup_tc_tables(ctx, o, t);
                 if (st != NPCF_OK) return st;
             }
+        } else if (o.N == 5) {
+            npcf_status st = setup_c5_tables(ctx, o, off);
+            if (st != NPCF_OK) return st;
         }
     }
     return NPCF_OK;
@@ -498,6 +610,41 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
                 return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: operands need %zu B of shared memory",
                             contract4_tc_smem_bytes(c));
             launch_contract4_tc(c, nchunk, s);
+        } else if (o.N == 5) {
+            if (ctx->c5nrows == 0) continue;
+            Contract5Args c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.nchunk = nchunk;
+            c.chunk = chunk;
+            c.terms12 = ctx->c5terms12.p;
+            c.segs12 = ctx->c5segs12.p;
+            c.t12_seg0 = ctx->c5t12seg0.p;
+            c.terms34 = ctx->c5terms34.p;
+            c.segs34 = ctx->c5segs34.p;
+            c.t34_seg0 = ctx->c5t34seg0.p;
+            c.t34_l12 = ctx->c5t34l12.p;
+            c.nterms12 = ctx->c5nterms12;
+            c.nterms34 = ctx->c5nterms34;
+            c.nseg12 = ctx->c5nseg12;
+            c.nseg34 = ctx->c5nseg34;
+            c.nt12 = ctx->c5nt12;
+            c.nt34 = ctx->c5nt34;
+            c.rowsA = ctx->c5rowsA.p;
+            c.rowsB = ctx->c5rowsB.p;
+            c.rowsC = ctx->c5rowsC.p;
+            c.blocks = ctx->c5blocks.p;
+            c.blk_t34 = ctx->c5blkt34.p;
+            c.nblocks = ctx->c5nblocks;
+            c.pairs = ctx->c5pairs.p;
+            c.npairs = ctx->c5npairs;
+            c.l12max = ctx->c5l12max;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            launch_contract5(c, s);
         } else if (o.N == 4) {
             if (ctx->c4nrows == 0) continue;
             Contract4Args c{};
@@ -527,7 +674,7 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         CU(cudaGetLastError());
     }
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[3], s));
-    if (ctx->total > 0) launch_reduce(ctx->partial.p, nchunk, ctx->total, ctx->zeta.p, s);
+    if (ctx->total > 0) launch_reduce(ctx->partial.p, nchunk, ctx->total, ctx->zscale.p, ctx->zeta.p, s);
     CU(cudaGetLastError());
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[4], s));
     ctx->nchunk = nchunk;
@@ -556,8 +703,6 @@ npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr, c
     if (!edges) return bad(fail(ctx, NPCF_EINVAL, "edges is null"));
     if ((order_mask & ~((1u << 3) | (1u << 4) | (1u << 5))) || order_mask == 0)
         return bad(fail(ctx, NPCF_EINVAL, "order_mask 0x%x must select orders among 3, 4, 5", order_mask));
-    if (order_mask & (1u << 5))
-        return bad(fail(ctx, NPCF_EUNSUPPORTED, "the 5PCF contraction is not built yet"));
     if (prec != NPCF_FP32 && prec != NPCF_SPLIT_BF16)
         return bad(fail(ctx, NPCF_EINVAL, "unknown precision %d", prec));
     for (int i = 0; i <= nr; ++i)
@@ -706,8 +851,16 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
     for (int64_t q = 0; q < k; ++q) {
         if (idx[q] < 0 || idx[q] >= n) return fail(ctx, NPCF_EINVAL, "index out of range");
         const int sp = inv[idx[q]];
-        CU(cudaMemcpy(alm + q * per * 2, ctx->alm.p + (size_t)sp * per, per * sizeof(float2),
-                      cudaMemcpyDeviceToHost));
+        float* dst = alm + q * per * 2;
+        CU(cudaMemcpy(dst, ctx->alm.p + (size_t)sp * per, per * sizeof(float2), cudaMemcpyDeviceToHost));
+        // the device holds reduced harmonics: restore sqrt((2l+1)/(4 pi))
+        for (int b = 0; b < ctx->nr; ++b)
+            for (int l = 0; l <= ctx->lmax; ++l)
+                for (int m = 0; m <= l; ++m) {
+                    const size_t e = 2 * ((size_t)b * ctx->nlm + lm_index(l, m));
+                    dst[e] = (float)(dst[e] * ylm_l_norm(l));
+                    dst[e + 1] = (float)(dst[e + 1] * ylm_l_norm(l));
+                }
         if (counts)
             CU(cudaMemcpy(counts + q * ctx->nr, ctx->cnt.p + (size_t)sp * ctx->nr, ctx->nr * sizeof(uint32_t),
                           cudaMemcpyDeviceToHost));

@@ -144,13 +144,15 @@ __global__ void k_contract4(const Contract4Args a) {
     }
 }
 
+// FP64 sum over the chunks' partials, times the multiplet's harmonic normalisation
+// prod_k sqrt((2 l_k + 1)/(4 pi)) (the contractions work on reduced harmonics).
 __global__ void k_reduce(const double* __restrict__ partial, int nchunk, int total,
-                         double* __restrict__ zeta) {
+                         const double* __restrict__ scale, double* __restrict__ zeta) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= total) return;
     double s = 0.0;
     for (int c = 0; c < nchunk; ++c) s += partial[(size_t)c * total + e];
-    zeta[e] += s;
+    zeta[e] += s * scale[e];
 }
 
 }  // namespace
@@ -177,8 +179,9 @@ void launch_contract4(const Contract4Args& a, cudaStream_t s) {
     k_contract4<<<grid, threads, smem, s>>>(a);
 }
 
-void launch_reduce(const double* partial, int nchunk, int total, double* zeta, cudaStream_t s) {
-    k_reduce<<<(total + 255) / 256, 256, 0, s>>>(partial, nchunk, total, zeta);
+void launch_reduce(const double* partial, int nchunk, int total, const double* scale, double* zeta,
+                   cudaStream_t s) {
+    k_reduce<<<(total + 255) / 256, 256, 0, s>>>(partial, nchunk, total, scale, zeta);
 }
 
 }  // namespace npcf

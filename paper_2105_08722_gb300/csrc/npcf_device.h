@@ -147,6 +147,43 @@ struct Contract4TCArgs {
 };
 
 void launch_contract4_tc(const Contract4TCArgs& a, int nchunk, cudaStream_t s);
+
+// 5PCF contraction (FP32 CUDA cores). For multiplet L = (l1, l2, l12, l3, l4):
+//   P12^{m12}(b1,b2) = sum_{m1} (l1 l2 l12; m1, m12-m1, -m12) a^{b1}_{l1 m1} a^{b2}_{l2, m12-m1}
+//   P34^{m12}(b3,b4) = sum_{m3} (l12 l3 l4; m12, m3, -m12-m3) a^{b3}_{l3 m3} a^{b4}_{l4, -m12-m3}
+//   zeta_L(b1..b4) += u sqrt(2 l12 + 1) sum_{m12>=0} 2 S(m12) (-1)^{l12-m12} Q_L[P12 P34].
+// Rows (L, b1, b2) with b2 <= nr - 3 are sorted by the (l12, l3, l4) triple; each block of
+// rows lists the distinct triples it needs (at most kMaxT34), whose P34 the block tabulates
+// per primary in shared memory.
+constexpr int kMaxT34 = 16;
+constexpr int kMaxPairs5 = 28;   // (b3, b4) pairs after b2 held per thread (nr <= 10)
+struct Contract5Args {
+    const float2* alm;
+    const float* wp;
+    int n, nr, nlm;
+    int nchunk, chunk;
+    const PairTerm* terms12;
+    const int2* segs12;        // term ranges per (l1 l2 l12 triple, m12)
+    const int* t12_seg0;       // first segment of each triple
+    const PairTerm* terms34;
+    const int2* segs34;
+    const int* t34_seg0;
+    const int* t34_l12;
+    int nterms12, nterms34, nseg12, nseg34, nt12, nt34;
+    const int4* rowsA;         // (multiplet, b1, b2, first output entry)
+    const int4* rowsB;         // (l1 l2 l12 triple, local l3 l4 triple, first pair index, pairs)
+    const float2* rowsC;       // (sqrt(2 l12 + 1), parity-odd ? 1 : 0)
+    const int4* blocks;        // (first row, rows, number of triples, 0)
+    const int* blk_t34;        // [nblocks][kMaxT34] triples of each block
+    int nblocks;
+    const int2* pairs;         // (b3, b4) of every pair b3 < b4 (lexicographic)
+    int npairs;
+    int l12max;
+    double* partial;
+    int total;
+};
+void launch_contract5(const Contract5Args& a, cudaStream_t s);
+size_t contract5_smem_bytes(const Contract5Args& a);
 size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
@@ -154,6 +191,8 @@ void launch_contract4(const Contract4Args& a, cudaStream_t s);
 size_t contract4_smem_bytes(const Contract4Args& a);
 
 // ---------------------------------------------------------------- FP64 reduction (a6)
-void launch_reduce(const double* partial, int nchunk, int total, double* zeta, cudaStream_t s);
+// zeta[e] += scale[e] * sum_c partial[c][e]
+void launch_reduce(const double* partial, int nchunk, int total, const double* scale, double* zeta,
+                   cudaStream_t s);
 
 }  // namespace npcf

@@ -1,6 +1,8 @@
 // Host-side tables of libencore_gpu (see npcf_tables.h).
 #include "npcf_tables.h"
 
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 
@@ -99,9 +101,13 @@ OrderTable make_order(int N, int lmax, int nr, bool allparity) {
     return o;
 }
 
+double ylm_l_norm(int l) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    return (double)std::sqrt((2.0L * l + 1.0L) / (4.0L * pi));
+}
+
 std::vector<double> ylm_chebyshev_matrix(int lmax) {
     const long double* f = facts().f;
-    const long double pi = 3.141592653589793238462643383279502884L;
     // power-series coefficients of the Chebyshev polynomials T_k, k <= lmax
     std::vector<std::vector<long double>> T(lmax + 1, std::vector<long double>(lmax + 1, 0.0L));
     T[0][0] = 1.0L;
@@ -117,7 +123,9 @@ std::vector<double> ylm_chebyshev_matrix(int lmax) {
             c[l - 2 * j] = neg1pow(j) * f[2 * l - 2 * j] /
                            (std::pow(2.0L, l) * f[j] * f[l - j] * f[l - 2 * j]);
         for (int m = 0; m <= l; ++m) {
-            long double norm = std::sqrt((2.0L * l + 1.0L) / (4.0L * pi) * f[l - m] / f[l + m]);
+            // reduced harmonic: the factor sqrt((2l+1)/(4 pi)) is left out here and
+            // applied once per multiplet in FP64 (ylm_l_norm)
+            long double norm = std::sqrt(f[l - m] / f[l + m]);
             // q(z) = N_lm (-1)^m d^m P_l / dz^m in powers of z
             std::vector<long double> q(l - m + 1, 0.0L);
             for (int kk = 0; kk + m <= l; ++kk) q[kk] = norm * neg1pow(m) * c[kk + m] * f[kk + m] / f[kk];
@@ -170,6 +178,57 @@ ContractTable4 make_contract4(const OrderTable& o) {
         }
     }
     t.lam_seg0.push_back((int)t.seg_begin.size());
+    return t;
+}
+
+ContractTable5 make_contract5(const OrderTable& o) {
+    ContractTable5 t;
+    std::vector<std::array<int, 3>> k12, k34;
+    auto find_or_add = [](std::vector<std::array<int, 3>>& v, std::array<int, 3> key) {
+        for (size_t i = 0; i < v.size(); ++i)
+            if (v[i] == key) return (int)i;
+        v.push_back(key);
+        return (int)v.size() - 1;
+    };
+    for (int a = 0; a < o.n_lambda(); ++a) {
+        const int* L = &o.lam[(size_t)a * 5];
+        t.lam_t12.push_back(find_or_add(k12, {L[0], L[1], L[2]}));
+        t.lam_t34.push_back(find_or_add(k34, {L[2], L[3], L[4]}));
+        t.l12max = std::max(t.l12max, L[2]);
+    }
+    for (const auto& k : k12) {
+        const int l1 = k[0], l2 = k[1], l12 = k[2];
+        t.t12_seg0.push_back((int)t.seg12_begin.size());
+        for (int m12 = 0; m12 <= l12; ++m12) {
+            t.seg12_begin.push_back((int)t.terms12.size());
+            for (int m1 = -l1; m1 <= l1; ++m1) {
+                const int m2 = m12 - m1;
+                if (std::abs(m2) > l2) continue;
+                const double c = wigner3j(l1, l2, l12, m1, m2, -m12);
+                if (std::fabs(c) < 1e-14) continue;
+                t.terms12.push_back(make_pair_term(c, l1, m1, l2, m2));
+            }
+            t.seg12_end.push_back((int)t.terms12.size());
+        }
+    }
+    t.t12_seg0.push_back((int)t.seg12_begin.size());
+    for (const auto& k : k34) {
+        const int l12 = k[0], l3 = k[1], l4 = k[2];
+        t.t34_seg0.push_back((int)t.seg34_begin.size());
+        t.t34_l12.push_back(l12);
+        for (int m12 = 0; m12 <= l12; ++m12) {
+            t.seg34_begin.push_back((int)t.terms34.size());
+            for (int m3 = -l3; m3 <= l3; ++m3) {
+                const int m4 = -m12 - m3;
+                if (std::abs(m4) > l4) continue;
+                const double c = wigner3j(l12, l3, l4, m12, m3, m4);
+                if (std::fabs(c) < 1e-14) continue;
+                t.terms34.push_back(make_pair_term(c, l3, m3, l4, m4));
+            }
+            t.seg34_end.push_back((int)t.terms34.size());
+        }
+    }
+    t.t34_seg0.push_back((int)t.seg34_begin.size());
     return t;
 }
 

@@ -37,7 +37,15 @@ OrderTable make_order(int N, int lmax, int nr, bool allparity);
 // unit vectors): the polynomial factor is rewritten in the Chebyshev basis, whose
 // coefficients stay O(1) where the plain powers z^k would alternate in sign and grow,
 // so the FP32 sums lose little to cancellation.
+//
+// The matrix yields the reduced coefficients a_lm / sqrt((2l+1)/(4 pi)): with that
+// factor gone the l = 0 row is exactly 1 and every m = 0 row is a dyadic rational, so
+// the FP32 sums carry no rounded normalisation. A rounded Y_00 = 1/(2 sqrt(pi)) would
+// otherwise bias every coefficient of order N by (N-1) times its relative rounding
+// (2e-7 for the 5PCF), far above the random rounding of the sums. The product of the
+// factors of a multiplet's N-1 harmonics is applied in FP64 after the reduction.
 std::vector<double> ylm_chebyshev_matrix(int lmax);
+double ylm_l_norm(int l);   // sqrt((2l+1)/(4 pi))
 
 // One product term c * a^{b1}_{l1 m1} * a^{b2}_{l2 m2} with m1, m2 of either sign,
 // written on the stored m >= 0 coefficients (x1 + i y1), (x2 + i y2) using
@@ -64,5 +72,20 @@ struct ContractTable4 {
 };
 
 ContractTable4 make_contract4(const OrderTable& o);
+
+// 5PCF coupling tables: the distinct (l1 l2 l12) and (l12 l3 l4) triples of the order's
+// multiplets, each with one term segment per m12 = 0..l12:
+//   P12: terms over m1 with m2 = m12 - m1, coefficient (l1 l2 l12; m1, m2, -m12);
+//   P34: terms over m3 with m4 = -m12 - m3, coefficient (l12 l3 l4; m12, m3, m4).
+struct ContractTable5 {
+    std::vector<PairTerm> terms12, terms34;
+    std::vector<int> seg12_begin, seg12_end, t12_seg0;   // t12_seg0: n_t12 + 1 entries
+    std::vector<int> seg34_begin, seg34_end, t34_seg0;
+    std::vector<int> t34_l12;
+    std::vector<int> lam_t12, lam_t34;                  // triple ids of each multiplet
+    int l12max = 0;
+};
+
+ContractTable5 make_contract5(const OrderTable& o);
 
 }  // namespace npcf

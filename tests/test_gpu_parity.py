@@ -313,3 +313,36 @@ def test_lognormal_200k_split_bf16_sampled_primaries(torch_dev, c2_workload):
     _, got, _ = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wp, prec=1)
     want, _ = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample)
     assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1, tol=TOL_BF16)
+
+
+# ------------------------------------------------------------------ 5PCF
+
+def test_5pcf_periodic_lmax3(torch_dev):
+    pos = catalogs.lognormal_box(900, 150.0, 32, seed=51)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(6.0, 42.0, 7)
+    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 3, edges, 150.0)
+    want, wcounts = oracle.npcf(pos, w, (5,), 3, edges, 150.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (5,), 3, 6)
+
+
+def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev):
+    pos, w = _catalog(500, 80.0, 52)
+    w = w - np.float32(0.8)
+    edges = np.linspace(5.0, 30.0, 6)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4, 5), 2, edges, 0.0, allparity=True)
+    want, wcounts = oracle.npcf(pos, w, (3, 4, 5), 2, edges, 0.0, allparity=True)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4, 5), 2, 5, allparity=True)
+
+
+def test_lognormal_100k_5pcf_lmax4_sampled_primaries(torch_dev):
+    wl = catalogs.c4_lognormal_5pcf()
+    rng = np.random.default_rng(2026)
+    sample = np.sort(rng.choice(wl.n, 16, replace=False))
+    wp = np.zeros(wl.n, np.float32)
+    wp[sample] = wl.w[sample]
+    _, got, _ = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wp)
+    want, _ = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample)
+    assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
