@@ -82,13 +82,12 @@ struct npcf_ctx {
     DevBuf<int2> c3rows, c3pairs;
     DevBuf<float> c3coef;
     int c3nrows = 0;
-    DevBuf<int4> c4rows;
     DevBuf<PairTerm> c4terms;
-    DevBuf<int> c4sb, c4se, c4lm3, c4lamseg0, c4odd;
-    DevBuf<float> c4fac;
-    int c4nrows = 0, c4nterms = 0, c4nseg = 0, c4nlam = 0;
+    DevBuf<int4> c4segs, c4items;
+    DevBuf<int> c4lamseg0;
+    int c4nitem = 0, c4nterms = 0, c4nseg = 0, c4nlam = 0;
     // tensor-core (split bf16) 4PCF contraction tables
-    DevBuf<int4> tc_segs, tc_groups, tc_tiles;
+    DevBuf<int4> tc_groups, tc_tiles;
     DevBuf<int> tc_group_lams, tc_group_bslab, tc_combo_bin;
     DevBuf<int2> tc_combos;
     int tc_ngroup = 0, tc_ntile = 0, tc_ncombo = 0, tc_nbslab = 0, tc_maxcomp = 0;
@@ -114,7 +113,6 @@ struct npcf_ctx {
     DevBuf<int> errflag, work;
     DevBuf<float> bbox;
     DevBuf<float> hpos_stage, hw_stage;
-    int nchunk = 0;
     int64_t last_n = 0;
     int nsm = 0;
 
@@ -164,7 +162,7 @@ npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTa
         combos.push_back(make_int2(B[0], B[1]));
         cbin.push_back(b);
     }
-    std::vector<int4> groups, tiles, segs;
+    std::vector<int4> groups, tiles;
     std::vector<int> glams, gbslab;
     int nbslab = 0, maxcomp = 0;
     for (int l3 = 0; l3 <= ctx->lmax; ++l3)
@@ -184,12 +182,6 @@ npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTa
             nbslab += ncomp;
             maxcomp = std::max(maxcomp, ncomp);
         }
-    for (size_t i = 0; i < t.seg_begin.size(); ++i) {
-        float f = t.seg_factor[i];
-        int fb;
-        std::memcpy(&fb, &f, 4);
-        segs.push_back(make_int4(t.seg_begin[i], t.seg_end[i], t.seg_lm3[i], fb));
-    }
     if (tiles.size() * 16 > 512 || groups.size() > 32)
         return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: %zu accumulator tiles exceed tensor memory "
                     "(at most 32; use fewer shells, a lower lmax or parity-even multiplets)", tiles.size());
@@ -199,7 +191,6 @@ npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTa
     ctx->tc_ncombo = (int)combos.size();
     ctx->tc_nbslab = nbslab;
     ctx->tc_maxcomp = maxcomp;
-    CU(upload(ctx->tc_segs, segs));
     CU(upload(ctx->tc_groups, groups));
     CU(upload(ctx->tc_tiles, tiles));
     CU(upload(ctx->tc_group_lams, glams));
@@ -344,36 +335,58 @@ npcf_status setup_tables(npcf_ctx* ctx) {
             (void)off;
         } else if (o.N == 4) {
             ContractTable4 t = make_contract4(o);
-            // rows (multiplet, b1, b2) with at least one b3 > b2, and their first output
-            std::vector<int4> rows;
             const int nb = o.n_bins();
-            for (int a = 0; a < o.n_lambda(); ++a)
-                for (int b = 0; b < nb; ++b) {
-                    const int* B = &o.bins[3 * b];
-                    if (B[2] != B[1] + 1) continue;  // first b3 of this (b1, b2)
-                    rows.push_back(make_int4(a, B[0], B[1], off + a * nb + b));
-                }
-            std::vector<int> odd;
-            for (int a = 0; a < o.n_lambda(); ++a) odd.push_back(o.odd(a) ? 1 : 0);
-            ctx->c4nrows = (int)rows.size();
-            ctx->c4nterms = (int)t.terms.size();
-            {
-                const size_t need = (size_t)t.terms.size() * 20 + t.seg_begin.size() * 16 +
-                                    (size_t)8 * ctx->nr * ctx->nlm * 8 + 4096;
-                if (need > 200 * 1024)
-                    return fail(ctx, NPCF_EUNSUPPORTED, "4PCF coupling table (%zu terms) exceeds shared "
-                                "memory; use lmax <= 7", t.terms.size());
+            std::vector<int4> segs;
+            for (size_t i = 0; i < t.seg_begin.size(); ++i) {
+                float f = t.seg_factor[i];
+                int fb;
+                std::memcpy(&fb, &f, 4);
+                segs.push_back(make_int4(t.seg_begin[i], t.seg_end[i], t.seg_lm3[i], fb));
             }
+            // items (multiplet, b1) with at least one (b2, b3) after b1; heaviest first
+            std::vector<std::pair<double, int4>> items;
+            for (int a = 0; a < o.n_lambda(); ++a)
+                for (int b1 = 0; b1 + 2 < ctx->nr; ++b1) {
+                    int first = -1;
+                    for (int b = 0; b < nb && first < 0; ++b)
+                        if (o.bins[3 * b] == b1 && o.bins[3 * b + 1] == b1 + 1 && o.bins[3 * b + 2] == b1 + 2)
+                            first = b;
+                    const int nb2 = ctx->nr - 1 - b1;
+                    double cost = 0;
+                    for (int sg = t.lam_seg0[a]; sg < t.lam_seg0[a + 1]; ++sg)
+                        cost += 10.0 * nb2 * (t.seg_end[sg] - t.seg_begin[sg]) + 2.0 * nb2 * (nb2 - 1);
+                    items.push_back({cost, make_int4(t.lam_seg0[a], t.lam_seg0[a + 1],
+                                                     b1 | ((o.odd(a) ? 1 : 0) << 8) | (nb2 << 16),
+                                                     off + a * nb + first)});
+                }
+            std::stable_sort(items.begin(), items.end(),
+                             [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+                                 return x.first > y.first;
+                             });
+            std::vector<int4> it;
+            for (const auto& x : items) it.push_back(x.second);
+            ctx->c4nitem = (int)it.size();
+            ctx->c4nterms = (int)t.terms.size();
             ctx->c4nseg = (int)t.seg_begin.size();
             ctx->c4nlam = o.n_lambda();
-            CU(upload(ctx->c4rows, rows));
+            {
+                Contract4WArgs c{};
+                c.nr = ctx->nr;
+                c.nlm = ctx->nlm;
+                c.nterms = ctx->c4nterms;
+                c.nseg = ctx->c4nseg;
+                int dev = 0, optin = 0;
+                CU(cudaGetDevice(&dev));
+                CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+                if (ctx->prec == NPCF_FP32 && contract4w_smem_bytes(c) + 1024 > (size_t)optin)
+                    return fail(ctx, NPCF_EUNSUPPORTED, "4PCF: %d shells x %d harmonics and %d coupling terms "
+                                "need %zu B of shared memory (limit %d)", ctx->nr, ctx->nlm, ctx->c4nterms,
+                                contract4w_smem_bytes(c), optin);
+            }
             CU(upload(ctx->c4terms, t.terms));
-            CU(upload(ctx->c4sb, t.seg_begin));
-            CU(upload(ctx->c4se, t.seg_end));
-            CU(upload(ctx->c4lm3, t.seg_lm3));
-            CU(upload(ctx->c4fac, t.seg_factor));
+            CU(upload(ctx->c4segs, segs));
+            CU(upload(ctx->c4items, it));
             CU(upload(ctx->c4lamseg0, t.lam_seg0));
-            CU(upload(ctx->c4odd, odd));
             ctx->off4 = off;
             ctx->nb4 = nb;
             if (ctx->prec == NPCF_SPLIT_BF16) {
@@ -461,11 +474,11 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     CU(ctx->count.ensure(g.ncell));
     CU(ctx->start.ensure(g.ncell + 1));
     CU(ctx->cursor.ensure(g.ncell));
-    CU(ctx->work.ensure(1));
+    CU(ctx->work.ensure(2));
 
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[0], s));
     CU(cudaMemsetAsync(ctx->count.p, 0, g.ncell * sizeof(uint32_t), s));
-    CU(cudaMemsetAsync(ctx->work.p, 0, sizeof(int), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 2 * sizeof(int), s));
     k_sumw<<<64, 256, 0, s>>>(d_w, n, ctx->sumw.p);
 
     BinArgs b{};
@@ -548,7 +561,15 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     nchunk = std::max(1, nchunk);
     const int chunk = (n + nchunk - 1) / nchunk;
     nchunk = (n + chunk - 1) / chunk;
-    CU(ctx->partial.ensure((size_t)nchunk * ctx->total));
+    // partial rows each order's contraction fills
+    std::vector<int> rows_of(ctx->orders.size(), nchunk);
+    int prow = nchunk;
+    for (size_t k = 0; k < ctx->orders.size(); ++k)
+        if (ctx->orders[k].N == 4 && ctx->prec == NPCF_FP32) {
+            rows_of[k] = contract4w_blocks(ctx->nsm, n);
+            prow = std::max(prow, rows_of[k]);
+        }
+    CU(ctx->partial.ensure((size_t)prow * ctx->total));
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
         if (o.N == 3) {
@@ -572,7 +593,7 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.nbins = o.n_bins();
             launch_contract3(c, s);
         } else if (o.N == 4 && ctx->prec == NPCF_SPLIT_BF16) {
-            if (ctx->c4nrows == 0) continue;
+            if (ctx->c4nitem == 0) continue;
             Contract4TCArgs c{};
             c.alm = ctx->alm.p;
             c.wp = ctx->wp.p;
@@ -582,7 +603,7 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.chunk = chunk;
             c.terms = ctx->c4terms.p;
             c.nterms = ctx->c4nterms;
-            c.segs = ctx->tc_segs.p;
+            c.segs = ctx->c4segs.p;
             c.nseg = ctx->c4nseg;
             c.lam_seg0 = ctx->c4lamseg0.p;
             c.nlam = ctx->c4nlam;
@@ -646,38 +667,36 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.total = ctx->total;
             launch_contract5(c, s);
         } else if (o.N == 4) {
-            if (ctx->c4nrows == 0) continue;
-            Contract4Args c{};
+            if (ctx->c4nitem == 0) continue;
+            Contract4WArgs c{};
             c.alm = ctx->alm.p;
             c.wp = ctx->wp.p;
             c.n = n;
             c.nr = ctx->nr;
             c.nlm = ctx->nlm;
-            c.nchunk = nchunk;
-            c.chunk = chunk;
-            c.rows = ctx->c4rows.p;
-            c.nrows = ctx->c4nrows;
             c.terms = ctx->c4terms.p;
             c.nterms = ctx->c4nterms;
-            c.seg_begin = ctx->c4sb.p;
-            c.seg_end = ctx->c4se.p;
-            c.seg_lm3 = ctx->c4lm3.p;
-            c.seg_factor = ctx->c4fac.p;
-            c.lam_seg0 = ctx->c4lamseg0.p;
-            c.lam_odd = ctx->c4odd.p;
+            c.segs = ctx->c4segs.p;
             c.nseg = ctx->c4nseg;
-            c.nlam = ctx->c4nlam;
+            c.items = ctx->c4items.p;
+            c.nitem = ctx->c4nitem;
             c.partial = ctx->partial.p;
             c.total = ctx->total;
-            launch_contract4(c, s);
+            c.out_off = ctx->order_off[k];
+            c.nout = o.n_lambda() * o.n_bins();
+            c.tile_counter = ctx->work.p + 1;
+            launch_contract4w(c, rows_of[k], s);
         }
         CU(cudaGetLastError());
     }
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[3], s));
-    if (ctx->total > 0) launch_reduce(ctx->partial.p, nchunk, ctx->total, ctx->zscale.p, ctx->zeta.p, s);
+    for (size_t k = 0; k < ctx->orders.size(); ++k) {
+        const OrderTable& o = ctx->orders[k];
+        launch_reduce(ctx->partial.p, rows_of[k], ctx->total, ctx->order_off[k], o.n_lambda() * o.n_bins(),
+                      ctx->zscale.p, ctx->zeta.p, s);
+    }
     CU(cudaGetLastError());
     if (ctx->timed) CU(cudaEventRecord(ctx->ev[4], s));
-    ctx->nchunk = nchunk;
     ctx->last_n = n;
     return NPCF_OK;
 }

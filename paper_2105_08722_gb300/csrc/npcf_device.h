@@ -93,25 +93,25 @@ struct Contract3Args {
     int nbins;
 };
 
-struct Contract4Args {
-    const float2* alm;
-    const float* wp;
+// 4PCF contraction, FP32 on the CUDA cores: lanes are primaries, warps take items
+// (multiplet, b1); see npcf_contract4.cu.
+struct Contract4WArgs {
+    const float2* alm;         // [n][nr][nlm]
+    const float* wp;           // [n] primary weights
     int n, nr, nlm;
-    int nchunk, chunk;
-    const int4* rows;          // (multiplet, b1, b2, first output entry)
-    int nrows;
     const PairTerm* terms;
     int nterms;
-    const int* seg_begin;
-    const int* seg_end;
-    const int* seg_lm3;
-    const float* seg_factor;
-    const int* lam_seg0;
-    const int* lam_odd;
-    int nseg, nlam;
-    double* partial;
-    int total;
+    const int4* segs;          // per (multiplet, m3): term range, lm of a_{l3 m3}, 2 S(m3) bits
+    int nseg;
+    const int4* items;         // (first segment, end, b1 | odd << 8 | (nr - 1 - b1) << 16, first output)
+    int nitem;
+    double* partial;           // [blocks][total]
+    int total, out_off, nout;  // this order's entries: [out_off, out_off + nout)
+    int* tile_counter;         // zeroed before the launch
 };
+void launch_contract4w(const Contract4WArgs& a, int nblocks, cudaStream_t s);
+size_t contract4w_smem_bytes(const Contract4WArgs& a);
+int contract4w_blocks(int nsm, int n);
 
 // 4PCF contraction on the tensor cores (split bf16, fp32 accumulation in tensor memory).
 // Rows (multiplet, b1, b2) are grouped by (l3, parity); each group's rows form 128-row
@@ -187,12 +187,10 @@ size_t contract5_smem_bytes(const Contract5Args& a);
 size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
-void launch_contract4(const Contract4Args& a, cudaStream_t s);
-size_t contract4_smem_bytes(const Contract4Args& a);
 
 // ---------------------------------------------------------------- FP64 reduction (a6)
-// zeta[e] += scale[e] * sum_c partial[c][e]
-void launch_reduce(const double* partial, int nchunk, int total, const double* scale, double* zeta,
-                   cudaStream_t s);
+// zeta[e] += scale[e] * sum_{c < nchunk} partial[c][e] for e in [off, off + count)
+void launch_reduce(const double* partial, int nchunk, int total, int off, int count, const double* scale,
+                   double* zeta, cudaStream_t s);
 
 }  // namespace npcf

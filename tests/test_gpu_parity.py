@@ -129,6 +129,17 @@ def test_3pcf_uniform_4096_box250_full(torch_dev):
     assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
 
 
+@pytest.mark.parametrize("nr,lmax,n", [(3, 4, 1500), (13, 3, 2100), (16, 2, 901)])
+def test_4pcf_shell_counts_and_ragged_tiles(torch_dev, nr, lmax, n):
+    # the FP32 contraction specialises on the number of shells after b1 and takes
+    # primaries in tiles of 64: few and many shells, n not a multiple of the tile
+    pos, w = _catalog(n, 160.0, 900 + nr)
+    edges = np.linspace(4.0, 40.0, nr + 1)
+    _, got, _ = gpu_run(torch_dev, pos, w, (4,), lmax, edges, 160.0, allparity=True)
+    want, _ = oracle.npcf(pos, w, (4,), lmax, edges, 160.0, allparity=True)
+    assert_orders_close(got, want, (4,), lmax, nr, allparity=True)
+
+
 def test_4pcf_3pcf_periodic_lmax5_10_shells(torch_dev):
     pos = catalogs.lognormal_box(2500, 300.0, 64, seed=31)
     w = np.ones(len(pos), np.float32)
