@@ -343,7 +343,9 @@ npcf_status setup_tables(npcf_ctx* ctx) {
                 std::memcpy(&fb, &f, 4);
                 segs.push_back(make_int4(t.seg_begin[i], t.seg_end[i], t.seg_lm3[i], fb));
             }
-            // items (multiplet, b1) with at least one (b2, b3) after b1; heaviest first
+            // items (multiplet, b1) with at least one (b2, b3) after b1, ordered by the number
+            // of shells after b1 (the kernel's specialisation: warps that run at the same time
+            // share one code path in the instruction cache), heaviest first within it
             std::vector<std::pair<double, int4>> items;
             for (int a = 0; a < o.n_lambda(); ++a)
                 for (int b1 = 0; b1 + 2 < ctx->nr; ++b1) {
@@ -355,7 +357,7 @@ npcf_status setup_tables(npcf_ctx* ctx) {
                     double cost = 0;
                     for (int sg = t.lam_seg0[a]; sg < t.lam_seg0[a + 1]; ++sg)
                         cost += 10.0 * nb2 * (t.seg_end[sg] - t.seg_begin[sg]) + 2.0 * nb2 * (nb2 - 1);
-                    items.push_back({cost, make_int4(t.lam_seg0[a], t.lam_seg0[a + 1],
+                    items.push_back({1e12 * nb2 + cost, make_int4(t.lam_seg0[a], t.lam_seg0[a + 1],
                                                      b1 | ((o.odd(a) ? 1 : 0) << 8) | (nb2 << 16),
                                                      off + a * nb + first)});
                 }
