@@ -166,6 +166,27 @@ npcf_status npcf_get_timings(npcf_ctx* ctx, float* ms4);
 npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, int nr, const double* edges,
                                      double box, uint64_t* d_counts, void* stream);
 
+/* Edge correction (Sec. 3.3, Eq. edge-corrected-NPCF; Sec. 4.2). For every order and
+ * bin tuple B it solves, in FP64 on the GPU,
+ *   sum_L zeta_L(B) M_{L L''}(B) = N_{L''}(B) / R_0(B),
+ *   M_{L L''}(B) = sum_{L'} (R_{L'}(B) / R_0(B)) E(L'') G^{L L' L''},
+ * with N the raw multiplets accumulated in nctx (data weighted +1, randoms -N_D/N_R),
+ * R those accumulated in rctx (randoms only, weighted +N_D/N_R) and G the generalized
+ * Gaunt integrals of App. A (see npcf_gaunt). Both contexts must have the same lmax,
+ * orders, shells and box, be parity-even (allparity = 0; E(L'') = +1) and hold orders 3
+ * and 4 only (NPCF_EUNSUPPORTED for 5). One block per bin tuple, Gaussian elimination
+ * with partial pivoting. Writes host out[npcf_output_size] in the layout of
+ * npcf_finalize; a bin tuple whose system is singular (R_0 = 0, no pivot) gets NaN and
+ * the call returns NPCF_EINVAL. Synchronises the device. */
+npcf_status npcf_edge_correct(npcf_ctx* nctx, npcf_ctx* rctx, double* out);
+
+/* Generalized Gaunt integral G^{L1 L2 L3} = int dR P_L1 P_L2 P_L3 (Eq. generalized-gaunt-def)
+ * from the closed forms of App. A (Wigner 3-j and 9-j symbols), the values the edge
+ * correction uses. Host-only (no device work). L1, L2, L3: host int multiplets of order
+ * N = 3, 4 or 5 laid out as npcf_layout gives them ({l, l}, {l1, l2, l3},
+ * {l1, l2, l12, l3, l4}); *out receives the value. */
+npcf_status npcf_gaunt(int N, const int* L1, const int* L2, const int* L3, double* out);
+
 /* Message of the last failed call on ctx; with ctx == NULL, of the last failed
  * npcf_create or npcf_pair_counts_noalloc on this thread. */
 const char* npcf_last_error(const npcf_ctx* ctx);

@@ -35,6 +35,8 @@ SIGNATURES = {
     "npcf_set_tuning": (_i, [_vp, _i, _i]),
     "npcf_get_timings": (_i, [_vp, _vp]),
     "npcf_pair_counts_noalloc": (_i, [_vp, _i64, _i, _vp, _d, _vp, _vp]),
+    "npcf_edge_correct": (_i, [_vp, _vp, _vp]),
+    "npcf_gaunt": (_i, [_i, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
 }
@@ -67,6 +69,18 @@ def pair_counts_noalloc(pos, edges, box: float, out, stream=None):
                                       _ptr(out), _stream_handle(stream))
     if st != NPCF_OK:
         raise NPCFError(st, lib.npcf_last_error(None).decode())
+
+
+def gaunt(N: int, L1, L2, L3) -> float:
+    """Generalized Gaunt integral G^{L1 L2 L3} as the library's edge correction uses it
+    (closed forms of App. A; host-only, npcf_gaunt)."""
+    lib = load()
+    a, b, c = (np.ascontiguousarray(x, dtype=np.int32) for x in (L1, L2, L3))
+    out = ctypes.c_double()
+    st = lib.npcf_gaunt(int(N), a.ctypes.data, b.ctypes.data, c.ctypes.data, ctypes.byref(out))
+    if st != NPCF_OK:
+        raise NPCFError(st, "npcf_gaunt: bad arguments")
+    return out.value
 
 
 class NPCFError(RuntimeError):
@@ -149,6 +163,13 @@ class NPCF:
     def finalize(self, normalize: bool = False) -> np.ndarray:
         out = np.zeros(self.size, dtype=np.float64)
         self._check(self._lib.npcf_finalize(self._h, out.ctypes.data, self.size, int(normalize)))
+        return out
+
+    def edge_correct(self, randoms: "NPCF") -> np.ndarray:
+        """Edge-corrected multiplets (npcf_edge_correct): this context holds the
+        data-minus-randoms sums, ``randoms`` the randoms-only sums."""
+        out = np.zeros(self.size, dtype=np.float64)
+        self._check(self._lib.npcf_edge_correct(self._h, randoms._h, out.ctypes.data))
         return out
 
     def pair_counts(self) -> np.ndarray:

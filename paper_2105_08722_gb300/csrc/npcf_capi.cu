@@ -113,6 +113,10 @@ struct npcf_ctx {
     DevBuf<int> errflag, work;
     DevBuf<float> bbox;
     DevBuf<float> hpos_stage, hw_stage;
+    // edge correction: sparse generalized Gaunt tables per order (built on first use)
+    DevBuf<int> e_tptr[3], e_tlp[3];
+    DevBuf<double> e_tg[3], e_out;
+    bool edge_ready = false;
     int64_t last_n = 0;
     int nsm = 0;
 
@@ -854,6 +858,95 @@ npcf_status npcf_pair_counts(npcf_ctx* ctx, uint64_t* out) {
     if (check_ctx(ctx) != NPCF_OK || !out) return NPCF_EINVAL;
     CU(cudaDeviceSynchronize());
     CU(cudaMemcpy(out, ctx->counts.p, ctx->nr * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return NPCF_OK;
+}
+
+npcf_status npcf_gaunt(int N, const int* L1, const int* L2, const int* L3, double* out) {
+    if (N < 3 || N > 5 || !L1 || !L2 || !L3 || !out) return NPCF_EINVAL;
+    const int width = N == 3 ? 2 : (N == 4 ? 3 : 5);
+    for (int i = 0; i < width; ++i)
+        if (L1[i] < 0 || L2[i] < 0 || L3[i] < 0 || L1[i] > 4 * kMaxL || L2[i] > 4 * kMaxL || L3[i] > 4 * kMaxL)
+            return NPCF_EINVAL;
+    *out = generalized_gaunt(N, L1, L2, L3);
+    return NPCF_OK;
+}
+
+npcf_status npcf_edge_correct(npcf_ctx* nctx, npcf_ctx* rctx, double* out) {
+    if (check_ctx(nctx) != NPCF_OK || check_ctx(rctx) != NPCF_OK) return NPCF_EINVAL;
+    npcf_ctx* ctx = nctx;   // CUDA failures are reported on the data context
+    if (!out && nctx->total > 0) return fail(nctx, NPCF_EINVAL, "output buffer is null");
+    if (nctx->lmax != rctx->lmax || nctx->mask != rctx->mask || nctx->nr != rctx->nr ||
+        nctx->box != rctx->box || nctx->allparity != rctx->allparity || nctx->edges != rctx->edges)
+        return fail(nctx, NPCF_EINVAL, "the two contexts differ in lmax, orders, shells or box");
+    if (nctx->allparity) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction takes parity-even multiplets");
+    for (const OrderTable& o : nctx->orders)
+        if (o.N == 5) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction is built for orders 3 and 4");
+    CU(cudaDeviceSynchronize());
+    int errbits = 0, rerr = 0;
+    CU(cudaMemcpy(&errbits, nctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&rerr, rctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if ((errbits | rerr) & 3) return fail(nctx, NPCF_EINVAL, "an accumulate call of either context failed");
+    if (!nctx->edge_ready) {
+        for (size_t k = 0; k < nctx->orders.size(); ++k) {
+            const OrderTable& o = nctx->orders[k];
+            const int nl = o.n_lambda(), w = o.width;
+            // G is symmetric in its three multiplets: evaluate a <= b <= c once
+            std::vector<double> G((size_t)nl * nl * nl, 0.0);
+            for (int a = 0; a < nl; ++a)
+                for (int b = a; b < nl; ++b)
+                    for (int c = b; c < nl; ++c) {
+                        const double g = generalized_gaunt(o.N, &o.lam[(size_t)a * w], &o.lam[(size_t)b * w],
+                                                           &o.lam[(size_t)c * w]);
+                        const int p[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+                        for (const auto& q : p) G[((size_t)q[0] * nl + q[1]) * nl + q[2]] = g;
+                    }
+            // entry M[L''][L] collects (L', G^{L L' L''}) over L'
+            std::vector<int> tptr(1, 0), tlp;
+            std::vector<double> tg;
+            for (int c = 0; c < nl; ++c)
+                for (int a = 0; a < nl; ++a) {
+                    for (int b = 0; b < nl; ++b) {
+                        const double g = G[((size_t)a * nl + b) * nl + c];
+                        if (std::fabs(g) > 1e-15) { tlp.push_back(b); tg.push_back(g); }
+                    }
+                    tptr.push_back((int)tlp.size());
+                }
+            CU(upload(nctx->e_tptr[k], tptr));
+            CU(upload(nctx->e_tlp[k], tlp));
+            CU(upload(nctx->e_tg[k], tg));
+        }
+        nctx->edge_ready = true;
+    }
+    if (nctx->total == 0) return NPCF_OK;
+    CU(nctx->e_out.ensure(nctx->total));
+    CU(cudaMemset(nctx->errflag.p, 0, sizeof(int)));
+    int dev = 0, optin = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (size_t k = 0; k < nctx->orders.size(); ++k) {
+        const OrderTable& o = nctx->orders[k];
+        if (o.n_bins() == 0) continue;
+        if (edge_smem_bytes(o.n_lambda()) > (size_t)optin)
+            return fail(nctx, NPCF_EUNSUPPORTED, "edge correction: %d multiplets exceed shared memory",
+                        o.n_lambda());
+        EdgeArgs e{};
+        e.nraw = nctx->zeta.p + nctx->order_off[k];
+        e.rraw = rctx->zeta.p + rctx->order_off[k];
+        e.nl = o.n_lambda();
+        e.nb = o.n_bins();
+        e.tptr = nctx->e_tptr[k].p;
+        e.tlp = nctx->e_tlp[k].p;
+        e.tg = nctx->e_tg[k].p;
+        e.out = nctx->e_out.p + nctx->order_off[k];
+        e.err = nctx->errflag.p;
+        launch_edge_solve(e, 0);
+        CU(cudaGetLastError());
+    }
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(out, nctx->e_out.p, nctx->total * sizeof(double), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&errbits, nctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemset(nctx->errflag.p, 0, sizeof(int)));
+    if (errbits & 4) return fail(nctx, NPCF_EINVAL, "edge correction: singular system (R_0 = 0?) for some bins");
     return NPCF_OK;
 }
 

@@ -188,6 +188,20 @@ size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- edge correction (a7)
+struct EdgeArgs {
+    const double* nraw;        // [nl][nb] raw multiplets of the data-minus-randoms run
+    const double* rraw;        // [nl][nb] raw multiplets of the randoms-only run
+    int nl, nb;
+    const int* tptr;           // [nl * nl + 1] entries of M[L''][L] in the sparse table
+    const int* tlp;            // L' of each entry
+    const double* tg;          // G^{L L' L''} of each entry
+    double* out;               // [nl][nb] edge-corrected zeta
+    int* err;                  // error bits (4: a singular system)
+};
+void launch_edge_solve(const EdgeArgs& a, cudaStream_t s);
+size_t edge_smem_bytes(int nl);
+
 // ---------------------------------------------------------------- FP64 reduction (a6)
 // zeta[e] += scale[e] * sum_{c < nchunk} partial[c][e] for e in [off, off + count)
 void launch_reduce(const double* partial, int nchunk, int total, int off, int count, const double* scale,

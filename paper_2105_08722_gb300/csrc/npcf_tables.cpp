@@ -10,12 +10,12 @@ namespace npcf {
 
 namespace {
 
-// n! for n <= 63 in long double (exact to 25! and within a few ulp beyond).
+// n! for n < 160 in long double (exact to 25! and within a few ulp beyond).
 struct FactTable {
-    long double f[64];
+    long double f[160];
     FactTable() {
         f[0] = 1.0L;
-        for (int i = 1; i < 64; ++i) f[i] = f[i - 1] * (long double)i;
+        for (int i = 1; i < 160; ++i) f[i] = f[i - 1] * (long double)i;
     }
 };
 const FactTable& facts() {
@@ -49,6 +49,74 @@ double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3) {
         sum += neg1pow(t) / d;
     }
     return (double)(neg1pow(j1 - j2 - m3) * root * sum);
+}
+
+namespace {
+
+bool triangle(int a, int b, int c) { return c <= a + b && c >= std::abs(a - b); }
+
+// sqrt of the triangle coefficient (a+b-c)! (a-b+c)! (-a+b+c)! / (a+b+c+1)!
+long double tri_root(int a, int b, int c) {
+    const long double* f = facts().f;
+    return std::sqrt(f[a + b - c] * f[a - b + c] * f[-a + b + c] / f[a + b + c + 1]);
+}
+
+}  // namespace
+
+double wigner6j(int j1, int j2, int j3, int j4, int j5, int j6) {
+    if (!triangle(j1, j2, j3) || !triangle(j1, j5, j6) || !triangle(j4, j2, j6) || !triangle(j4, j5, j3))
+        return 0.0;
+    const long double* f = facts().f;
+    const int a1 = j1 + j2 + j3, a2 = j1 + j5 + j6, a3 = j4 + j2 + j6, a4 = j4 + j5 + j3;
+    const int b1 = j1 + j2 + j4 + j5, b2 = j2 + j3 + j5 + j6, b3 = j3 + j1 + j6 + j4;
+    const int lo = std::max({a1, a2, a3, a4}), hi = std::min({b1, b2, b3});
+    long double sum = 0.0L;
+    for (int t = lo; t <= hi; ++t)
+        sum += neg1pow(t) * f[t + 1] /
+               (f[t - a1] * f[t - a2] * f[t - a3] * f[t - a4] * f[b1 - t] * f[b2 - t] * f[b3 - t]);
+    return (double)(tri_root(j1, j2, j3) * tri_root(j1, j5, j6) * tri_root(j4, j2, j6) * tri_root(j4, j5, j3) *
+                    sum);
+}
+
+double wigner9j(int j1, int j2, int j3, int j4, int j5, int j6, int j7, int j8, int j9) {
+    // sum over x of (2x+1) {j1 j4 j7; j8 j9 x} {j2 j5 j8; j4 x j6} {j3 j6 j9; x j1 j2}
+    const int lo = std::max({std::abs(j1 - j9), std::abs(j4 - j8), std::abs(j2 - j6)});
+    const int hi = std::min({j1 + j9, j4 + j8, j2 + j6});
+    double sum = 0.0;
+    for (int x = lo; x <= hi; ++x)
+        sum += (2.0 * x + 1.0) * wigner6j(j1, j4, j7, j8, j9, x) * wigner6j(j2, j5, j8, j4, x, j6) *
+               wigner6j(j3, j6, j9, x, j1, j2);
+    return sum;
+}
+
+double generalized_gaunt(int N, const int* L1, const int* L2, const int* L3) {
+    const double fourpi = 4.0 * 3.14159265358979323846;
+    // one factor per principal angular momentum: sqrt((2l+1)(2l'+1)(2l''+1)) (l l' l''; 0 0 0)
+    auto leg = [](int a, int b, int c) {
+        return std::sqrt((2.0 * a + 1.0) * (2.0 * b + 1.0) * (2.0 * c + 1.0)) * wigner3j(a, b, c, 0, 0, 0);
+    };
+    if (N == 3) {
+        const double t = wigner3j(L1[0], L2[0], L3[0], 0, 0, 0);
+        return std::sqrt((2.0 * L1[0] + 1.0) * (2.0 * L2[0] + 1.0) * (2.0 * L3[0] + 1.0)) * t * t / fourpi;
+    }
+    if (N == 4) {
+        double p = 1.0;
+        for (int i = 0; i < 3; ++i) p *= leg(L1[i], L2[i], L3[i]);
+        if (p == 0.0) return 0.0;
+        return p * std::pow(fourpi, -1.5) *
+               wigner9j(L1[0], L2[0], L3[0], L1[1], L2[1], L3[1], L1[2], L2[2], L3[2]);
+    }
+    if (N == 5) {
+        // multiplets (l1, l2, l12, l3, l4)
+        double p = 1.0;
+        for (int i : {0, 1, 3, 4}) p *= leg(L1[i], L2[i], L3[i]);
+        if (p == 0.0) return 0.0;
+        p *= std::sqrt((2.0 * L1[2] + 1.0) * (2.0 * L2[2] + 1.0) * (2.0 * L3[2] + 1.0));
+        return p / (fourpi * fourpi) *
+               wigner9j(L1[0], L1[1], L1[2], L2[0], L2[1], L2[2], L3[0], L3[1], L3[2]) *
+               wigner9j(L1[2], L1[3], L1[4], L2[2], L2[3], L2[4], L3[2], L3[3], L3[4]);
+    }
+    return 0.0;
 }
 
 bool OrderTable::odd(int a) const {

@@ -14,6 +14,16 @@ constexpr int kMaxNr = 16;   // largest number of radial shells
 // Wigner 3-j symbol (Racah's closed form, DLMF 34.2.4).
 double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
 
+// Wigner 6-j symbol (Racah's single-sum form, DLMF 34.4.3) and 9-j symbol (sum over
+// products of three 6-j symbols, DLMF 34.6.2), integer arguments.
+double wigner6j(int j1, int j2, int j3, int j4, int j5, int j6);
+double wigner9j(int j1, int j2, int j3, int j4, int j5, int j6, int j7, int j8, int j9);
+
+// Generalized Gaunt integral G^{L L' L''} = int dR P_L P_L' P_L'' of Eq. (generalized-
+// gaunt-def), from the closed forms of App. A for N = 3, 4, 5 (multiplets laid out as in
+// OrderTable: (l, l), (l1, l2, l3), (l1, l2, l12, l3, l4)); 0 for other N.
+double generalized_gaunt(int N, const int* L1, const int* L2, const int* L3);
+
 // Number of complex slots per shell in the a_lm layout: l <= lmax, 0 <= m <= l.
 inline int nlm(int lmax) { return (lmax + 1) * (lmax + 2) / 2; }
 inline int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }

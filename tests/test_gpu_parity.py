@@ -357,3 +357,81 @@ def test_lognormal_100k_5pcf_lmax4_sampled_primaries(torch_dev):
     _, got, _ = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wp)
     want, _ = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample)
     assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
+
+
+# ------------------------------------------------------------------ edge correction (a7)
+
+def _ball_catalogs(seed, n_data=900, n_rand=3600, radius=55.0):
+    """Data clustered inside a ball, uniform randoms in the same ball (non-periodic)."""
+    rng = np.random.default_rng(seed)
+    centre = np.array([60.0, 60.0, 60.0])
+
+    def in_ball(p):
+        return np.sum((p - centre) ** 2, axis=1) < radius ** 2
+
+    r = rng.uniform(centre - radius, centre + radius, size=(4 * n_rand, 3))
+    r = r[in_ball(r)][:n_rand]
+    d = catalogs.lognormal_box(4 * n_data, 120.0, 32, seed=seed).astype(np.float64)
+    d = d[in_ball(d)][:n_data]
+    ratio = len(d) / len(r)
+    pos = np.concatenate([d, r]).astype(np.float32)
+    w = np.concatenate([np.ones(len(d)), np.full(len(r), -ratio)]).astype(np.float32)
+    return pos, w, r.astype(np.float32), np.full(len(r), ratio, np.float32)
+
+
+def _edge_contexts(torch_dev, pos, w, rpos, rw, lmax, edges):
+    nctx, nraw, _ = gpu_run(torch_dev, pos, w, (3, 4), lmax, edges, 0.0)
+    rctx, rraw, _ = gpu_run(torch_dev, rpos, rw, (3, 4), lmax, edges, 0.0)
+    return nctx, rctx, nraw, rraw
+
+
+def test_edge_correction_solve_matches_oracle_on_the_same_raw_multiplets(torch_dev):
+    # the FP64 solve alone: the oracle corrects the GPU's own raw N and R
+    pos, w, rpos, rw = _ball_catalogs(71)
+    lmax, edges = 3, np.linspace(5.0, 30.0, 6)
+    nr = len(edges) - 1
+    nctx, rctx, nraw, rraw = _edge_contexts(torch_dev, pos, w, rpos, rw, lmax, edges)
+    got = oracle.split_orders(nctx.edge_correct(rctx), (3, 4), lmax, nr)
+    n = oracle.split_orders(nraw, (3, 4), lmax, nr)
+    r = oracle.split_orders(rraw, (3, 4), lmax, nr)
+    for N in (3, 4):
+        want = oracle.edge_correct(N, lmax, nr, n[N], r[N])
+        scale = np.sqrt(np.mean(want ** 2))
+        assert np.max(np.abs(got[N] - want)) <= 1e-10 * scale, N
+
+
+def test_edge_correction_end_to_end_against_oracle(torch_dev):
+    # GPU raw sums + GPU solve against oracle raw sums + oracle solve. The raw sums agree
+    # to the FP32 tolerance; the solve can amplify that by the condition number of M,
+    # so the bound here is 100 times the FP32 bar.
+    pos, w, rpos, rw = _ball_catalogs(72)
+    lmax, edges = 3, np.linspace(5.0, 30.0, 6)
+    nr = len(edges) - 1
+    nctx, rctx, _, _ = _edge_contexts(torch_dev, pos, w, rpos, rw, lmax, edges)
+    got = oracle.split_orders(nctx.edge_correct(rctx), (3, 4), lmax, nr)
+    nraw, _ = oracle.npcf(pos, w, (3, 4), lmax, edges, 0.0)
+    rraw, _ = oracle.npcf(rpos, rw, (3, 4), lmax, edges, 0.0)
+    n = oracle.split_orders(nraw, (3, 4), lmax, nr)
+    r = oracle.split_orders(rraw, (3, 4), lmax, nr)
+    for N in (3, 4):
+        want = oracle.edge_correct(N, lmax, nr, n[N], r[N])
+        scale = np.sqrt(np.mean(want ** 2))
+        err = np.max(np.abs(got[N] - want)) / scale
+        assert err <= 100 * TOL_FP32, (N, err)
+
+
+def test_edge_correction_rejects_mismatched_or_unsupported_contexts(torch_dev):
+    from paper_2105_08722_gb300._lib import NPCF, NPCFError
+    edges = np.linspace(5.0, 30.0, 6)
+    a = NPCF(3, (3, 4), edges, 0.0)
+    b = NPCF(2, (3, 4), edges, 0.0)
+    with pytest.raises(NPCFError):
+        a.edge_correct(b)
+    c = NPCF(3, (3, 4), edges, 0.0, 0, True)
+    with pytest.raises(NPCFError):
+        c.edge_correct(c)
+    d = NPCF(2, (5,), edges, 0.0)
+    with pytest.raises(NPCFError):
+        d.edge_correct(d)
+    for x in (a, b, c, d):
+        x.close()

@@ -67,3 +67,32 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.npcf_create(ctypes.byref(h), 3, 8, 3, None, 0.0, 0, 0) == NPCF_EINVAL
     assert h.value is None
     assert b"edges" in lib.npcf_last_error(None)
+
+
+@pytest.mark.parametrize("N,lmax", [(3, 6), (4, 2), (5, 1)])
+def test_library_gaunt_closed_forms_match_the_oracle_definition(lib, N, lmax):
+    # npcf_gaunt evaluates the App. A closed forms (3-j and 9-j symbols, host code of
+    # the library); the oracle integrates Eq. (generalized-gaunt-def) through its dense
+    # coupling coefficients. Every triple of multiplets at small lmax.
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import oracle
+    from paper_2105_08722_gb300 import _lib
+    oracle.build()
+    width = {3: 2, 4: 3, 5: 5}[N]
+    lam = np.asarray(oracle.multiplets(N, lmax, False)).reshape(-1, width)
+    nonzero = 0
+    for a in lam:
+        for b in lam:
+            for c in lam:
+                got = _lib.gaunt(N, a, b, c)
+                want = oracle.gaunt(N, a, b, c)
+                assert got == pytest.approx(want, abs=1e-13), (a, b, c)
+                nonzero += abs(want) > 1e-12
+    assert nonzero > len(lam)
+
+
+def test_gaunt_rejects_bad_order(lib):
+    from paper_2105_08722_gb300 import _lib
+    with pytest.raises(_lib.NPCFError):
+        _lib.gaunt(6, [0] * 5, [0] * 5, [0] * 5)
