@@ -193,6 +193,24 @@ def c3_survey(n_data: int = 400_000, n_rand: int = 1_600_000, mesh: int = 256):
     return dr, rr
 
 
+def c3_subset(dr: "Workload", rr: "Workload", n_data: int = 4000, n_rand: int = 16000,
+              seed: int = 3003):
+    """Seeded subset of the survey catalogs (n_data data points, n_rand randoms), with the
+    randoms re-weighted to -n_data/n_rand (D-R) and +n_data/n_rand (R only)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nd = int(np.sum(dr.w > 0))
+    di = np.sort(rng.choice(nd, n_data, replace=False))
+    ri = np.sort(rng.choice(len(rr.pos), n_rand, replace=False))
+    ratio = n_data / n_rand
+    pos = np.concatenate([dr.pos[di], rr.pos[ri]])
+    w = np.concatenate([np.ones(n_data, np.float32), np.full(n_rand, -ratio, np.float32)])
+    sub_dr = Workload(dr.name + "_subset%dk" % ((n_data + n_rand) // 1000), pos, w, dr.edges, dr.lmax,
+                      dr.orders, 0.0)
+    sub_rr = Workload(rr.name + "_subset%dk" % (n_rand // 1000), rr.pos[ri],
+                      np.full(n_rand, ratio, np.float32), rr.edges, rr.lmax, rr.orders, 0.0)
+    return sub_dr, sub_rr
+
+
 def c5_batch_sizes(ncat: int = 64) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(5000))
     return np.round(np.exp(rng.uniform(math.log(2e4), math.log(3e5), size=ncat))).astype(np.int64)

@@ -435,3 +435,47 @@ def test_edge_correction_rejects_mismatched_or_unsupported_contexts(torch_dev):
         d.edge_correct(d)
     for x in (a, b, c, d):
         x.close()
+
+
+# ------------------------------------------------------------------ survey geometry (D - R)
+
+@pytest.fixture(scope="module")
+def survey():
+    return catalogs.c3_survey()
+
+
+def test_survey_subset_dmr_multiplets_and_edge_correction(torch_dev, survey):
+    # the seeded 20k subset (4k data, 16k randoms) of the 400k + 1.6M survey catalogs:
+    # raw D - R and R multiplets, then the edge-corrected ones, against the oracle
+    dr, rr = catalogs.c3_subset(*survey)
+    nr = len(dr.edges) - 1
+    nctx, nraw, ncnt = gpu_run(torch_dev, dr.pos, dr.w, dr.orders, dr.lmax, dr.edges, 0.0)
+    rctx, rraw, _ = gpu_run(torch_dev, rr.pos, rr.w, rr.orders, rr.lmax, rr.edges, 0.0)
+    onraw, ocnt = oracle.npcf(dr.pos, dr.w, dr.orders, dr.lmax, dr.edges, 0.0)
+    orraw, _ = oracle.npcf(rr.pos, rr.w, rr.orders, rr.lmax, rr.edges, 0.0)
+    assert np.array_equal(ncnt, ocnt)
+    assert_orders_close(nraw, onraw, dr.orders, dr.lmax, nr)
+    assert_orders_close(rraw, orraw, rr.orders, rr.lmax, nr)
+    got = oracle.split_orders(nctx.edge_correct(rctx), dr.orders, dr.lmax, nr)
+    n = oracle.split_orders(onraw, dr.orders, dr.lmax, nr)
+    r = oracle.split_orders(orraw, dr.orders, dr.lmax, nr)
+    for N in dr.orders:
+        want = oracle.edge_correct(N, dr.lmax, nr, n[N], r[N])
+        err = np.max(np.abs(got[N] - want)) / np.sqrt(np.mean(want ** 2))
+        assert err <= 100 * TOL_FP32, (N, err)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_survey_full_dmr_sampled_primaries(torch_dev, survey, prec):
+    # the full 2M-point D - R catalog; 24 seeded primaries (data and randoms) summed
+    # against every secondary, FP32 and split-bf16 contractions
+    dr, _ = survey
+    rng = np.random.default_rng(3004)
+    sample = np.sort(np.concatenate([rng.choice(400_000, 8, replace=False),
+                                     400_000 + rng.choice(1_600_000, 16, replace=False)]))
+    wp = np.zeros(dr.n, np.float32)
+    wp[sample] = dr.w[sample]
+    _, got, _ = gpu_run(torch_dev, dr.pos, dr.w, dr.orders, dr.lmax, dr.edges, 0.0, wprim=wp, prec=prec)
+    want, _ = oracle.npcf(dr.pos, dr.w, dr.orders, dr.lmax, dr.edges, 0.0, prim=sample)
+    assert_orders_close(got, want, dr.orders, dr.lmax, len(dr.edges) - 1,
+                        tol=TOL_FP32 if prec == 0 else TOL_BF16)
