@@ -139,7 +139,8 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
  * more neighbours read them from global memory instead), key 5 = x-adjacent cells
  * per pair-kernel work unit (1..4), key 6 = split-bf16 contraction: steps of 16 primaries
  * between drains of the tensor-memory accumulators into FP64 (>= 1; fewer steps bound the
- * accumulation error of the tensor cores more tightly). */
+ * accumulation error of the tensor cores more tightly), key 7 = pair kernel: cut each staged
+ * row of neighbour cells to the primary's x-window (1, default) or scan whole rows (0). */
 npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);
 
 /* Device time in ms of the stages of the last accumulate call:

@@ -3,8 +3,10 @@
 // placed on a Cartesian grid before the pair search).
 //
 // Stages: per-point cell id + histogram -> exclusive scan -> scatter into cell order
-// as float4 (x, y, z, w) -> per-cell reorder by input index so the sorted order, and
-// every sum that follows it, is deterministic.
+// as float4 (x, y, z, w) -> per-cell sort by (x, input index). The order is
+// deterministic, so every sum that follows it is too, and a run of x-adjacent cells is
+// sorted by x as a whole, which lets the pair kernel cut each row of neighbour cells to
+// the x-window of one primary by binary search.
 #include "npcf_device.h"
 
 #include <cfloat>
@@ -112,18 +114,25 @@ __global__ void k_scatter(BinArgs a) {
     a.cell_of[k] = c;
 }
 
-// Order each cell's members by input index (insertion sort; cells hold tens of points).
+// Order each cell's members by (x, input index) (insertion sort; cells hold tens of
+// points). Cells above the bound stay in scatter order and flag error bit 8, which turns
+// the pair kernel's x-window cut off.
 __global__ void k_cell_order(BinArgs a) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.g.ncell) return;
     uint32_t s0 = a.start[c], s1 = a.start[c + 1];
-    if (s1 - s0 > 4096u) return;  // keep the quadratic sort bounded; order then follows the scatter
+    if (s1 - s0 > 4096u) {  // keep the quadratic sort bounded
+        atomicOr(a.err, 8);
+        return;
+    }
     for (uint32_t k = s0 + 1; k < s1; ++k) {
         uint32_t key = a.idx[k];
         float4 p = a.pts[k];
         float u = a.wp[k];
         uint32_t j = k;
-        while (j > s0 && a.idx[j - 1] > key) {
+        while (j > s0) {
+            const float xj = a.pts[j - 1].x;
+            if (!(xj > p.x || (xj == p.x && a.idx[j - 1] > key))) break;
             a.idx[j] = a.idx[j - 1];
             a.pts[j] = a.pts[j - 1];
             a.wp[j] = a.wp[j - 1];

@@ -71,6 +71,7 @@ struct npcf_ctx {
     int pair_cap = 4096;       // per group of the pair kernel
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int drain_steps = 2;       // tensor-core contraction: steps of 16 primaries per TMEM drain
+    int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -541,6 +542,15 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         pa.linear = lin ? 1 : 0;
         pa.lin_r0 = (float)r0;
         pa.lin_inv_w = lin ? (float)(1.0 / w) : 0.f;
+        // x-window cut of the staged rows: row cells are packed in 13 bits per axis
+        const double cell = 1.0 / (double)g.inv_cell;
+        double M = 0.0;
+        const double o[3] = {g.ox, g.oy, g.oz};
+        const int dims[3] = {g.gx, g.gy, g.gz};
+        for (int q = 0; q < 3; ++q) M = std::max({M, std::fabs(o[q]), std::fabs(o[q] + dims[q] * cell)});
+        pa.cell = (float)cell;
+        pa.trim_margin = (float)std::max(cell * 1e-3, M * 4e-6);
+        pa.trim = (ctx->trim && g.gy < 8192 && g.gz < 8192) ? 1 : 0;
     }
     {
         int dev = 0, optin = 0;
@@ -1009,6 +1019,10 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
         case 6:
             if (value < 1) return fail(ctx, NPCF_EINVAL, "drain interval must be >= 1");
             ctx->drain_steps = value;
+            return NPCF_OK;
+        case 7:
+            if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "x-window cut is 0 or 1");
+            ctx->trim = value;
             return NPCF_OK;
         default:
             return fail(ctx, NPCF_EINVAL, "unknown tuning key %d", key);

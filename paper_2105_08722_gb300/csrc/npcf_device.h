@@ -71,6 +71,9 @@ struct PairArgs {
     int run;                   // cells per work unit (x-adjacent)
     int linear;                // edges are linear in r: shell estimated from sqrt(r2)
     float lin_r0, lin_inv_w;   // first edge and 1 / shell width of linear edges
+    int trim;                  // cut staged rows to each primary's x-window (cells sorted by x)
+    float cell;                // cell side of the grid
+    float trim_margin;         // slack of the cut (covers FP32 rounding of the cell bounds)
 };
 
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s);

@@ -124,8 +124,9 @@ __device__ __forceinline__ int pair_shell(const float4 pj, const float4 pi, floa
 }
 
 // The neighbour rows of a run of cells (x-adjacent, same y and z) as segments of the
-// cell-sorted point array: (global start, count, offset in the staging buffer, shift code
-// 2 bits per axis). Computed by one warp; the totals go to shared memory.
+// cell-sorted point array: (global start, count, offset in the staging buffer, code).
+// code bits 0-5: periodic shift, 2 bits per axis; bits 6-18: the row's y cell; bits 19-31:
+// its z cell. Computed by one warp; the totals go to shared memory.
 __device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int cy, int cz, int run,
                                int4* segs, int* out_nseg, int* out_total, int lane) {
     const GridInfo& g = a.g;
@@ -145,6 +146,7 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int 
             }
             if (ok) {
                 const int base = (zz * g.gy + yy) * g.gx;
+                cyz |= (yy << 6) | (zz << 19);   // the row's cell (y, z) rides along for the x-window cut
                 int x0 = cx + rw.z, x1 = cx + run - 1 + rw.w;
                 if (g.periodic) {
                     if (x0 < 0) {
@@ -197,7 +199,7 @@ constexpr int kShiftCodes = 64;   // 2 bits per axis
 // Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
 // cap is the neighbour-list capacity of one group in 16-bit entries.
 struct PairLayout {
-    size_t cand, scode, segs, rows, ulist, slist, ushell, part, total;
+    size_t cand, scode, segs, rows, tpref, tdelta, tcode, ulist, slist, ushell, part, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -208,7 +210,11 @@ __host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int c
     l.scode = align16(l.cand + (size_t)cand_cap * 16);
     l.segs = align16(l.scode + (size_t)cand_cap);
     l.rows = align16(l.segs + (size_t)2 * nrows * 16);
-    l.ulist = align16(l.rows + (size_t)nrows * 16);
+    // per group: flat-index prefix, staging offset minus prefix, and shift code of each row
+    l.tpref = align16(l.rows + (size_t)nrows * 16);
+    l.tdelta = align16(l.tpref + (size_t)kG * (2 * nrows + 1) * 4);
+    l.tcode = align16(l.tdelta + (size_t)kG * 2 * nrows * 4);
+    l.ulist = align16(l.tcode + (size_t)kG * 2 * nrows * 4);
     l.slist = align16(l.ulist + (size_t)kG * cap * 2);
     l.ushell = align16(l.slist + (size_t)kG * cap * 2);
     l.part = align16(l.ushell + (size_t)kG * cap);
@@ -223,6 +229,7 @@ struct GroupShared {
     uint32_t off[kMaxNr + 1];      // shell offsets of the sorted slice
     uint32_t tot[kMaxNr];          // shell totals of the current primary
     int done[kW];
+    int wtot[kW];                  // per-warp sums of the row-trimming prefix
 };
 
 template <int L>
@@ -245,9 +252,90 @@ __device__ __forceinline__ void group_sync(int grp) {
 // kW equal chunks whose per-shell sums go to per-warp partials; the partials give a_lm
 // at the end. Sub-lists that fill up end the slice early, and the scan resumes where it
 // stopped.
+// First index in [0, n) of the staged row at 'base' whose x is >= v (upper: > v).
+template <bool UPPER>
+__device__ __forceinline__ int x_bound(const float4* cand, int base, int n, float v) {
+    int lo = 0;
+    while (n > 0) {
+        const int half = n >> 1;
+        const float x = cand[base + lo + half].x;
+        if (UPPER ? !(x > v) : (x < v)) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// The part of every staged row this primary can reach, as one flat index space:
+// row s covers flat [tpref[s], tpref[s+1]) and staged index = flat + tdelta[s]. With
+// trim, a row keeps only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus a
+// margin) of the primary, d_yz the distance from the primary to the row's (y, z) cell
+// square; the exact FP32 rule is applied to what remains. Rows are sorted by x (cells
+// in x order, members sorted by x). Returns the flat total.
+template <int L>
+__device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>& sh, const float4* cand,
+                                         const int4* segs, int nseg, const float4 pi, int* tpref, int* tdelta,
+                                         int* tcode, int* wtot, bool trim, int grp, int warp, int lane) {
+    const int gt = warp * 32 + lane;
+    const int per = (nseg + kW * 32 - 1) / (kW * 32);   // rows per thread
+    const int s0 = min(nseg, gt * per), s1 = min(nseg, s0 + per);
+    const float R2 = sh.e2[a.nr], m = a.trim_margin, c = a.cell;
+    int cnt_local = 0;
+    for (int s = s0; s < s1; ++s) {
+        const int4 sg = segs[s];
+        int lo = 0, hi = sg.y;
+        if (trim) {
+            const float4 sf = sh.shift[sg.w & 63];
+            const int yy = (sg.w >> 6) & 8191, zz = (int)((unsigned)sg.w >> 19);
+            const float ylo = a.g.oy + (float)yy * c - sf.y - m, yhi = ylo + c + 2.f * m;
+            const float zlo = a.g.oz + (float)zz * c - sf.z - m, zhi = zlo + c + 2.f * m;
+            const float dy = fmaxf(0.f, fmaxf(ylo - pi.y, pi.y - yhi));
+            const float dz = fmaxf(0.f, fmaxf(zlo - pi.z, pi.z - zhi));
+            const float d2 = dy * dy + dz * dz;
+            if (d2 >= R2 * (1.f + 1e-5f)) {
+                hi = 0;
+            } else {
+                const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
+                const float xc = pi.x + sf.x;
+                lo = x_bound<false>(cand, sg.z, sg.y, xc - h);
+                hi = x_bound<true>(cand, sg.z, sg.y, xc + h);
+            }
+        }
+        tdelta[s] = sg.z + lo;                    // minus the prefix below
+        tcode[s] = (sg.w & 63) | ((hi - lo) << 8);  // the count rides along until then
+        cnt_local += hi - lo;
+    }
+    // exclusive prefix of the counts over the group's threads
+    int incl = cnt_local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    group_sync(grp);
+    int base = incl - cnt_local;
+    for (int w = 0; w < warp; ++w) base += wtot[w];
+    int total = 0;
+    for (int w = 0; w < kW; ++w) total += wtot[w];
+    for (int s = s0; s < s1; ++s) {
+        const int cs = tcode[s] >> 8;
+        tcode[s] &= 63;
+        tpref[s] = base;
+        tdelta[s] -= base;
+        base += cs;
+    }
+    if (gt == 0) tpref[nseg] = total;
+    group_sync(grp);
+    return total;
+}
+
 template <int L, bool STAGED>
 __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
                                             const uint8_t* scode, const int4* segs, int nseg, int total,
+                                            int* tpref, int* tdelta, int* tcode, bool trim,
                                             uint16_t* ulist, uint16_t* slist, uint8_t* ushell, float* part,
                                             int p, int grp, int warp, int lane, const int* slot_org) {
     constexpr int NC = ncomp(L);
@@ -274,39 +362,72 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     uint32_t* ul32 = reinterpret_cast<uint32_t*>(ul16);
     uint8_t* us = ushell + (size_t)warp * (a.cap / kW);
     uint32_t* sl32 = reinterpret_cast<uint32_t*>(slist);
-    const int per = (total + kW - 1) / kW;
-    int cursor = STAGED ? min(total, warp * per) : 0;
-    const int kend = STAGED ? min(total, cursor + per) : 0;
+    // staged: the rows cut to this primary's x-window, one flat index space split evenly
+    const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, pi, tpref, tdelta, tcode, G.wtot, trim, grp,
+                                        warp, lane)
+                         : total;
+    const int per = (T + kW - 1) / kW;
+    int cursor = STAGED ? min(T, warp * per) : 0;
+    const int kend = STAGED ? min(T, cursor + per) : 0;
     int seg = warp, segpos = 0;   // global-memory path: segments warp, warp + kW, ...
     const unsigned lt = (1u << lane) - 1u;
+    // staged: the row of flat index cursor + lane (first s with tpref[s + 1] > it), its end,
+    // its staged offset and its periodic shift
+    int srow = 0, snext = 0, sdelta = 0;
+    float4 ssf = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (STAGED && cursor + lane < kend) {
+        const int k0 = cursor + lane;
+        int lo = 0, n = nseg;
+        while (n > 0) {
+            const int half = n >> 1;
+            if (tpref[lo + half + 1] <= k0) {
+                lo += half + 1;
+                n -= half + 1;
+            } else {
+                n = half;
+            }
+        }
+        srow = lo;
+        snext = tpref[srow + 1];
+        sdelta = tdelta[srow];
+        ssf = sh.shift[tcode[srow]];
+    }
     group_sync(grp);   // partials zeroed before any warp adds to them
 
     for (;;) {
         // ---- scan: append accepted neighbours while the sub-list has room
         int cw = 0;
         if (STAGED) {
-            const int iters = min((kend - cursor + 31) / 32, capw / 32);
-#pragma unroll 2
-            for (int it = 0; it < iters; ++it) {
-                const int k = cursor + it * 32 + lane;
-                int b = -1;
+            // batches of 32 candidates while a whole batch still fits in the sub-list
+            while (cw + 32 <= capw && cursor < kend) {
+                const int k = cursor + lane;
+                int b = -1, q = 0;
                 if (k < kend) {
-                    const float4 sf = sh.shift[scode[k]];
-                    b = pair_shell(cand[k], pi, sf.x, sf.y, sf.z, sh.e2, nr, a.linear, a.lin_r0, a.lin_inv_w);
+                    if (k >= snext) {
+                        do {
+                            ++srow;
+                            snext = tpref[srow + 1];
+                        } while (k >= snext);
+                        sdelta = tdelta[srow];
+                        ssf = sh.shift[tcode[srow]];
+                    }
+                    q = k + sdelta;
+                    b = pair_shell(cand[q], pi, ssf.x, ssf.y, ssf.z, sh.e2, nr, a.linear, a.lin_r0, a.lin_inv_w);
                 }
                 const unsigned m = __ballot_sync(kFull, b >= 0);
                 if (b >= 0) {
                     const int pos = cw + __popc(m & lt);
-                    ul16[pos] = (uint16_t)k;
+                    ul16[pos] = (uint16_t)q;
                     us[pos] = (uint8_t)b;
                 }
                 cw += __popc(m);
+                cursor += 32;
             }
-            cursor = min(kend, cursor + iters * 32);
+            cursor = min(cursor, kend);
         } else {
             while (seg < nseg && cw + 32 <= capw) {
                 const int4 sg = segs[seg];
-                const float4 sf = sh.shift[sg.w];
+                const float4 sf = sh.shift[sg.w & 63];
                 const int k = segpos + lane;
                 int b = -1;
                 if (k < sg.y)
@@ -486,6 +607,11 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist) + (size_t)grp * a.cap;
     uint8_t* ushell = dsm + lay.ushell + (size_t)grp * a.cap;
     float* part = reinterpret_cast<float*>(dsm + lay.part) + (size_t)grp * kW * a.nr * ncomp(L);
+    int* tpref = reinterpret_cast<int*>(dsm + lay.tpref) + (size_t)grp * (2 * a.nrows + 1);
+    int* tdelta = reinterpret_cast<int*>(dsm + lay.tdelta) + (size_t)grp * 2 * a.nrows;
+    int* tcode = reinterpret_cast<int*>(dsm + lay.tcode) + (size_t)grp * 2 * a.nrows;
+    // the x-window cut needs every cell sorted by x (binning flags bit 8 otherwise)
+    const bool trim = a.trim != 0 && (*(volatile int*)a.err & 8) == 0;
     int slot_org[R::F];
 #pragma unroll
     for (int i = 0; i < R::F; ++i) slot_org[i] = R::origin(i, lane);
@@ -531,7 +657,7 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
             // periodic shift code of every staged point
             for (int s = wblk; s < nseg; s += kG * kW) {
                 const int4 sg = segs[s];
-                for (int k = lane; k < sg.y; k += 32) scode[sg.z + k] = (uint8_t)sg.w;
+                for (int k = lane; k < sg.y; k += 32) scode[sg.z + k] = (uint8_t)(sg.w & 63);
             }
             const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
             // the whole block leaves together if any thread's wait gave up
@@ -544,11 +670,11 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
         }
         for (int p = pbeg + grp; p < pend; p += kG) {
             if (staged)
-                one_primary<L, true>(a, sh, cand, scode, segs, nseg, total, ulist, slist, ushell, part, p,
-                                     grp, warp, lane, slot_org);
+                one_primary<L, true>(a, sh, cand, scode, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
+                                     slist, ushell, part, p, grp, warp, lane, slot_org);
             else
-                one_primary<L, false>(a, sh, cand, scode, segs, nseg, total, ulist, slist, ushell, part, p,
-                                      grp, warp, lane, slot_org);
+                one_primary<L, false>(a, sh, cand, scode, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
+                                      slist, ushell, part, p, grp, warp, lane, slot_org);
         }
         __syncthreads();   // both groups are done with the staged points of this unit
     }

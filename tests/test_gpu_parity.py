@@ -77,6 +77,25 @@ def test_pair_counts_bit_exact(torch_dev, n, box, edges):
         est.close()
 
 
+@pytest.mark.parametrize("box", [0.0, 220.0])
+def test_x_window_cut_keeps_every_neighbour(torch_dev, box):
+    # the pair kernel cuts staged rows to each primary's x-window; with the cut on or off,
+    # for several cell sizes, the neighbour sets (hence counts) must be the same
+    pos = catalogs.lognormal_box(6000, 220.0, 32, seed=77)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(3.0, 40.0, 9)
+    want = oracle.pair_counts(pos, edges, box)
+    ref = None
+    for k in (1, 3, 5):
+        for t in (0, 1):
+            _, z, counts = gpu_run(torch_dev, pos, w, (3,), 4, edges, box, tuning={0: k, 7: t})
+            assert np.array_equal(counts, want), (k, t)
+            if ref is None:
+                ref = z
+            scale = np.sqrt(np.mean(ref ** 2))
+            assert np.max(np.abs(z - ref)) <= 1e-5 * scale, (k, t)
+
+
 def test_pair_counts_on_exact_edges_and_duplicates(torch_dev):
     # secondaries placed at exactly representable distances equal to the shell edges,
     # coincident points and points at |d| = L/2 in a periodic box
