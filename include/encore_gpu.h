@@ -133,7 +133,7 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
 /* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8; the cell
  * side of the neighbour grid is about r_max / key0), key 2 = contraction primaries
  * per chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per block
- * (multiple of 256 in 512..16384 entries; larger lists mean fewer slices for dense
+ * (multiple of 256 in 1024..16384 entries; larger lists mean fewer slices for dense
  * primaries, smaller ones leave more shared memory for staging), key 4 = cap on the
  * neighbour points staged in shared memory per cell (0 = as many as fit; cells with
  * more neighbours read them from global memory instead), key 5 = x-adjacent cells

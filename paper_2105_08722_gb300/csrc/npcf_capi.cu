@@ -67,8 +67,8 @@ struct npcf_ctx {
 
     // cell-list tuning and geometry
     int cells_per_rmax = 5;
-    int cell_run = 2;          // x-adjacent cells per pair-kernel work unit
-    int pair_cap = 4096;       // per group of the pair kernel
+    int cell_run = 3;          // x-adjacent cells per pair-kernel work unit
+    int pair_cap = 6144;       // per group of the pair kernel
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int drain_steps = 2;       // tensor-core contraction: steps of 16 primaries per TMEM drain
     int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
@@ -466,6 +466,9 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", (long long)n64);
     if (n64 == 0) return NPCF_OK;
     if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+    if (n64 >= (int64_t(1) << 28))
+        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^28 points per call",
+                    (long long)n64);
     const int n = (int)n64;
     npcf_status st = setup_grid(ctx, d_pos, n, s);
     if (st != NPCF_OK) return st;
@@ -536,7 +539,8 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         if (g.periodic) pa.run = std::max(1, std::min(pa.run, g.gx - 2 * reach));
         // linear shell edges allow a direct shell estimate (corrected exactly on the device)
         const double r0 = ctx->edges[0], w = (ctx->edges[ctx->nr] - r0) / ctx->nr;
-        bool lin = w > 0;
+        // (shells narrower than 1e-3 r_max take the binary search)
+        bool lin = w >= 1e-3 * ctx->edges[ctx->nr];
         for (int i = 0; i <= ctx->nr && lin; ++i)
             lin = std::fabs(ctx->edges[i] - (r0 + i * w)) <= 1e-9 * ctx->edges[ctx->nr];
         pa.linear = lin ? 1 : 0;
@@ -557,12 +561,13 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         pa.cand_cap = 0;
-        // each staged point takes 16 B plus a 1-byte periodic shift code
-        const long long room = (long long)optin - kPairStaticSmem - (long long)pair_dynamic_smem(pa) - 256;
-        if (room < 17 * 256)
+        // each staged point takes 16 B
+        const long long room =
+            (long long)optin - (long long)pair_static_smem(ctx->lmax) - (long long)pair_dynamic_smem(pa) - 256;
+        if (room < 16 * 256)
             return fail(ctx, NPCF_EINVAL, "pair kernel: neighbour-list capacity %d leaves no room for "
                         "staging (shared memory limit %d B)", pa.cap, optin);
-        pa.cand_cap = (int)std::min<long long>(room / 17, 65535);
+        pa.cand_cap = (int)std::min<long long>(room / 16, 65535);
         if (ctx->stage_limit > 0) pa.cand_cap = std::min(pa.cand_cap, ctx->stage_limit);
     }
     launch_pair(pa, ctx->nsm, s);   // persistent: one block per SM, cells taken dynamically
@@ -1004,8 +1009,10 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             ctx->chunk_target = value;
             return NPCF_OK;
         case 3:
-            if (value < 512 || value > 16384 || (value % 256))
-                return fail(ctx, NPCF_EINVAL, "pair list capacity must be a multiple of 256 in [512, 16384]");
+            // the staged scan appends up to 128 entries per warp and step: a warp's list
+            // (capacity / 8) must hold one whole step, or the scan cannot advance
+            if (value < 1024 || value > 16384 || (value % 256))
+                return fail(ctx, NPCF_EINVAL, "pair list capacity must be a multiple of 256 in [1024, 16384]");
             ctx->pair_cap = value;
             return NPCF_OK;
         case 4:

@@ -79,7 +79,7 @@ struct PairArgs {
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s);
 // dynamic shared memory of the pair kernel for a given capacity setting
 size_t pair_dynamic_smem(const PairArgs& a);
-constexpr int kPairStaticSmem = 16 * 1024;   // upper bound of its static shared memory
+size_t pair_static_smem(int lmax);   // static shared memory of the pair kernel for lmax
 
 // ---------------------------------------------------------------- contraction (a4 + a5)
 struct Contract3Args {

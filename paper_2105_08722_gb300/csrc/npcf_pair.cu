@@ -30,7 +30,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 using warp::TR;
-constexpr int kMaxWarps = 16;
 
 __host__ __device__ constexpr int ncomp(int L) { return (L + 1) * (L + 1); }
 __host__ __device__ constexpr int nlmc(int L) { return (L + 1) * (L + 2) / 2; }
@@ -91,36 +90,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// Shell of an accepted pair. For linear bins the shell is estimated from sqrt(r2) and then
-// corrected against the exact squared edges, so the decision stays the rule's
-// e2[b] <= r2 < e2[b+1]; other edges use a binary search.
-__device__ __forceinline__ int shell_index(float r2, const float* e2, int nr, int linear, float r0,
-                                           float inv_w) {
+// The exact FP32 neighbour rule (same operations as shell_of in npcf_rules.cuh) followed
+// by the shell lookup; -1 for a rejected pair. No loops: the range test is a predicate
+// and linear edges take a direct estimate with one correction. e2lo = e2[0], e2hi = e2[nr].
+__device__ __forceinline__ int pair_shell_fast(const float4 pj, const float4 pi, float sx, float sy, float sz,
+                                               const float* e2, int nr, float e2lo, float e2hi, int linear,
+                                               float r0, float inv_w) {
+    const float dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
+    const float dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
+    const float dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    const bool ok = (r2 > 0.f) & (r2 >= e2lo) & (r2 < e2hi);
     int b;
     if (linear) {
+        // the estimate is within one shell of the rule's shell (shells are wider than 1e-3
+        // r_max when linear is set, far above the FP32 error of the estimate), so one
+        // correction against both of its edges, loaded together, is exact
         b = (int)((r2 * rsqrtf(r2) - r0) * inv_w);
-        b = b < 0 ? 0 : (b >= nr ? nr - 1 : b);
-        while (b > 0 && r2 < e2[b]) --b;
-        while (b + 1 < nr && r2 >= e2[b + 1]) ++b;
+        b = min(max(b, 0), nr - 1);
+        const float lo = e2[b], hi = e2[b + 1];
+        b += (r2 >= hi ? 1 : 0) - (r2 < lo ? 1 : 0);
     } else {
         b = 0;
 #pragma unroll
         for (int step = 8; step >= 1; step >>= 1)
             if (b + step < nr && r2 >= e2[b + step]) b += step;
     }
-    return b;
-}
-
-// The exact FP32 neighbour rule (same operations as shell_of in npcf_rules.cuh) followed
-// by the shell lookup above; -1 for a rejected pair.
-__device__ __forceinline__ int pair_shell(const float4 pj, const float4 pi, float sx, float sy, float sz,
-                                          const float* e2, int nr, int linear, float r0, float inv_w) {
-    const float dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
-    const float dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
-    const float dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
-    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    if (!(r2 > 0.f) || !(r2 >= e2[0]) || !(r2 < e2[nr])) return -1;
-    return shell_index(r2, e2, nr, linear, r0, inv_w);
+    return ok ? b : -1;
 }
 
 // The neighbour rows of a run of cells (x-adjacent, same y and z) as segments of the
@@ -199,26 +195,32 @@ constexpr int kShiftCodes = 64;   // 2 bits per axis
 // Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
 // cap is the neighbour-list capacity of one group in 16-bit entries.
 struct PairLayout {
-    size_t cand, scode, segs, rows, tpref, tdelta, tcode, ulist, slist, ushell, part, total;
+    size_t cand, segs, rows, tpref, tdelta, tcode, ulist, ushell, slist, part, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Floats of one group's partial area: nr + kW - 1 slots for the slice's per-warp sums
+// (warp w's share of shell t goes to slot t + w: the warps' equal chunks of the
+// shell-sorted slice are ordered, so these never collide) and nr per-shell sums.
+__host__ __device__ constexpr int part_floats(int nr, int nc) { return (2 * nr + kW - 1) * nc; }
+
 __host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int cap, int nr, int nc) {
     PairLayout l;
     l.cand = 0;
-    l.scode = align16(l.cand + (size_t)cand_cap * 16);
-    l.segs = align16(l.scode + (size_t)cand_cap);
+    l.segs = align16(l.cand + (size_t)cand_cap * 16);
     l.rows = align16(l.segs + (size_t)2 * nrows * 16);
     // per group: flat-index prefix, staging offset minus prefix, and shift code of each row
     l.tpref = align16(l.rows + (size_t)nrows * 16);
     l.tdelta = align16(l.tpref + (size_t)kG * (2 * nrows + 1) * 4);
     l.tcode = align16(l.tdelta + (size_t)kG * 2 * nrows * 4);
     l.ulist = align16(l.tcode + (size_t)kG * 2 * nrows * 4);
-    l.slist = align16(l.ulist + (size_t)kG * cap * 2);
-    l.ushell = align16(l.slist + (size_t)kG * cap * 2);
-    l.part = align16(l.ushell + (size_t)kG * cap);
-    l.total = align16(l.part + (size_t)kG * kW * nr * nc * 4);
+    l.ushell = align16(l.ulist + (size_t)kG * cap * 2);
+    l.slist = align16(l.ushell + (size_t)kG * cap);
+    // per group: the slice's (warp, shell) partials in slots shell + warp, then the
+    // primary's per-shell sums
+    l.part = align16(l.slist + (size_t)kG * cap * 2);
+    l.total = align16(l.part + (size_t)kG * part_floats(nr, nc) * 4);
     return l;
 }
 
@@ -334,9 +336,9 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
 
 template <int L, bool STAGED>
 __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
-                                            const uint8_t* scode, const int4* segs, int nseg, int total,
+                                            const int4* segs, int nseg, int total,
                                             int* tpref, int* tdelta, int* tcode, bool trim,
-                                            uint16_t* ulist, uint16_t* slist, uint8_t* ushell, float* part,
+                                            uint16_t* ulist, uint8_t* ushell, uint16_t* slist, float* part,
                                             int p, int grp, int warp, int lane, const int* slot_org) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
@@ -353,14 +355,18 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         return;
     }
     const float4 pi = a.pts[p];
-    for (int i = gt; i < kW * nr * NC; i += kW * 32) part[i] = 0.f;
+    float* slot = part;                          // [nr + kW - 1][NC], rewritten every slice
+    float* psum = part + (nr + kW - 1) * NC;     // [nr][NC] sums of the primary
+    for (int i = gt; i < nr * NC; i += kW * 32) psum[i] = 0.f;
     if (gt < kMaxNr) G.tot[gt] = 0u;
 
     // this warp's share of the neighbours and its sub-list
     const int capw = STAGED ? a.cap / kW : a.cap / (2 * kW);
+    // sub-list entries: 16-bit staged index (staged) or 32-bit point index (global), shell
     uint16_t* ul16 = ulist + (size_t)warp * (a.cap / kW);
     uint32_t* ul32 = reinterpret_cast<uint32_t*>(ul16);
     uint8_t* us = ushell + (size_t)warp * (a.cap / kW);
+    const float e2lo = sh.e2[0], e2hi = sh.e2[nr];
     uint32_t* sl32 = reinterpret_cast<uint32_t*>(slist);
     // staged: the rows cut to this primary's x-window, one flat index space split evenly
     const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, pi, tpref, tdelta, tcode, G.wtot, trim, grp,
@@ -395,33 +401,62 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     group_sync(grp);   // partials zeroed before any warp adds to them
 
     for (;;) {
-        // ---- scan: append accepted neighbours while the sub-list has room
+        // ---- scan: append accepted neighbours while the sub-list has room, counting shells
         int cw = 0;
+        if (lane < kMaxNr) G.hist[warp][lane] = 0u;
+        __syncwarp();
         if (STAGED) {
-            // batches of 32 candidates while a whole batch still fits in the sub-list
-            while (cw + 32 <= capw && cursor < kend) {
-                const int k = cursor + lane;
-                int b = -1, q = 0;
-                if (k < kend) {
-                    if (k >= snext) {
-                        do {
-                            ++srow;
-                            snext = tpref[srow + 1];
-                        } while (k >= snext);
-                        sdelta = tdelta[srow];
-                        ssf = sh.shift[tcode[srow]];
+            // two batches of 32 candidates per step while both still fit in the sub-list
+            auto locate = [&](int k) {
+                if (k >= snext) {
+                    do {
+                        ++srow;
+                        snext = tpref[srow + 1];
+                    } while (k >= snext);
+                    sdelta = tdelta[srow];
+                    ssf = sh.shift[tcode[srow]];
+                }
+            };
+            // candidates per lane per step (independent chains). A step appends up to
+            // 32 KC entries, so capw >= 32 KC is required for progress: the host admits
+            // list capacities of at least 1024 (capw >= 128).
+            constexpr int KC = 4;
+            while (cw + 32 * KC <= capw && cursor < kend) {
+                int q[KC], b[KC];
+                float4 sf[KC];
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    const int k = cursor + 32 * j + lane;
+                    q[j] = 0;
+                    sf[j] = ssf;
+                    if (k < kend) {
+                        locate(k);
+                        q[j] = k + sdelta;
+                        sf[j] = ssf;
                     }
-                    q = k + sdelta;
-                    b = pair_shell(cand[q], pi, ssf.x, ssf.y, ssf.z, sh.e2, nr, a.linear, a.lin_r0, a.lin_inv_w);
                 }
-                const unsigned m = __ballot_sync(kFull, b >= 0);
-                if (b >= 0) {
-                    const int pos = cw + __popc(m & lt);
-                    ul16[pos] = (uint16_t)q;
-                    us[pos] = (uint8_t)b;
+                float4 c[KC];
+#pragma unroll
+                for (int j = 0; j < KC; ++j) c[j] = cand[q[j]];
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    const int r = pair_shell_fast(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.e2, nr, e2lo, e2hi,
+                                                  a.linear, a.lin_r0, a.lin_inv_w);
+                    b[j] = (cursor + 32 * j + lane < kend) ? r : -1;
                 }
-                cw += __popc(m);
-                cursor += 32;
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    const unsigned m = __ballot_sync(kFull, b[j] >= 0);
+                    if (b[j] >= 0) {
+                        const int pos = cw + __popc(m & lt);
+                        ul16[pos] = (uint16_t)q[j];
+                        us[pos] = (uint8_t)b[j];
+                    }
+                    cw += __popc(m);
+                    const unsigned gm = __match_any_sync(kFull, b[j]);
+                    if (b[j] >= 0 && lane == __ffs(gm) - 1) atomicAdd(&G.hist[warp][b[j]], (uint32_t)__popc(gm));
+                }
+                cursor += 32 * KC;
             }
             cursor = min(cursor, kend);
         } else {
@@ -431,8 +466,8 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                 const int k = segpos + lane;
                 int b = -1;
                 if (k < sg.y)
-                    b = pair_shell(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.e2, nr, a.linear, a.lin_r0,
-                                   a.lin_inv_w);
+                    b = pair_shell_fast(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.e2, nr, e2lo, e2hi, a.linear,
+                                        a.lin_r0, a.lin_inv_w);
                 const unsigned m = __ballot_sync(kFull, b >= 0);
                 if (b >= 0) {
                     const int pos = cw + __popc(m & lt);
@@ -440,22 +475,13 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                     us[pos] = (uint8_t)b;
                 }
                 cw += __popc(m);
+                const unsigned gm = __match_any_sync(kFull, b);
+                if (b >= 0 && lane == __ffs(gm) - 1) atomicAdd(&G.hist[warp][b], (uint32_t)__popc(gm));
                 segpos += 32;
                 if (segpos >= sg.y) { seg += kW; segpos = 0; }
             }
         }
         const bool done = STAGED ? (cursor >= kend) : (seg >= nseg);
-
-        // ---- shell histogram of this warp's sub-list
-        if (lane < kMaxNr) G.hist[warp][lane] = 0u;
-        __syncwarp();
-        for (int k0 = 0; k0 < cw; k0 += 32) {
-            const bool ok = k0 + lane < cw;
-            const int shk = ok ? (int)us[k0 + lane] : -1;
-            const unsigned m = __match_any_sync(kFull, shk);
-            if (ok && lane == __ffs(m) - 1) G.hist[warp][shk] += (uint32_t)__popc(m);
-            __syncwarp();
-        }
         if (lane == 0) G.done[warp] = done ? 1 : 0;
         group_sync(grp);
         int all_done = 1;
@@ -512,39 +538,48 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                 for (int i = 0; i < NC; ++i) acc[i] = 0.f;
                 for (int k = lo + lane; k < hi; k += 32) {
                     float dx, dy, dz, wj;
-                    if (STAGED) {
-                        const int q = slist[k];
-                        const float4 pj = cand[q];
-                        const float4 sf = sh.shift[scode[q]];
-                        dx = (pj.x - pi.x) - sf.x;
-                        dy = (pj.y - pi.y) - sf.y;
-                        dz = (pj.z - pi.z) - sf.z;
-                        wj = pj.w;
-                    } else {
-                        const float4 pj = a.pts[sl32[k]];
-                        dx = pj.x - pi.x;
-                        dy = pj.y - pi.y;
-                        dz = pj.z - pi.z;
-                        wj = pj.w;
-                        if (g.periodic) {
-                            dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
-                            dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
-                            dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
-                        }
+                    // accepted pairs are closer than r_max < L/3: the minimum image is the
+                    // image the neighbour rule accepted
+                    const float4 pj = STAGED ? cand[slist[k]] : a.pts[sl32[k]];
+                    dx = pj.x - pi.x;
+                    dy = pj.y - pi.y;
+                    dz = pj.z - pi.z;
+                    wj = pj.w;
+                    if (g.periodic) {
+                        dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
+                        dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
+                        dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
                     }
                     const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                     harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, wj);
                 }
                 R::run(acc, lane);
-                float* pw = part + ((size_t)warp * nr + t) * NC;
+                float* pw = slot + (size_t)(t + warp) * NC;
 #pragma unroll
                 for (int i = 0; i < R::F; ++i)
-                    if (slot_org[i] >= 0) pw[slot_org[i]] += acc[i];
+                    if (slot_org[i] >= 0) pw[slot_org[i]] = acc[i];
             }
         }
         group_sync(grp);   // lists are rewritten by the next slice
+        // fold the slice's slots into the primary's sums, warps in order (deterministic);
+        // the next slice writes slots only after its next group barrier
+        {
+            const int ns = (int)G.off[nr];
+            const int chunk = (ns + kW - 1) / kW;
+            for (int i = gt; i < nr * NC; i += kW * 32) {
+                const int t = i / NC, c = i - t * NC;
+                const int o0 = (int)G.off[t], o1 = (int)G.off[t + 1];
+                float v = 0.f;
+                for (int w = 0; w < kW; ++w) {
+                    const int c0 = min(ns, w * chunk), c1 = min(ns, c0 + chunk);
+                    if (max(c0, o0) < min(c1, o1)) v += slot[(t + w) * NC + c];
+                }
+                psum[i] += v;
+            }
+        }
         if (all_done) break;
     }
+    group_sync(grp);   // every fold is done before the sums are read
 
     // ---- combine the per-warp partials and convert to a_lm
     for (int i = gt; i < nr * NLM; i += kW * 32) {
@@ -554,12 +589,8 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         float re = 0.f, im = 0.f;
         for (int k = l - m; k >= 0; k -= 2) {
             const int si = s_index(L, m, k);
-            float sr = 0.f, sim = 0.f;
-            for (int w = 0; w < kW; ++w) {
-                const float* pw = part + ((size_t)w * nr + t) * NC;
-                sr += pw[si];
-                if (m > 0) sim += pw[si + 1];
-            }
+            const float sr = psum[t * NC + si];
+            const float sim = m > 0 ? psum[t * NC + si + 1] : 0.f;
             const float kk = sh.kmat[q * (L + 1) + k];
             re = fmaf(kk, sr, re);
             im = fmaf(kk, sim, im);
@@ -580,7 +611,6 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
     const PairLayout lay = pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(L));
     float4* cand = reinterpret_cast<float4*>(dsm + lay.cand);
-    uint8_t* scode = dsm + lay.scode;
     int4* segs = reinterpret_cast<int4*>(dsm + lay.segs);
     int4* rows = reinterpret_cast<int4*>(dsm + lay.rows);
     __shared__ PairShared<L> sh;
@@ -604,9 +634,9 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     const int wblk = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = wblk / kW, warp = wblk % kW;
     uint16_t* ulist = reinterpret_cast<uint16_t*>(dsm + lay.ulist) + (size_t)grp * a.cap;
-    uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist) + (size_t)grp * a.cap;
     uint8_t* ushell = dsm + lay.ushell + (size_t)grp * a.cap;
-    float* part = reinterpret_cast<float*>(dsm + lay.part) + (size_t)grp * kW * a.nr * ncomp(L);
+    uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist) + (size_t)grp * a.cap;
+    float* part = reinterpret_cast<float*>(dsm + lay.part) + (size_t)grp * part_floats(a.nr, ncomp(L));
     int* tpref = reinterpret_cast<int*>(dsm + lay.tpref) + (size_t)grp * (2 * a.nrows + 1);
     int* tdelta = reinterpret_cast<int*>(dsm + lay.tdelta) + (size_t)grp * 2 * a.nrows;
     int* tcode = reinterpret_cast<int*>(dsm + lay.tcode) + (size_t)grp * 2 * a.nrows;
@@ -654,11 +684,6 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
                         : "memory");
                 }
             }
-            // periodic shift code of every staged point
-            for (int s = wblk; s < nseg; s += kG * kW) {
-                const int4 sg = segs[s];
-                for (int k = lane; k < sg.y; k += 32) scode[sg.z + k] = (uint8_t)(sg.w & 63);
-            }
             const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
             // the whole block leaves together if any thread's wait gave up
             if (__syncthreads_or(ok ? 0 : 1)) {
@@ -670,11 +695,11 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
         }
         for (int p = pbeg + grp; p < pend; p += kG) {
             if (staged)
-                one_primary<L, true>(a, sh, cand, scode, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
-                                     slist, ushell, part, p, grp, warp, lane, slot_org);
+                one_primary<L, true>(a, sh, cand, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
+                                     ushell, slist, part, p, grp, warp, lane, slot_org);
             else
-                one_primary<L, false>(a, sh, cand, scode, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
-                                      slist, ushell, part, p, grp, warp, lane, slot_org);
+                one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
+                                      ushell, slist, part, p, grp, warp, lane, slot_org);
         }
         __syncthreads();   // both groups are done with the staged points of this unit
     }
@@ -688,6 +713,30 @@ void launch_L(const PairArgs& a, int nblocks, cudaStream_t s) {
 }
 
 }  // namespace
+
+template <int L>
+size_t static_L() {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_pair<L>) != cudaSuccess) return 16 * 1024;
+    return fa.sharedSizeBytes;
+}
+
+size_t pair_static_smem(int lmax) {
+    switch (lmax) {
+        case 0: return static_L<0>();
+        case 1: return static_L<1>();
+        case 2: return static_L<2>();
+        case 3: return static_L<3>();
+        case 4: return static_L<4>();
+        case 5: return static_L<5>();
+        case 6: return static_L<6>();
+        case 7: return static_L<7>();
+        case 8: return static_L<8>();
+        case 9: return static_L<9>();
+        case 10: return static_L<10>();
+        default: return 16 * 1024;
+    }
+}
 
 size_t pair_dynamic_smem(const PairArgs& a) {
     return pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(a.lmax)).total;

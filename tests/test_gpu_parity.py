@@ -197,12 +197,14 @@ def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
 
 @pytest.mark.parametrize("tuning", [
     {},                 # staged neighbour cells, one list slice per primary
-    {3: 512},           # staged, several list slices per primary
+    {3: 1024},          # staged, several list slices per primary
     {4: 256},           # neighbour cells too large to stage: global-memory path
-    {3: 512, 4: 256},   # global-memory path with several list slices
+    {3: 1024, 4: 256},  # global-memory path with several list slices
 ])
 def test_dense_primaries_staged_and_global_paths(torch_dev, tuning):
-    pos, w = _catalog(3000, 60.0, 61)
+    # ~1000 neighbours per primary: with a list capacity of 1024 every primary takes
+    # several slices
+    pos, w = _catalog(9000, 60.0, 61)
     edges = np.linspace(2.0, 18.0, 5)
     _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0, tuning=tuning)
     want, wcounts = oracle.npcf(pos, w, (3, 4), 3, edges, 60.0)
