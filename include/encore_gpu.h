@@ -110,12 +110,41 @@ npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len);
 npcf_status npcf_layout(const npcf_ctx* ctx, int order, int* n_lambda, int* n_bins,
                         int* lambdas, int* bins);
 
-/* Copy the FP64 multiplets accumulated so far to host out[out_len] (synchronises).
+/* Copy the FP64 multiplets accumulated so far to host out[out_len] (synchronises;
+ * NPCF_EINVAL when the context holds a batch of several catalogs).
  * normalize = 0: raw sums as defined above. normalize = 1 (periodic only): divide by
  * V prod_k v_{b_k} (Eq. NPCF-mult-discrete-binned-estimator, Eq. alm-binned-def with
  * v_b = 4 pi (r_{b+1}^3 - r_b^3) / 3, V = box^3) and by R_0 = (4pi)^{-(N-1)/2} nbar^N
  * with nbar = sum w / V (Eq. R-periodic-form). */
 npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normalize);
+
+/* Batch of catalogs in one call (a8): catalog k is points offsets[k] .. offsets[k+1]-1 of
+ * d_pos / d_w (device, caller-owned, as in npcf_accumulate); offsets: host int64
+ * [ncat+1], offsets[0] = 0, non-decreasing; 1 <= ncat <= 65535. Periodic boxes only (every
+ * catalog uses the same grid shape; NPCF_EUNSUPPORTED otherwise). All catalogs run through
+ * the same kernels in one pass: the cell lists of all catalogs are built together (cell
+ * ids offset per catalog), the pair kernel takes work units over (catalog, cell run) from
+ * one device counter, the contractions take chunks of primaries that never cross a
+ * catalog, and each catalog keeps its own FP64 multiplets (read with
+ * npcf_finalize_batch), sums of weights and pair counts. The device work of a call is
+ * captured into a CUDA graph on the first call with a given shape and replayed by later
+ * calls with the same pointers, offsets, tuning and context buffers (a launch on the legacy
+ * default stream is enqueued directly: that stream cannot be captured). The first
+ * accumulate call after npcf_create or npcf_reset fixes the number of catalogs the
+ * accumulators hold; later calls must use the same number (they co-add per catalog). */
+npcf_status npcf_accumulate_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w,
+                                  const int64_t* offsets, int ncat, void* stream);
+
+/* Multiplets of every catalog, host out[ncat][npcf_output_size] (synchronises);
+ * normalize as in npcf_finalize, catalog k with its own sum of weights. */
+npcf_status npcf_finalize_batch(npcf_ctx* ctx, double* out, size_t out_len, int normalize);
+
+/* Per-catalog pair counts, host uint64 out[ncat][nr] (synchronises). */
+npcf_status npcf_pair_counts_batch(npcf_ctx* ctx, uint64_t* out, size_t out_len);
+
+/* Catalogs the accumulators hold (0 before the first accumulate call) and how many batch
+ * calls were run as CUDA-graph launches. Either pointer may be NULL. */
+npcf_status npcf_batch_info(const npcf_ctx* ctx, int* ncat, int64_t* graph_launches);
 
 /* Per-shell pair counts accumulated so far (uint64 [nr], exact; synchronises). */
 npcf_status npcf_pair_counts(npcf_ctx* ctx, uint64_t* out);

@@ -36,6 +36,10 @@ SIGNATURES = {
     "npcf_get_timings": (_i, [_vp, _vp]),
     "npcf_pair_counts_noalloc": (_i, [_vp, _i64, _i, _vp, _d, _vp, _vp]),
     "npcf_edge_correct": (_i, [_vp, _vp, _vp]),
+    "npcf_accumulate_batch": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "npcf_finalize_batch": (_i, [_vp, _vp, _sz, _i]),
+    "npcf_pair_counts_batch": (_i, [_vp, _vp, _sz]),
+    "npcf_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64)]),
     "npcf_gaunt": (_i, [_i, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
@@ -163,6 +167,30 @@ class NPCF:
     def finalize(self, normalize: bool = False) -> np.ndarray:
         out = np.zeros(self.size, dtype=np.float64)
         self._check(self._lib.npcf_finalize(self._h, out.ctypes.data, self.size, int(normalize)))
+        return out
+
+    def accumulate_batch(self, pos, w, offsets, stream=None):
+        """Co-add a batch of catalogs (npcf_accumulate_batch): pos [n, 3] and w [n] CUDA
+        tensors, catalog k = rows offsets[k] .. offsets[k+1]-1."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self._lib.npcf_accumulate_batch(self._h, _ptr(pos), _ptr(w), off.ctypes.data, len(off) - 1,
+                                                    _stream_handle(stream)))
+
+    def batch_info(self) -> Tuple[int, int]:
+        k, g = ctypes.c_int(), ctypes.c_int64()
+        self._check(self._lib.npcf_batch_info(self._h, ctypes.byref(k), ctypes.byref(g)))
+        return k.value, g.value
+
+    def finalize_batch(self, normalize: bool = False) -> np.ndarray:
+        k = max(self.batch_info()[0], 1)
+        out = np.zeros((k, self.size), dtype=np.float64)
+        self._check(self._lib.npcf_finalize_batch(self._h, out.ctypes.data, out.size, int(normalize)))
+        return out
+
+    def pair_counts_batch(self) -> np.ndarray:
+        k = max(self.batch_info()[0], 1)
+        out = np.zeros((k, self.nr), dtype=np.uint64)
+        self._check(self._lib.npcf_pair_counts_batch(self._h, out.ctypes.data, out.size))
         return out
 
     def edge_correct(self, randoms: "NPCF") -> np.ndarray:

@@ -62,7 +62,14 @@ __global__ void k_assign(BinArgs a) {
     int cx = cell_coord(x, a.g.ox, a.g.inv_cell, a.g.gx);
     int cy = cell_coord(y, a.g.oy, a.g.inv_cell, a.g.gy);
     int cz = cell_coord(z, a.g.oz, a.g.inv_cell, a.g.gz);
-    uint32_t c = (uint32_t)((cz * a.g.gy + cy) * a.g.gx + cx);
+    // catalog of point i: last k with off[k] <= i (binary search over the batch offsets)
+    int lo = 0, hi = a.ncat - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.off[mid] <= (long long)i) lo = mid;
+        else hi = mid - 1;
+    }
+    uint32_t c = (uint32_t)lo * (uint32_t)a.g.ncell + (uint32_t)((cz * a.g.gy + cy) * a.g.gx + cx);
     a.cid[i] = c;
     atomicAdd(&a.count[c], 1u);
 }
@@ -119,7 +126,7 @@ __global__ void k_scatter(BinArgs a) {
 // the pair kernel's x-window cut off.
 __global__ void k_cell_order(BinArgs a) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.g.ncell) return;
+    if (c >= a.g.ncell * a.ncat) return;
     uint32_t s0 = a.start[c], s1 = a.start[c + 1];
     if (s1 - s0 > 4096u) {  // keep the quadratic sort bounded
         atomicOr(a.err, 8);
@@ -153,9 +160,10 @@ void launch_bbox(const float* pos, int n, float* part, int nblocks, cudaStream_t
 void launch_bin(const BinArgs& a, cudaStream_t s) {
     int nb = (a.n + 255) / 256;
     if (a.n > 0) k_assign<<<nb, 256, 0, s>>>(a);
-    k_scan<<<1, 1024, 0, s>>>(a.count, a.start, a.cursor, a.g.ncell);
+    const int cells = a.g.ncell * a.ncat;
+    k_scan<<<1, 1024, 0, s>>>(a.count, a.start, a.cursor, cells);
     if (a.n > 0) k_scatter<<<nb, 256, 0, s>>>(a);
-    k_cell_order<<<(a.g.ncell + 127) / 128, 128, 0, s>>>(a);
+    k_cell_order<<<(cells + 127) / 128, 128, 0, s>>>(a);
 }
 
 }  // namespace npcf

@@ -114,6 +114,19 @@ struct npcf_ctx {
     DevBuf<int> errflag, work;
     DevBuf<float> bbox;
     DevBuf<float> hpos_stage, hw_stage;
+    // catalogs the accumulators hold (0: none yet; fixed by the first accumulate call)
+    int ncat = 0;
+    // tables of the current batch (host copies decide whether an upload is needed)
+    DevBuf<long long> d_off;
+    std::vector<long long> h_off;
+    DevBuf<int2> chunks;
+    std::vector<int2> h_chunks;
+    DevBuf<int> cbeg;
+    std::vector<int> h_cbeg;
+    // CUDA graph of the last batch shape
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uintptr_t> gsig;
+    long long graph_launches = 0;
     // edge correction: sparse generalized Gaunt tables per order (built on first use)
     DevBuf<int> e_tptr[3], e_tlp[3];
     DevBuf<double> e_tg[3], e_out;
@@ -454,25 +467,49 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s)
     return NPCF_OK;
 }
 
-__global__ void k_sumw(const float* __restrict__ w, int n, double* out) {
-    double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += w[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+// Host plan of one accumulate call: a single catalog is a batch of one.
+struct Plan {
+    int n = 0, ncat = 0, nchunk = 0;
+    PairArgs pa{};
+};
+
+template <typename T>
+bool same_table(const DevBuf<T>& b, const std::vector<T>& host, const std::vector<T>& v) {
+    return b.p && host.size() == v.size() && std::memcmp(host.data(), v.data(), v.size() * sizeof(T)) == 0;
 }
 
-npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim,
-                           int64_t n64, cudaStream_t s) {
-    if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", (long long)n64);
-    if (n64 == 0) return NPCF_OK;
-    if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+// Host part of an accumulate call: validation, grid, buffers and the tables of this batch
+// (catalog offsets, contraction chunks). Uploads happen only when a table changes, so a
+// repeated call with the same shapes does no synchronous work here.
+npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const std::vector<long long>& off,
+                    cudaStream_t s, Plan& P) {
+    const long long n64 = off.back();
+    const int ncat = (int)off.size() - 1;
+    if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", n64);
     if (n64 >= (int64_t(1) << 28))
-        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^28 points per call",
-                    (long long)n64);
+        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^28 points per call", n64);
+    if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+    if (ctx->ncat != 0 && ctx->ncat != ncat)
+        return fail(ctx, NPCF_EINVAL, "the accumulators hold %d catalogs, this call has %d (npcf_reset first)",
+                    ctx->ncat, ncat);
     const int n = (int)n64;
+    P.n = n;
+    P.ncat = ncat;
+    if (ctx->ncat == 0) {
+        // the first call fixes how many catalogs the accumulators hold
+        CU(ctx->zeta.ensure((size_t)ncat * std::max(ctx->total, 1)));
+        CU(ctx->counts.ensure((size_t)ncat * ctx->nr));
+        CU(ctx->sumw.ensure(ncat));
+        if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, (size_t)ncat * ctx->total * sizeof(double)));
+        CU(cudaMemset(ctx->counts.p, 0, (size_t)ncat * ctx->nr * sizeof(unsigned long long)));
+        CU(cudaMemset(ctx->sumw.p, 0, ncat * sizeof(double)));
+        ctx->ncat = ncat;
+    }
     npcf_status st = setup_grid(ctx, d_pos, n, s);
     if (st != NPCF_OK) return st;
     const GridInfo& g = ctx->grid;
+    const size_t cells = (size_t)g.ncell * ncat;
+    if (cells >= (size_t)1 << 31) return fail(ctx, NPCF_EUNSUPPORTED, "%zu cells in the batch's grids", cells);
 
     CU(ctx->pts.ensure(n));
     CU(ctx->wp.ensure(n));
@@ -481,36 +518,42 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     CU(ctx->cid.ensure(n));
     CU(ctx->alm.ensure((size_t)n * ctx->nr * ctx->nlm));
     CU(ctx->cnt.ensure((size_t)n * ctx->nr));
-    CU(ctx->count.ensure(g.ncell));
-    CU(ctx->start.ensure(g.ncell + 1));
-    CU(ctx->cursor.ensure(g.ncell));
+    CU(ctx->count.ensure(cells));
+    CU(ctx->start.ensure(cells + 1));
+    CU(ctx->cursor.ensure(cells));
     CU(ctx->work.ensure(2));
 
-    if (ctx->timed) CU(cudaEventRecord(ctx->ev[0], s));
-    CU(cudaMemsetAsync(ctx->count.p, 0, g.ncell * sizeof(uint32_t), s));
-    CU(cudaMemsetAsync(ctx->work.p, 0, 2 * sizeof(int), s));
-    k_sumw<<<64, 256, 0, s>>>(d_w, n, ctx->sumw.p);
+    // contraction chunks: ranges of about n / (waves x SMs) primaries (a multiple of the
+    // FP32 kernel's 64-primary tile), never crossing a catalog; the tensor-core kernel keeps
+    // its accumulators for a whole chunk, so it takes one wave
+    const int waves = ctx->prec == NPCF_SPLIT_BF16 ? 1 : 4;
+    long long C = ctx->chunk_target > 0 ? ctx->chunk_target : (n64 + (long long)waves * ctx->nsm - 1) /
+                                                                   ((long long)waves * ctx->nsm);
+    C = std::max(64LL, (C + 63) / 64 * 64);
+    std::vector<int2> chunks;
+    std::vector<int> cbeg(1, 0);
+    for (int k = 0; k < ncat; ++k) {
+        for (long long p = off[k]; p < off[k + 1]; p += C)
+            chunks.push_back(make_int2((int)p, (int)std::min(off[k + 1], p + C)));
+        cbeg.push_back((int)chunks.size());
+    }
+    P.nchunk = (int)chunks.size();
+    if (!same_table(ctx->d_off, ctx->h_off, off)) {
+        CU(upload(ctx->d_off, off));
+        ctx->h_off = off;
+    }
+    if (!same_table(ctx->chunks, ctx->h_chunks, chunks)) {
+        CU(upload(ctx->chunks, chunks));
+        ctx->h_chunks = chunks;
+    }
+    if (!same_table(ctx->cbeg, ctx->h_cbeg, cbeg)) {
+        CU(upload(ctx->cbeg, cbeg));
+        ctx->h_cbeg = cbeg;
+    }
+    CU(ctx->partial.ensure((size_t)std::max(P.nchunk, 1) * std::max(ctx->total, 1)));
 
-    BinArgs b{};
-    b.pos = d_pos;
-    b.w = d_w;
-    b.wprim = d_wprim;
-    b.n = n;
-    b.g = g;
-    b.cid = ctx->cid.p;
-    b.count = ctx->count.p;
-    b.start = ctx->start.p;
-    b.cursor = ctx->cursor.p;
-    b.pts = ctx->pts.p;
-    b.wp = ctx->wp.p;
-    b.idx = ctx->idx.p;
-    b.cell_of = ctx->cell_of.p;
-    b.err = ctx->errflag.p;
-    launch_bin(b, s);
-    CU(cudaGetLastError());
-    if (ctx->timed) CU(cudaEventRecord(ctx->ev[1], s));
-
-    PairArgs pa{};
+    PairArgs& pa = P.pa;
+    pa = PairArgs{};
     pa.pts = ctx->pts.p;
     pa.wp = ctx->wp.p;
     pa.cell_of = ctx->cell_of.p;
@@ -525,6 +568,7 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
     pa.alm = ctx->alm.p;
     pa.cnt = ctx->cnt.p;
     pa.counts = ctx->counts.p;
+    pa.ncat = ncat;
     pa.n = n;
     pa.work = ctx->work.p;
     pa.cap = ctx->pair_cap;
@@ -538,8 +582,8 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         pa.run = std::max(1, ctx->cell_run);
         if (g.periodic) pa.run = std::max(1, std::min(pa.run, g.gx - 2 * reach));
         // linear shell edges allow a direct shell estimate (corrected exactly on the device)
-        const double r0 = ctx->edges[0], w = (ctx->edges[ctx->nr] - r0) / ctx->nr;
         // (shells narrower than 1e-3 r_max take the binary search)
+        const double r0 = ctx->edges[0], w = (ctx->edges[ctx->nr] - r0) / ctx->nr;
         bool lin = w >= 1e-3 * ctx->edges[ctx->nr];
         for (int i = 0; i <= ctx->nr && lin; ++i)
             lin = std::fabs(ctx->edges[i] - (r0 + i * w)) <= 1e-9 * ctx->edges[ctx->nr];
@@ -560,7 +604,6 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         int dev = 0, optin = 0;
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        pa.cand_cap = 0;
         // each staged point takes 16 B
         const long long room =
             (long long)optin - (long long)pair_static_smem(ctx->lmax) - (long long)pair_dynamic_smem(pa) - 256;
@@ -570,27 +613,63 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
         pa.cand_cap = (int)std::min<long long>(room / 16, 65535);
         if (ctx->stage_limit > 0) pa.cand_cap = std::min(pa.cand_cap, ctx->stage_limit);
     }
-    launch_pair(pa, ctx->nsm, s);   // persistent: one block per SM, cells taken dynamically
-    CU(cudaGetLastError());
-    if (ctx->timed) CU(cudaEventRecord(ctx->ev[2], s));
+    if (ctx->prec == NPCF_SPLIT_BF16) {
+        int dev = 0, optin = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        Contract4TCArgs c{};
+        c.nr = ctx->nr;
+        c.nlm = ctx->nlm;
+        c.nterms = ctx->c4nterms;
+        c.nseg = ctx->c4nseg;
+        c.nlam = ctx->c4nlam;
+        c.ncombo = ctx->tc_ncombo;
+        c.maxcomp = ctx->tc_maxcomp;
+        if (ctx->c4nitem > 0 && contract4_tc_smem_bytes(c) + 1024 > (size_t)optin)
+            return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: operands need %zu B of shared memory",
+                        contract4_tc_smem_bytes(c));
+    }
+    ctx->last_n = n;
+    return NPCF_OK;
+}
 
-    // contraction over primaries: chunks of cell-sorted primaries
-    // (the tensor-core contraction keeps its accumulators for a whole chunk: one wave)
-    const int waves = ctx->prec == NPCF_SPLIT_BF16 ? 1 : 4;
-    int nchunk = ctx->chunk_target > 0 ? (n + ctx->chunk_target - 1) / ctx->chunk_target
-                                       : std::min(std::max(1, n / 64), waves * ctx->nsm);
-    nchunk = std::max(1, nchunk);
-    const int chunk = (n + nchunk - 1) / nchunk;
-    nchunk = (n + chunk - 1) / chunk;
-    // partial rows each order's contraction fills
-    std::vector<int> rows_of(ctx->orders.size(), nchunk);
-    int prow = nchunk;
-    for (size_t k = 0; k < ctx->orders.size(); ++k)
-        if (ctx->orders[k].N == 4 && ctx->prec == NPCF_FP32) {
-            rows_of[k] = contract4w_blocks(ctx->nsm, n);
-            prow = std::max(prow, rows_of[k]);
-        }
-    CU(ctx->partial.ensure((size_t)prow * ctx->total));
+// Device part of an accumulate call: memsets and kernels only, all on stream s, so that a
+// batch can be captured into a CUDA graph and replayed. Stage events only when timed.
+npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim, const Plan& P,
+                    cudaStream_t s, bool timed) {
+    const GridInfo& g = ctx->grid;
+    const int n = P.n, ncat = P.ncat;
+    const size_t cells = (size_t)g.ncell * ncat;
+    if (timed) CU(cudaEventRecord(ctx->ev[0], s));
+    CU(cudaMemsetAsync(ctx->count.p, 0, cells * sizeof(uint32_t), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 2 * sizeof(int), s));
+    launch_sumw(d_w, ctx->d_off.p, ncat, ctx->sumw.p, s);
+
+    BinArgs b{};
+    b.pos = d_pos;
+    b.w = d_w;
+    b.wprim = d_wprim;
+    b.n = n;
+    b.g = g;
+    b.cid = ctx->cid.p;
+    b.count = ctx->count.p;
+    b.start = ctx->start.p;
+    b.cursor = ctx->cursor.p;
+    b.pts = ctx->pts.p;
+    b.wp = ctx->wp.p;
+    b.idx = ctx->idx.p;
+    b.cell_of = ctx->cell_of.p;
+    b.err = ctx->errflag.p;
+    b.off = ctx->d_off.p;
+    b.ncat = ncat;
+    launch_bin(b, s);
+    CU(cudaGetLastError());
+    if (timed) CU(cudaEventRecord(ctx->ev[1], s));
+
+    launch_pair(P.pa, ctx->nsm, s);   // persistent: one block per SM, work units taken dynamically
+    CU(cudaGetLastError());
+    if (timed) CU(cudaEventRecord(ctx->ev[2], s));
+
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
         if (o.N == 3) {
@@ -602,8 +681,8 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.nr = ctx->nr;
             c.nlm = ctx->nlm;
             c.lmax = ctx->lmax;
-            c.nchunk = nchunk;
-            c.chunk = chunk;
+            c.chunks = ctx->chunks.p;
+            c.nchunk = P.nchunk;
             c.rows = ctx->c3rows.p;
             c.pairs = ctx->c3pairs.p;
             c.coef = ctx->c3coef.p;
@@ -621,7 +700,7 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.n = n;
             c.nr = ctx->nr;
             c.nlm = ctx->nlm;
-            c.chunk = chunk;
+            c.chunks = ctx->chunks.p;
             c.terms = ctx->c4terms.p;
             c.nterms = ctx->c4nterms;
             c.segs = ctx->c4segs.p;
@@ -645,13 +724,29 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.partial = ctx->partial.p;
             c.total = ctx->total;
             c.err = ctx->errflag.p;
-            int dev = 0, optin = 0;
-            CU(cudaGetDevice(&dev));
-            CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-            if (contract4_tc_smem_bytes(c) + 1024 > (size_t)optin)
-                return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: operands need %zu B of shared memory",
-                            contract4_tc_smem_bytes(c));
-            launch_contract4_tc(c, nchunk, s);
+            launch_contract4_tc(c, P.nchunk, s);
+        } else if (o.N == 4) {
+            if (ctx->c4nitem == 0) continue;
+            Contract4WArgs c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.terms = ctx->c4terms.p;
+            c.nterms = ctx->c4nterms;
+            c.segs = ctx->c4segs.p;
+            c.nseg = ctx->c4nseg;
+            c.items = ctx->c4items.p;
+            c.nitem = ctx->c4nitem;
+            c.chunks = ctx->chunks.p;
+            c.nchunk = P.nchunk;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            c.out_off = ctx->order_off[k];
+            c.nout = o.n_lambda() * o.n_bins();
+            c.chunk_counter = ctx->work.p + 1;
+            launch_contract4w(c, contract4w_blocks(ctx->nsm, P.nchunk), s);
         } else if (o.N == 5) {
             if (ctx->c5nrows == 0) continue;
             Contract5Args c{};
@@ -660,8 +755,8 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.n = n;
             c.nr = ctx->nr;
             c.nlm = ctx->nlm;
-            c.nchunk = nchunk;
-            c.chunk = chunk;
+            c.chunks = ctx->chunks.p;
+            c.nchunk = P.nchunk;
             c.terms12 = ctx->c5terms12.p;
             c.segs12 = ctx->c5segs12.p;
             c.t12_seg0 = ctx->c5t12seg0.p;
@@ -687,38 +782,81 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
             c.partial = ctx->partial.p;
             c.total = ctx->total;
             launch_contract5(c, s);
-        } else if (o.N == 4) {
-            if (ctx->c4nitem == 0) continue;
-            Contract4WArgs c{};
-            c.alm = ctx->alm.p;
-            c.wp = ctx->wp.p;
-            c.n = n;
-            c.nr = ctx->nr;
-            c.nlm = ctx->nlm;
-            c.terms = ctx->c4terms.p;
-            c.nterms = ctx->c4nterms;
-            c.segs = ctx->c4segs.p;
-            c.nseg = ctx->c4nseg;
-            c.items = ctx->c4items.p;
-            c.nitem = ctx->c4nitem;
-            c.partial = ctx->partial.p;
-            c.total = ctx->total;
-            c.out_off = ctx->order_off[k];
-            c.nout = o.n_lambda() * o.n_bins();
-            c.tile_counter = ctx->work.p + 1;
-            launch_contract4w(c, rows_of[k], s);
         }
         CU(cudaGetLastError());
     }
-    if (ctx->timed) CU(cudaEventRecord(ctx->ev[3], s));
+    if (timed) CU(cudaEventRecord(ctx->ev[3], s));
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
-        launch_reduce(ctx->partial.p, rows_of[k], ctx->total, ctx->order_off[k], o.n_lambda() * o.n_bins(),
+        launch_reduce(ctx->partial.p, ctx->cbeg.p, ncat, ctx->total, ctx->order_off[k], o.n_lambda() * o.n_bins(),
                       ctx->zscale.p, ctx->zeta.p, s);
     }
     CU(cudaGetLastError());
-    if (ctx->timed) CU(cudaEventRecord(ctx->ev[4], s));
-    ctx->last_n = n;
+    if (timed) CU(cudaEventRecord(ctx->ev[4], s));
+    return NPCF_OK;
+}
+
+npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim,
+                           int64_t n64, cudaStream_t s) {
+    if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", (long long)n64);
+    if (n64 == 0) return NPCF_OK;
+    Plan P;
+    npcf_status st = prepare(ctx, d_pos, d_w, std::vector<long long>{0, (long long)n64}, s, P);
+    if (st != NPCF_OK) return st;
+    return enqueue(ctx, d_pos, d_w, d_wprim, P, s, ctx->timed);
+}
+
+// Batch: catalog k holds points off[k] .. off[k+1] of d_pos / d_w. The device work is
+// captured into a CUDA graph on the first call with a given shape; later calls with the
+// same pointers, offsets, tuning and context buffers replay the graph (one launch). The
+// legacy default stream cannot be captured: there the work is enqueued directly.
+npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const std::vector<long long>& off,
+                      cudaStream_t s) {
+    if (!(ctx->box > 0))
+        return fail(ctx, NPCF_EUNSUPPORTED, "batches take periodic boxes (one grid shape for every catalog)");
+    for (size_t k = 0; k + 1 < off.size(); ++k)
+        if (off[k + 1] < off[k]) return fail(ctx, NPCF_EINVAL, "batch offsets must not decrease");
+    if (off.front() != 0) return fail(ctx, NPCF_EINVAL, "batch offsets must start at 0");
+    Plan P;
+    npcf_status st = prepare(ctx, d_pos, d_w, off, s, P);
+    if (st != NPCF_OK) return st;
+    if (P.n == 0) return NPCF_OK;
+    if (s == 0 || s == cudaStreamLegacy || s == cudaStreamPerThread) return enqueue(ctx, d_pos, d_w, nullptr, P, s, false);
+    // everything the captured work depends on
+    std::vector<uintptr_t> sig = {
+        (uintptr_t)d_pos, (uintptr_t)d_w, (uintptr_t)ctx->pts.p, (uintptr_t)ctx->wp.p, (uintptr_t)ctx->idx.p,
+        (uintptr_t)ctx->cell_of.p, (uintptr_t)ctx->cid.p, (uintptr_t)ctx->alm.p, (uintptr_t)ctx->cnt.p,
+        (uintptr_t)ctx->count.p, (uintptr_t)ctx->start.p, (uintptr_t)ctx->cursor.p, (uintptr_t)ctx->work.p,
+        (uintptr_t)ctx->partial.p, (uintptr_t)ctx->zeta.p, (uintptr_t)ctx->counts.p, (uintptr_t)ctx->sumw.p,
+        (uintptr_t)ctx->d_off.p, (uintptr_t)ctx->chunks.p, (uintptr_t)ctx->cbeg.p, (uintptr_t)ctx->rows.p,
+        (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.run, (uintptr_t)P.pa.cap,
+        (uintptr_t)P.pa.cand_cap, (uintptr_t)P.pa.trim, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
+    for (long long v : off) sig.push_back((uintptr_t)v);
+    if (ctx->gexec && sig == ctx->gsig) {
+        CU(cudaGraphLaunch(ctx->gexec, s));
+        ++ctx->graph_launches;
+        return NPCF_OK;
+    }
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gsig.clear();
+    }
+    CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    st = enqueue(ctx, d_pos, d_w, nullptr, P, s, false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != NPCF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    CU(e);
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    CU(ei);
+    ctx->gsig = sig;
+    CU(cudaGraphLaunch(ctx->gexec, s));
+    ++ctx->graph_launches;
     return NPCF_OK;
 }
 
@@ -779,10 +917,12 @@ npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr, c
 
 npcf_status npcf_reset(npcf_ctx* ctx) {
     if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
-    if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, ctx->total * sizeof(double)));
-    CU(cudaMemset(ctx->counts.p, 0, ctx->nr * sizeof(unsigned long long)));
+    const size_t k = (size_t)std::max(ctx->ncat, 1);
+    if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, k * ctx->total * sizeof(double)));
+    CU(cudaMemset(ctx->counts.p, 0, k * ctx->nr * sizeof(unsigned long long)));
     CU(cudaMemset(ctx->errflag.p, 0, sizeof(int)));
-    CU(cudaMemset(ctx->sumw.p, 0, sizeof(double)));
+    CU(cudaMemset(ctx->sumw.p, 0, k * sizeof(double)));
+    ctx->ncat = 0;   // the next accumulate call fixes the number of catalogs again
     return NPCF_OK;
 }
 
@@ -833,27 +973,36 @@ npcf_status npcf_layout(const npcf_ctx* ctx, int order, int* n_lambda, int* n_bi
     return NPCF_EINVAL;
 }
 
-npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normalize) {
-    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
-    if ((!out && ctx->total > 0) || out_len < (size_t)ctx->total)
-        return fail(ctx, NPCF_EINVAL, "output buffer too small");
+}  // extern "C"
+
+namespace {
+
+// Copy ncopy catalogs' multiplets (synchronises); normalise catalog k with its own sum of
+// weights when asked.
+npcf_status finalize_catalogs(npcf_ctx* ctx, double* out, int ncopy, int normalize) {
     CU(cudaDeviceSynchronize());
     int errbits = 0;
     CU(cudaMemcpy(&errbits, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (errbits & 1) return fail(ctx, NPCF_EINVAL, "positions outside [0, box) or not finite");
     if (errbits & 2) return fail(ctx, NPCF_ETIMEOUT, "a bounded device wait gave up; results are incomplete");
-    if (ctx->total > 0)
-        CU(cudaMemcpy(out, ctx->zeta.p, ctx->total * sizeof(double), cudaMemcpyDeviceToHost));
-    if (normalize) {
-        if (!(ctx->box > 0)) return fail(ctx, NPCF_EUNSUPPORTED, "normalisation needs a periodic box");
-        double sumw = 0;
-        CU(cudaMemcpy(&sumw, ctx->sumw.p, sizeof(double), cudaMemcpyDeviceToHost));
-        const double V = ctx->box * ctx->box * ctx->box;
-        const double nbar = sumw / V;
-        const double fourpi = 4.0 * M_PI;
-        std::vector<double> vb(ctx->nr);
-        for (int b = 0; b < ctx->nr; ++b)
-            vb[b] = fourpi / 3.0 * (std::pow(ctx->edges[b + 1], 3) - std::pow(ctx->edges[b], 3));
+    if (ctx->total == 0 || ncopy == 0) return NPCF_OK;
+    if (ctx->ncat == 0) {
+        std::memset(out, 0, (size_t)ncopy * ctx->total * sizeof(double));
+        return NPCF_OK;
+    }
+    CU(cudaMemcpy(out, ctx->zeta.p, (size_t)ncopy * ctx->total * sizeof(double), cudaMemcpyDeviceToHost));
+    if (!normalize) return NPCF_OK;
+    if (!(ctx->box > 0)) return fail(ctx, NPCF_EUNSUPPORTED, "normalisation needs a periodic box");
+    std::vector<double> sumw(ncopy);
+    CU(cudaMemcpy(sumw.data(), ctx->sumw.p, ncopy * sizeof(double), cudaMemcpyDeviceToHost));
+    const double V = ctx->box * ctx->box * ctx->box;
+    const double fourpi = 4.0 * M_PI;
+    std::vector<double> vb(ctx->nr);
+    for (int b = 0; b < ctx->nr; ++b)
+        vb[b] = fourpi / 3.0 * (std::pow(ctx->edges[b + 1], 3) - std::pow(ctx->edges[b], 3));
+    for (int c = 0; c < ncopy; ++c) {
+        const double nbar = sumw[c] / V;
+        double* oc = out + (size_t)c * ctx->total;
         for (size_t k = 0; k < ctx->orders.size(); ++k) {
             const OrderTable& o = ctx->orders[k];
             const int N = o.N, nb = o.n_bins();
@@ -862,15 +1011,60 @@ npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normal
                 for (int b = 0; b < nb; ++b) {
                     double vB = V;
                     for (int q = 0; q < N - 1; ++q) vB *= vb[o.bins[(size_t)b * (N - 1) + q]];
-                    out[ctx->order_off[k] + a * nb + b] /= vB * R0;
+                    oc[ctx->order_off[k] + a * nb + b] /= vB * R0;
                 }
         }
     }
     return NPCF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normalize) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if ((!out && ctx->total > 0) || out_len < (size_t)ctx->total)
+        return fail(ctx, NPCF_EINVAL, "output buffer too small");
+    if (ctx->ncat > 1) return fail(ctx, NPCF_EINVAL, "the context holds a batch: use npcf_finalize_batch");
+    return finalize_catalogs(ctx, out, 1, normalize);
+}
+
+npcf_status npcf_finalize_batch(npcf_ctx* ctx, double* out, size_t out_len, int normalize) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    const int k = std::max(ctx->ncat, 1);
+    if ((!out && ctx->total > 0) || out_len < (size_t)k * ctx->total)
+        return fail(ctx, NPCF_EINVAL, "output buffer too small (%d catalogs x %d)", k, ctx->total);
+    return finalize_catalogs(ctx, out, k, normalize);
+}
+
+npcf_status npcf_accumulate_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const int64_t* offsets,
+                                  int ncat, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (ncat < 1 || ncat > 65535 || !offsets) return fail(ctx, NPCF_EINVAL, "ncat must be in [1, 65535]");
+    std::vector<long long> off(offsets, offsets + ncat + 1);
+    return run_batch(ctx, d_pos, d_w, off, (cudaStream_t)stream);
+}
+
+npcf_status npcf_batch_info(const npcf_ctx* ctx, int* ncat, int64_t* graph_launches) {
+    if (!ctx) return NPCF_EINVAL;
+    if (ncat) *ncat = ctx->ncat;
+    if (graph_launches) *graph_launches = ctx->graph_launches;
+    return NPCF_OK;
+}
+
+npcf_status npcf_pair_counts_batch(npcf_ctx* ctx, uint64_t* out, size_t out_len) {
+    if (check_ctx(ctx) != NPCF_OK || !out) return NPCF_EINVAL;
+    const int k = std::max(ctx->ncat, 1);
+    if (out_len < (size_t)k * ctx->nr) return fail(ctx, NPCF_EINVAL, "output buffer too small");
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(out, ctx->counts.p, (size_t)k * ctx->nr * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return NPCF_OK;
+}
+
 npcf_status npcf_pair_counts(npcf_ctx* ctx, uint64_t* out) {
     if (check_ctx(ctx) != NPCF_OK || !out) return NPCF_EINVAL;
+    if (ctx->ncat > 1) return fail(ctx, NPCF_EINVAL, "the context holds a batch: use npcf_pair_counts_batch");
     CU(cudaDeviceSynchronize());
     CU(cudaMemcpy(out, ctx->counts.p, ctx->nr * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     return NPCF_OK;
@@ -894,6 +1088,7 @@ npcf_status npcf_edge_correct(npcf_ctx* nctx, npcf_ctx* rctx, double* out) {
         nctx->box != rctx->box || nctx->allparity != rctx->allparity || nctx->edges != rctx->edges)
         return fail(nctx, NPCF_EINVAL, "the two contexts differ in lmax, orders, shells or box");
     if (nctx->allparity) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction takes parity-even multiplets");
+    if (nctx->ncat > 1 || rctx->ncat > 1) return fail(nctx, NPCF_EINVAL, "edge correction takes single catalogs");
     for (const OrderTable& o : nctx->orders)
         if (o.N == 5) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction is built for orders 3 and 4");
     CU(cudaDeviceSynchronize());
@@ -1055,6 +1250,7 @@ void npcf_destroy(npcf_ctx* ctx) {
     if (!ctx) return;
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     delete ctx;  // device buffers are released by their destructors
 }
 

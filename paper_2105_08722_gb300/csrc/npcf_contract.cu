@@ -4,9 +4,9 @@
 // 3PCF (Eq. N=3-coeff with App. B halving):
 //   zeta_l(b1,b2) = sum_i u_i (l l 0; 0 0 0) sum_{m=-l..l} a^{b1}_{lm} conj(a^{b2}_{lm})
 //                 = sum_i u_i (-1)^l / sqrt(2l+1) [a_{l0} a_{l0} + 2 sum_{m>0} Re(a1 conj a2)].
-// Each block owns a contiguous chunk of cell-sorted primaries and a set of output rows;
-// FP32 sums over the chunk go to a per-chunk FP64 partial, and the reduction adds the
-// partials in chunk order, so results do not depend on scheduling.
+// Each block owns a chunk of cell-sorted primaries (a range within one catalog) and a set
+// of output rows; FP32 sums over the chunk go to the chunk's FP64 partial row, and the
+// reduction adds a catalog's rows in chunk order, so results do not depend on scheduling.
 #include "npcf_device.h"
 
 namespace npcf {
@@ -29,8 +29,8 @@ __global__ void k_contract3(const Contract3Args a) {
     float2* X = reinterpret_cast<float2*>(dsm);
     float* su = reinterpret_cast<float*>(X + kTile * per);
     const int chunk = blockIdx.x;
-    const int p0 = chunk * a.chunk;
-    const int p1 = min(a.n, p0 + a.chunk);
+    const int2 C = a.chunks[chunk];   // primaries [C.x, C.y) of one catalog
+    const int p0 = C.x, p1 = C.y;
     const int r = threadIdx.x;
     int l = 0, b1 = 0, b2 = 0, pr = 0;
     if (r < a.nrows) {
@@ -63,13 +63,32 @@ __global__ void k_contract3(const Contract3Args a) {
         a.partial[(size_t)chunk * a.total + a.out_off + l * a.nbins + pr] = (double)a.coef[l] * (double)acc;
 }
 
-__global__ void k_reduce(const double* __restrict__ partial, int nchunk, int total, int off, int count,
-                         const double* __restrict__ scale, double* __restrict__ zeta) {
+// Catalog blockIdx.y: its chunks' partial rows in order, times the harmonic scale.
+__global__ void k_reduce(const double* __restrict__ partial, const int* __restrict__ cbeg, int total, int off,
+                         int count, const double* __restrict__ scale, double* __restrict__ zeta) {
     const int e = off + blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= off + count) return;
+    const int k = blockIdx.y, r0 = cbeg[k], r1 = cbeg[k + 1];
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += partial[(size_t)c * total + e];
-    zeta[e] += s * scale[e];
+    for (int c = r0; c < r1; ++c) s += partial[(size_t)c * total + e];
+    zeta[(size_t)k * total + e] += s * scale[e];
+}
+
+// Sum of weights of catalog blockIdx.x, in a fixed order (block tree), added to sumw[k].
+__global__ void k_sumw(const float* __restrict__ w, const long long* __restrict__ off, double* sumw) {
+    const int k = blockIdx.x;
+    const long long i0 = off[k], i1 = off[k + 1];
+    double s = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += part[q];
+        sumw[k] += t;
+    }
 }
 
 }  // namespace
@@ -82,10 +101,14 @@ void launch_contract3(const Contract3Args& a, cudaStream_t s) {
     k_contract3<<<a.nchunk, threads, smem, s>>>(a);
 }
 
-void launch_reduce(const double* partial, int nchunk, int total, int off, int count, const double* scale,
-                   double* zeta, cudaStream_t s) {
-    if (count <= 0) return;
-    k_reduce<<<(count + 255) / 256, 256, 0, s>>>(partial, nchunk, total, off, count, scale, zeta);
+void launch_reduce(const double* partial, const int* cbeg, int ncat, int total, int off, int count,
+                   const double* scale, double* zeta, cudaStream_t s) {
+    if (count <= 0 || ncat <= 0) return;
+    k_reduce<<<dim3((count + 255) / 256, ncat), 256, 0, s>>>(partial, cbeg, total, off, count, scale, zeta);
+}
+
+void launch_sumw(const float* w, const long long* off, int ncat, double* sumw, cudaStream_t s) {
+    if (ncat > 0) k_sumw<<<ncat, 512, 0, s>>>(w, off, sumw);
 }
 
 }  // namespace npcf

@@ -12,9 +12,9 @@
 // (b2, b3) sums, also in registers. Coupling coefficients, loop bounds and branches are
 // the same on every lane, so each coefficient is one broadcast load and no lane waits on
 // another; a_lm loads are consecutive across lanes. When the tile is done the warp
-// reduces its sums across lanes (transpose-reduction) and adds them to the block's FP64
-// partial. Tiles of primaries are taken from a global counter, so blocks stay busy to
-// the end.
+// reduces its sums across lanes (transpose-reduction) and adds them to the FP64 partial
+// row of the chunk the tile belongs to. Chunks (ranges of primaries within one catalog)
+// are taken from a global counter, so blocks stay busy to the end.
 #include "npcf_device.h"
 #include "npcf_warp.cuh"
 
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract4w(const Contract4WArgs 
     float4* coef = reinterpret_cast<float4*>(dsm + lay.coef);
     int2* toff = reinterpret_cast<int2*>(dsm + lay.toff);
     int4* segs = reinterpret_cast<int4*>(dsm + lay.segs);
-    __shared__ int tile_s, item_next;
+    __shared__ int chunk_s, item_next;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int rows = a.nr * a.nlm;
@@ -163,20 +163,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract4w(const Contract4WArgs 
         const int4 S = a.segs[i];   // (first term, end, lm of a_{l3 m3}, 2 S(m3) bits)
         segs[i] = make_int4(S.x, S.y, S.z * a.nr * kRS, S.w);
     }
-    double* dst = a.partial + (size_t)blockIdx.x * a.total;
-    for (int i = tid; i < a.nout; i += blockDim.x) dst[a.out_off + i] = 0.0;
-
-    const int ntile = (a.n + kT4 - 1) / kT4;
+    // chunks (primary ranges of one catalog) are taken dynamically; chunk c sums into row c
     for (;;) {
-        if (tid == 0) {
-            tile_s = atomicAdd(a.tile_counter, 1);
-            item_next = 0;
-        }
+        if (tid == 0) chunk_s = atomicAdd(a.chunk_counter, 1);
         __syncthreads();
-        const int tile = tile_s;
-        if (tile >= ntile) break;
-        const int p0 = tile * kT4;
-        const int np = min(kT4, a.n - p0);
+        const int c = chunk_s;
+        if (c >= a.nchunk) break;
+        const int2 C = a.chunks[c];
+        double* dst = a.partial + (size_t)c * a.total;
+        for (int i = tid; i < a.nout; i += blockDim.x) dst[a.out_off + i] = 0.0;
+        for (int p0 = C.x; p0 < C.y; p0 += kT4) {
+        const int np = min(kT4, C.y - p0);
+        if (tid == 0) item_next = 0;
         // stage [lm][b][q] from the pair kernel's [q][b][lm]
         const float2* src = a.alm + (size_t)p0 * rows;
         for (int i = tid; i < kT4 * rows; i += blockDim.x) {
@@ -185,7 +183,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract4w(const Contract4WArgs 
             X[(lm * a.nr + b) * kRS + q] = q < np ? src[i] : make_float2(0.f, 0.f);
         }
         if (tid < kT4) su[tid] = tid < np ? a.wp[p0 + tid] : 0.f;
-        __syncthreads();
+        __syncthreads();   // also orders the row's zeroing before the first sums
         for (;;) {
             int it = 0;
             if (lane == 0) it = atomicAdd(&item_next, 1);
@@ -205,6 +203,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract4w(const Contract4WArgs 
             }
         }
         __syncthreads();
+        }
+        __syncthreads();   // every thread has read chunk_s before it is taken again
     }
 }
 
@@ -214,10 +214,7 @@ size_t contract4w_smem_bytes(const Contract4WArgs& a) {
     return c4_layout(a.nr, a.nlm, a.nterms, a.nseg).total;
 }
 
-int contract4w_blocks(int nsm, int n) {
-    const int ntile = (n + kT4 - 1) / kT4;
-    return std::max(1, std::min(nsm, ntile));
-}
+int contract4w_blocks(int nsm, int nchunk) { return std::max(1, std::min(nsm, nchunk)); }
 
 void launch_contract4w(const Contract4WArgs& a, int nblocks, cudaStream_t s) {
     const size_t smem = contract4w_smem_bytes(a);

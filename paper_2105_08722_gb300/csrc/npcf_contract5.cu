@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(kThreads5) k_contract5(const Contract5Args a) 
     if (threadIdx.x < kMaxT34) t34s[threadIdx.x] = a.blk_t34[blockIdx.y * kMaxT34 + threadIdx.x];
     if (threadIdx.x == 0) nt34 = B.z;
     const int chunk = blockIdx.x;
-    const int p0 = chunk * a.chunk;
-    const int p1 = min(a.n, p0 + a.chunk);
+    const int2 C = a.chunks[chunk];   // primaries [C.x, C.y) of one catalog
+    const int p0 = C.x, p1 = C.y;
     const bool valid = threadIdx.x < B.y;
     const int row = B.x + threadIdx.x;
     int4 ra = make_int4(0, 0, 0, 0), rb = make_int4(0, 0, 0, 0);

@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract4_tc(const Contract4TCA
     tc::fence_after_sync();
     const uint32_t tbase = tmem_base;
 
-    const int p0 = blockIdx.x * a.chunk;
-    const int p1 = min(a.n, p0 + a.chunk);
+    const int2 C = a.chunks[blockIdx.x];   // primaries [C.x, C.y) of one catalog
+    const int p0 = C.x, p1 = C.y;
     const int per = a.nr * a.nlm;
     uint32_t ncommit = 0;   // commits issued so far (thread 0 issues, every thread counts)
     bool ok = true;

@@ -9,9 +9,10 @@
 
 namespace npcf {
 
-// Cartesian cell grid of the neighbour search (cells sorted x fastest, then y, z).
+// Cartesian cell grid of the neighbour search (cells sorted x fastest, then y, z). A batch
+// of catalogs uses one grid per catalog: cell c of catalog k has the global id k ncell + c.
 struct GridInfo {
-    int gx, gy, gz, ncell;
+    int gx, gy, gz, ncell;     // ncell: cells of one catalog's grid
     float ox, oy, oz;      // origin of cell (0,0,0)
     float inv_cell;        // 1 / cell side
     int periodic;
@@ -42,6 +43,8 @@ struct BinArgs {
     uint32_t* cell_of;     // [n] sorted -> cell
     int* err;              // error bits (1: position outside the periodic box / NaN)
     float* bbox_part;      // [nblocks][6] partial min/max (non-periodic)
+    const long long* off;  // [ncat + 1] first point of each catalog (device)
+    int ncat;
 };
 
 void launch_bbox(const float* pos, int n, float* part, int nblocks, cudaStream_t s);
@@ -62,7 +65,8 @@ struct PairArgs {
     const float* kmat;         // [nlm][lmax + 1] Y_lm conversion matrix
     float2* alm;               // [n][nr][nlm]
     uint32_t* cnt;             // [n][nr]
-    unsigned long long* counts;// [nr]
+    unsigned long long* counts;// [ncat][nr]
+    int ncat;                  // catalogs; work units run over catalogs x cell runs
     int n;
     int* work;                 // dynamic cell counter (zeroed by caller)
     int* err;                  // error bits (2: a bounded wait gave up)
@@ -86,7 +90,8 @@ struct Contract3Args {
     const float2* alm;
     const float* wp;
     int n, nr, nlm, lmax;
-    int nchunk, chunk;         // primaries per chunk
+    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
+    int nchunk;
     const int2* rows;          // (l, pair index) rows
     const int2* pairs;         // (b1, b2)
     const float* coef;         // per l
@@ -108,13 +113,15 @@ struct Contract4WArgs {
     int nseg;
     const int4* items;         // (first segment, end, b1 | odd << 8 | (nr - 1 - b1) << 16, first output)
     int nitem;
-    double* partial;           // [blocks][total]
+    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
+    int nchunk;
+    double* partial;           // [nchunk][total]: chunk c sums into row c
     int total, out_off, nout;  // this order's entries: [out_off, out_off + nout)
-    int* tile_counter;         // zeroed before the launch
+    int* chunk_counter;        // zeroed before the launch
 };
 void launch_contract4w(const Contract4WArgs& a, int nblocks, cudaStream_t s);
 size_t contract4w_smem_bytes(const Contract4WArgs& a);
-int contract4w_blocks(int nsm, int n);
+int contract4w_blocks(int nsm, int nchunk);
 
 // 4PCF contraction on the tensor cores (split bf16, fp32 accumulation in tensor memory).
 // Rows (multiplet, b1, b2) are grouped by (l3, parity); each group's rows form 128-row
@@ -124,7 +131,7 @@ struct Contract4TCArgs {
     const float2* alm;
     const float* wp;
     int n, nr, nlm;
-    int chunk;                 // primaries per block
+    const int2* chunks;        // one primary range per block, none crossing a catalog
     const PairTerm* terms;
     int nterms;
     const int4* segs;          // per (multiplet, m3): term range, lm of a_{l3 m3}, 2 S(m3)
@@ -164,7 +171,8 @@ struct Contract5Args {
     const float2* alm;
     const float* wp;
     int n, nr, nlm;
-    int nchunk, chunk;
+    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
+    int nchunk;
     const PairTerm* terms12;
     const int2* segs12;        // term ranges per (l1 l2 l12 triple, m12)
     const int* t12_seg0;       // first segment of each triple
@@ -206,8 +214,10 @@ void launch_edge_solve(const EdgeArgs& a, cudaStream_t s);
 size_t edge_smem_bytes(int nl);
 
 // ---------------------------------------------------------------- FP64 reduction (a6)
-// zeta[e] += scale[e] * sum_{c < nchunk} partial[c][e] for e in [off, off + count)
-void launch_reduce(const double* partial, int nchunk, int total, int off, int count, const double* scale,
-                   double* zeta, cudaStream_t s);
+// For every catalog k (grid row): zeta[k][e] += scale[e] * sum_{cbeg[k] <= c < cbeg[k+1]}
+// partial[c][e], e in [off, off + count); zeta rows are total long.
+void launch_reduce(const double* partial, const int* cbeg, int ncat, int total, int off, int count,
+                   const double* scale, double* zeta, cudaStream_t s);
+void launch_sumw(const float* w, const long long* off, int ncat, double* sumw, cudaStream_t s);
 
 }  // namespace npcf

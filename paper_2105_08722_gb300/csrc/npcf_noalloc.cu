@@ -102,6 +102,11 @@ struct CountArgs {
     unsigned long long* counts;
 };
 
+__global__ void k_set_range(long long* off, long long n) {
+    off[0] = 0;
+    off[1] = n;
+}
+
 __global__ void k_fill_ones(float* w, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) w[i] = 1.0f;
@@ -252,6 +257,8 @@ extern "C" npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, i
     CUN(cudaMemsetAsync(misc, 0, 2 * sizeof(int), s));
     float* w = reinterpret_cast<float*>(base + kOffW);
     k_fill_ones<<<(int)((n + 255) / 256), 256, 0, s>>>(w, (int)n);
+    long long* d_off = reinterpret_cast<long long*>(base + kOffMisc + 64);   // one catalog: {0, n}
+    k_set_range<<<1, 1, 0, s>>>(d_off, (long long)n);
 
     BinArgs b{};
     b.pos = d_pos;
@@ -268,6 +275,8 @@ extern "C" npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, i
     b.idx = reinterpret_cast<uint32_t*>(base + kOffIdx);
     b.cell_of = reinterpret_cast<uint32_t*>(base + kOffCellOf);
     b.err = misc;
+    b.off = d_off;
+    b.ncat = 1;
     launch_bin(b, s);
     CUN(cudaGetLastError());
 

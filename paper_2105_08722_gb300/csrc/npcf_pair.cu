@@ -123,7 +123,7 @@ __device__ __forceinline__ int pair_shell_fast(const float4 pj, const float4 pi,
 // cell-sorted point array: (global start, count, offset in the staging buffer, code).
 // code bits 0-5: periodic shift, 2 bits per axis; bits 6-18: the row's y cell; bits 19-31:
 // its z cell. Computed by one warp; the totals go to shared memory.
-__device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int cy, int cz, int run,
+__device__ void build_segments(const PairArgs& a, const int4* rows, int cbase, int cx, int cy, int cz, int run,
                                int4* segs, int* out_nseg, int* out_total, int lane) {
     const GridInfo& g = a.g;
     int nseg = 0, total = 0;
@@ -141,7 +141,7 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cx, int 
                 ok = yy >= 0 && yy < g.gy && zz >= 0 && zz < g.gz;
             }
             if (ok) {
-                const int base = (zz * g.gy + yy) * g.gx;
+                const int base = cbase + (zz * g.gy + yy) * g.gx;
                 cyz |= (yy << 6) | (zz << 19);   // the row's cell (y, z) rides along for the x-window cut
                 int x0 = cx + rw.z, x1 = cx + run - 1 + rw.w;
                 if (g.periodic) {
@@ -339,7 +339,7 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                                             const int4* segs, int nseg, int total,
                                             int* tpref, int* tdelta, int* tcode, bool trim,
                                             uint16_t* ulist, uint8_t* ushell, uint16_t* slist, float* part,
-                                            int p, int grp, int warp, int lane, const int* slot_org) {
+                                            int p, int cat, int grp, int warp, int lane, const int* slot_org) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
     using R = TR<NC>;
@@ -600,7 +600,7 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     if (gt < nr) {
         const uint32_t c = G.tot[gt];
         a.cnt[(size_t)p * nr + gt] = c;
-        if (c) atomicAdd(&a.counts[gt], (unsigned long long)c);
+        if (c) atomicAdd(&a.counts[(size_t)cat * nr + gt], (unsigned long long)c);
     }
     group_sync(grp);   // partials and totals are reset by the next primary
 }
@@ -647,23 +647,27 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     for (int i = 0; i < R::F; ++i) slot_org[i] = R::origin(i, lane);
     uint32_t parity = 0;
     const int upr = (g.gx + a.run - 1) / a.run;   // units per row of cells
-    const int nunits = upr * g.gy * g.gz;
+    const int ucat = upr * g.gy * g.gz;           // units per catalog
+    const int nunits = ucat * a.ncat;
 
     for (;;) {
         if (threadIdx.x == 0) sh.unit[0] = atomicAdd(a.work, 1);
         __syncthreads();
         const int u = sh.unit[0];
         if (u >= nunits) break;
-        const int row = u / upr, cx = (u % upr) * a.run;
+        // unit u: catalog u / ucat, then a run of x-adjacent cells of that catalog's grid
+        const int cat = u / ucat, uc = u - cat * ucat;
+        const int cbase = cat * g.ncell;
+        const int row = uc / upr, cx = (uc % upr) * a.run;
         const int run = min(a.run, g.gx - cx);
         const int cy = row % g.gy, cz = row / g.gy;
-        const int c0 = (cz * g.gy + cy) * g.gx + cx;
+        const int c0 = cbase + (cz * g.gy + cy) * g.gx + cx;
         const int pbeg = (int)a.cell_start[c0], pend = (int)a.cell_start[c0 + run];
         if (pbeg == pend) {
             __syncthreads();
             continue;
         }
-        if (wblk == 0) build_segments(a, rows, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], lane);
+        if (wblk == 0) build_segments(a, rows, cbase, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], lane);
         __syncthreads();
         const int nseg = sh.unit[1], total = sh.unit[2];
         const bool staged = total <= a.cand_cap;
@@ -696,10 +700,10 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
         for (int p = pbeg + grp; p < pend; p += kG) {
             if (staged)
                 one_primary<L, true>(a, sh, cand, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
-                                     ushell, slist, part, p, grp, warp, lane, slot_org);
+                                     ushell, slist, part, p, cat, grp, warp, lane, slot_org);
             else
                 one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
-                                      ushell, slist, part, p, grp, warp, lane, slot_org);
+                                      ushell, slist, part, p, cat, grp, warp, lane, slot_org);
         }
         __syncthreads();   // both groups are done with the staged points of this unit
     }

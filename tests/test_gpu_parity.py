@@ -500,3 +500,78 @@ def test_survey_full_dmr_sampled_primaries(torch_dev, survey, prec):
     want, _ = oracle.npcf(dr.pos, dr.w, dr.orders, dr.lmax, dr.edges, 0.0, prim=sample)
     assert_orders_close(got, want, dr.orders, dr.lmax, len(dr.edges) - 1,
                         tol=TOL_FP32 if prec == 0 else TOL_BF16)
+
+
+# ------------------------------------------------------------------ batches of catalogs (a8)
+
+def _batch_run(torch_dev, cats, ws, orders, lmax, edges, box, prec=0, repeat=1, tuning=None):
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    est = NPCF(lmax, orders, edges, box, prec)
+    for k, v in (tuning or {}).items():
+        est.set_tuning(k, v)
+    pos = torch.from_numpy(np.ascontiguousarray(np.concatenate(cats), np.float32)).to(dev)
+    w = torch.from_numpy(np.ascontiguousarray(np.concatenate(ws), np.float32)).to(dev)
+    off = np.concatenate([[0], np.cumsum([len(c) for c in cats])])
+    stream = torch.cuda.Stream(dev)   # a capturable stream: the batch runs as a CUDA graph
+    with torch.cuda.stream(stream):
+        for _ in range(repeat):
+            est.accumulate_batch(pos, w, off, stream=stream)
+    stream.synchronize()
+    return est, est.finalize_batch(), est.pair_counts_batch()
+
+
+def test_batch_matches_single_catalog_runs(torch_dev):
+    # catalogs of uneven size (one empty, one with a single point) in one batch: every
+    # catalog's multiplets and counts equal those of its own single-catalog run
+    rng = np.random.default_rng(81)
+    sizes = [700, 0, 1, 2600, 1500]
+    cats = [rng.uniform(0, 120.0, size=(n, 3)).astype(np.float32) for n in sizes]
+    ws = [rng.uniform(0.5, 1.5, size=n).astype(np.float32) for n in sizes]
+    edges = np.linspace(4.0, 30.0, 7)
+    est, got, counts = _batch_run(torch_dev, cats, ws, (3, 4), 4, edges, 120.0)
+    assert est.batch_info() == (len(sizes), 1)
+    for k, (c, w) in enumerate(zip(cats, ws)):
+        if len(c) == 0:
+            assert np.all(got[k] == 0) and np.all(counts[k] == 0)
+            continue
+        _, want, wcounts = gpu_run(torch_dev, c, w, (3, 4), 4, edges, 120.0)
+        assert np.array_equal(counts[k], wcounts), k
+        scale = max(np.sqrt(np.mean(want ** 2)), 1e-300)
+        assert np.max(np.abs(got[k] - want)) <= TOL_FP32 * scale, k
+
+
+def test_batch_graph_replay_coadds_and_mode_errors(torch_dev):
+    from paper_2105_08722_gb300._lib import NPCFError
+    rng = np.random.default_rng(82)
+    cats = [rng.uniform(0, 100.0, size=(n, 3)).astype(np.float32) for n in (900, 1300)]
+    ws = [np.ones(len(c), np.float32) for c in cats]
+    edges = np.linspace(4.0, 25.0, 6)
+    est1, once, c1 = _batch_run(torch_dev, cats, ws, (3, 4), 3, edges, 100.0)
+    est3, thrice, c3 = _batch_run(torch_dev, cats, ws, (3, 4), 3, edges, 100.0, repeat=3)
+    assert est3.batch_info() == (2, 3)   # captured once, launched as a graph three times
+    assert np.array_equal(c3, 3 * c1)
+    assert np.max(np.abs(thrice - 3 * once)) <= 1e-12 * np.max(np.abs(once))
+    with pytest.raises(NPCFError):   # a batch context is read with the batch calls
+        est3.finalize()
+    torch, dev = torch_dev
+    single = torch.from_numpy(cats[0]).to(dev)
+    with pytest.raises(NPCFError):   # one catalog into accumulators that hold two
+        est3.accumulate(single, torch.ones(len(cats[0]), device=dev))
+    est3.reset()
+    est3.accumulate(single, torch.ones(len(cats[0]), device=dev))
+    assert est3.batch_info()[0] == 1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lognormal_batch_against_oracle(torch_dev, prec):
+    # three log-normal periodic catalogs of different sizes in one batch, each against the
+    # oracle; FP32 and split-bf16 contractions
+    cats = [catalogs.lognormal_box(n, 300.0, 32, seed=5100 + n) for n in (1200, 2500, 1800)]
+    ws = [np.ones(len(c), np.float32) for c in cats]
+    edges = np.linspace(8.0, 60.0, 9)
+    _, got, counts = _batch_run(torch_dev, cats, ws, (3, 4), 4, edges, 300.0, prec=prec)
+    for k, c in enumerate(cats):
+        want, wcounts = oracle.npcf(c, ws[k], (3, 4), 4, edges, 300.0)
+        assert np.array_equal(counts[k], wcounts), k
+        assert_orders_close(got[k], want, (3, 4), 4, 8, tol=TOL_FP32 if prec == 0 else TOL_BF16)
