@@ -142,6 +142,16 @@ npcf_status npcf_finalize_batch(npcf_ctx* ctx, double* out, size_t out_len, int 
 /* Per-catalog pair counts, host uint64 out[ncat][nr] (synchronises). */
 npcf_status npcf_pair_counts_batch(npcf_ctx* ctx, uint64_t* out, size_t out_len);
 
+/* Autotuner: runs the pipeline on the catalog (d_pos, d_w, n as in npcf_accumulate) for
+ * candidate settings and keeps the fastest: pair kernel (median of three timed runs after a
+ * warm-up) over cells per r_max {4, 5, 6} x cells per work unit {2, 3, 4} x list capacity
+ * {4096, 6144}, then the contractions over primaries per chunk (1, 2, 4 or 8 waves of
+ * chunks over the SMs). The accumulators must be empty (fresh context or npcf_reset) and
+ * are reset afterwards. chosen (nullable, host int[4]) receives the settings: tuning keys
+ * 0, 5, 3 and 2. Synchronises the stream; takes some tens of pipeline runs. */
+npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream,
+                          int* chosen);
+
 /* Catalogs the accumulators hold (0 before the first accumulate call) and how many batch
  * calls were run as CUDA-graph launches. Either pointer may be NULL. */
 npcf_status npcf_batch_info(const npcf_ctx* ctx, int* ncat, int64_t* graph_launches);

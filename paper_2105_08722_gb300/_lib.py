@@ -40,6 +40,7 @@ SIGNATURES = {
     "npcf_finalize_batch": (_i, [_vp, _vp, _sz, _i]),
     "npcf_pair_counts_batch": (_i, [_vp, _vp, _sz]),
     "npcf_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64)]),
+    "npcf_autotune": (_i, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "npcf_gaunt": (_i, [_i, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
@@ -175,6 +176,15 @@ class NPCF:
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self._check(self._lib.npcf_accumulate_batch(self._h, _ptr(pos), _ptr(w), off.ctypes.data, len(off) - 1,
                                                     _stream_handle(stream)))
+
+    def autotune(self, pos, w, stream=None) -> Dict[str, int]:
+        """Pick the fastest pair-kernel and contraction settings for this catalog
+        (npcf_autotune); the accumulators are left empty."""
+        chosen = np.zeros(4, dtype=np.int32)
+        self._check(self._lib.npcf_autotune(self._h, _ptr(pos), _ptr(w), int(pos.shape[0]),
+                                            _stream_handle(stream), chosen.ctypes.data))
+        return {"cells_per_rmax": int(chosen[0]), "cell_run": int(chosen[1]), "pair_cap": int(chosen[2]),
+                "chunk": int(chosen[3])}
 
     def batch_info(self) -> Tuple[int, int]:
         k, g = ctypes.c_int(), ctypes.c_int64()

@@ -1046,6 +1046,76 @@ npcf_status npcf_accumulate_batch(npcf_ctx* ctx, const float* d_pos, const float
     return run_batch(ctx, d_pos, d_w, off, (cudaStream_t)stream);
 }
 
+npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream,
+                          int* chosen) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (ctx->ncat != 0) return fail(ctx, NPCF_EINVAL, "autotune needs empty accumulators (npcf_reset first)");
+    if (n <= 0 || !d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "autotune needs a non-empty catalog");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool was_timed = ctx->timed;
+    ctx->timed = true;
+    // median of three timed runs of one stage (after one warm-up run)
+    auto stage_ms = [&](int stage, float* ms) -> npcf_status {
+        float t[3];
+        for (int r = 0; r < 4; ++r) {
+            npcf_status st = run_accumulate(ctx, d_pos, d_w, nullptr, n, s);
+            if (st != NPCF_OK) return st;
+            CU(cudaEventSynchronize(ctx->ev[stage + 1]));
+            if (r > 0) CU(cudaEventElapsedTime(&t[r - 1], ctx->ev[stage], ctx->ev[stage + 1]));
+        }
+        std::sort(t, t + 3);
+        *ms = t[1];
+        return NPCF_OK;
+    };
+    const int keep[4] = {ctx->cells_per_rmax, ctx->cell_run, ctx->pair_cap, ctx->chunk_target};
+    int best[4] = {keep[0], keep[1], keep[2], keep[3]};
+    float best_ms = 1e30f;
+    // pair kernel: grid cell size, cells per work unit, neighbour-list capacity
+    for (int k : {4, 5, 6})
+        for (int run : {2, 3, 4})
+            for (int cap : {4096, 6144}) {
+                ctx->cells_per_rmax = k;
+                ctx->cell_run = run;
+                ctx->pair_cap = cap;
+                float ms = 0.f;
+                if (stage_ms(1, &ms) != NPCF_OK) continue;   // e.g. no room to stage: skip
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best[0] = k;
+                    best[1] = run;
+                    best[2] = cap;
+                }
+            }
+    ctx->cells_per_rmax = best[0];
+    ctx->cell_run = best[1];
+    ctx->pair_cap = best[2];
+    // contractions: primaries per chunk (waves of chunks over the SMs)
+    best_ms = 1e30f;
+    for (int waves : {1, 2, 4, 8}) {
+        ctx->chunk_target = (int)std::max<int64_t>(64, (n + (int64_t)waves * ctx->nsm - 1) / ((int64_t)waves * ctx->nsm));
+        float ms = 0.f;
+        if (stage_ms(2, &ms) != NPCF_OK) continue;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best[3] = ctx->chunk_target;
+        }
+    }
+    ctx->chunk_target = best[3];
+    ctx->timed = was_timed;
+    npcf_status st = npcf_reset(ctx);
+    if (st != NPCF_OK) return st;
+    if (best_ms >= 1e30f) {
+        ctx->cells_per_rmax = keep[0];
+        ctx->cell_run = keep[1];
+        ctx->pair_cap = keep[2];
+        ctx->chunk_target = keep[3];
+        return fail(ctx, NPCF_EINVAL, "autotune: no candidate setting ran");
+    }
+    if (chosen)
+        for (int i = 0; i < 4; ++i) chosen[i] = best[i];
+    return NPCF_OK;
+}
+
 npcf_status npcf_batch_info(const npcf_ctx* ctx, int* ncat, int64_t* graph_launches) {
     if (!ctx) return NPCF_EINVAL;
     if (ncat) *ncat = ctx->ncat;

@@ -41,7 +41,9 @@ __global__ void k_contract3(const Contract3Args a) {
         b1 = bb.x;
         b2 = bb.y;
     }
-    float acc = 0.f;
+    // FP32 sums over one tile of primaries, folded into FP64 after every tile, so the
+    // rounding does not grow with the chunk length
+    double dacc = 0.0;
     const int lm0 = l * (l + 1) / 2;
     for (int t0 = p0; t0 < p1; t0 += kTile) {
         const int np = min(kTile, p1 - t0);
@@ -49,6 +51,7 @@ __global__ void k_contract3(const Contract3Args a) {
         stage_tile(a.alm, a.wp, t0, np, per, X, su);
         __syncthreads();
         if (r < a.nrows) {
+            float acc = 0.f;
             for (int q = 0; q < np; ++q) {
                 const float2* A1 = X + q * per + b1 * a.nlm + lm0;
                 const float2* A2 = X + q * per + b2 * a.nlm + lm0;
@@ -57,10 +60,11 @@ __global__ void k_contract3(const Contract3Args a) {
                 for (int m = 1; m <= l; ++m) s2 = fmaf(A1[m].x, A2[m].x, fmaf(A1[m].y, A2[m].y, s2));
                 acc = fmaf(su[q], fmaf(2.f, s2, s), acc);
             }
+            dacc += (double)acc;
         }
     }
     if (r < a.nrows && chunk < a.nchunk)
-        a.partial[(size_t)chunk * a.total + a.out_off + l * a.nbins + pr] = (double)a.coef[l] * (double)acc;
+        a.partial[(size_t)chunk * a.total + a.out_off + l * a.nbins + pr] = (double)a.coef[l] * dacc;
 }
 
 // Catalog blockIdx.y: its chunks' partial rows in order, times the harmonic scale.

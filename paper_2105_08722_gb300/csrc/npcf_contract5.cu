@@ -18,6 +18,7 @@ namespace {
 
 constexpr int kTile5 = 8;     // primaries staged per pass
 constexpr int kThreads5 = 256;
+constexpr int kFold5 = 4;     // tiles between folds of the FP32 sums into FP64
 
 __device__ __forceinline__ void pair_product(const PairTerm& t, float2 x1, float2 x2, float& pr, float& pi) {
     pr = fmaf(t.cA * x1.x, x2.x, pr);
@@ -55,6 +56,12 @@ __global__ void __launch_bounds__(kThreads5) k_contract5(const Contract5Args a) 
     float acc[kMaxPairs5];
 #pragma unroll
     for (int k = 0; k < kMaxPairs5; ++k) acc[k] = 0.f;
+    // this thread's outputs in the chunk's FP64 row: the FP32 sums are added there every
+    // kFold5 tiles, so the rounding does not grow with the chunk length
+    double* dst = a.partial + (size_t)chunk * a.total + ra.w;
+    if (valid && chunk < a.nchunk)
+        for (int k = 0; k < np; ++k) dst[k] = 0.0;
+    int tiles = 0;
     __syncthreads();
 
     for (int s0 = p0; s0 < p1; s0 += kTile5) {
@@ -113,12 +120,17 @@ __global__ void __launch_bounds__(kThreads5) k_contract5(const Contract5Args a) 
             }
             __syncthreads();
         }
-    }
-    if (valid && chunk < a.nchunk) {
-        double* dst = a.partial + (size_t)chunk * a.total + ra.w;
+        if (++tiles == kFold5 || s0 + kTile5 >= p1) {
+            if (valid && chunk < a.nchunk) {
 #pragma unroll
-        for (int k = 0; k < kMaxPairs5; ++k)
-            if (k < np) dst[k] = (double)acc[k];
+                for (int k = 0; k < kMaxPairs5; ++k)
+                    if (k < np) {
+                        dst[k] += (double)acc[k];
+                        acc[k] = 0.f;
+                    }
+            }
+            tiles = 0;
+        }
     }
 }
 

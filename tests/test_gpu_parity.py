@@ -575,3 +575,21 @@ def test_lognormal_batch_against_oracle(torch_dev, prec):
         want, wcounts = oracle.npcf(c, ws[k], (3, 4), 4, edges, 300.0)
         assert np.array_equal(counts[k], wcounts), k
         assert_orders_close(got[k], want, (3, 4), 4, 8, tol=TOL_FP32 if prec == 0 else TOL_BF16)
+
+
+def test_autotune_picks_candidates_and_leaves_sums_empty(torch_dev):
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    pos = catalogs.lognormal_box(20000, 500.0, 64, seed=91)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(10.0, 80.0, 8)
+    tp, tw = torch.from_numpy(pos).to(dev), torch.from_numpy(w).to(dev)
+    est = NPCF(4, (3, 4), edges, 500.0)
+    chosen = est.autotune(tp, tw)
+    assert chosen["cells_per_rmax"] in (4, 5, 6) and chosen["cell_run"] in (2, 3, 4)
+    assert chosen["pair_cap"] in (4096, 6144) and chosen["chunk"] >= 64
+    assert est.batch_info()[0] == 0 and np.all(est.finalize() == 0)
+    est.accumulate(tp, tw)
+    got = est.finalize()
+    _, want, _ = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 500.0)
+    assert np.max(np.abs(got - want)) <= TOL_FP32 * np.sqrt(np.mean(want ** 2))
