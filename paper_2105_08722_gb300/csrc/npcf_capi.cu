@@ -123,6 +123,10 @@ struct npcf_ctx {
     std::vector<int2> h_chunks;
     DevBuf<int> cbeg;
     std::vector<int> h_cbeg;
+    DevBuf<int2> chunks4;          // coarser chunks of the FP32 4PCF kernel
+    std::vector<int2> h_chunks4;
+    DevBuf<int> cbeg4;
+    std::vector<int> h_cbeg4;
     // CUDA graph of the last batch shape
     cudaGraphExec_t gexec = nullptr;
     std::vector<uintptr_t> gsig;
@@ -469,7 +473,7 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s)
 
 // Host plan of one accumulate call: a single catalog is a batch of one.
 struct Plan {
-    int n = 0, ncat = 0, nchunk = 0;
+    int n = 0, ncat = 0, nchunk = 0, nchunk4 = 0;
     PairArgs pa{};
 };
 
@@ -538,6 +542,26 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         cbeg.push_back((int)chunks.size());
     }
     P.nchunk = (int)chunks.size();
+    // the FP32 4PCF kernel takes chunks dynamically and writes one FP64 row per chunk: a
+    // coarser table (about one chunk per SM and catalog, whole 64-primary tiles) keeps the
+    // rows few and the tiles full
+    const long long C4 = std::max(64LL, ((n64 + ctx->nsm - 1) / ctx->nsm + 63) / 64 * 64);
+    std::vector<int2> chunks4;
+    std::vector<int> cbeg4(1, 0);
+    for (int k = 0; k < ncat; ++k) {
+        for (long long p = off[k]; p < off[k + 1]; p += C4)
+            chunks4.push_back(make_int2((int)p, (int)std::min(off[k + 1], p + C4)));
+        cbeg4.push_back((int)chunks4.size());
+    }
+    P.nchunk4 = (int)chunks4.size();
+    if (!same_table(ctx->chunks4, ctx->h_chunks4, chunks4)) {
+        CU(upload(ctx->chunks4, chunks4));
+        ctx->h_chunks4 = chunks4;
+    }
+    if (!same_table(ctx->cbeg4, ctx->h_cbeg4, cbeg4)) {
+        CU(upload(ctx->cbeg4, cbeg4));
+        ctx->h_cbeg4 = cbeg4;
+    }
     if (!same_table(ctx->d_off, ctx->h_off, off)) {
         CU(upload(ctx->d_off, off));
         ctx->h_off = off;
@@ -550,7 +574,7 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         CU(upload(ctx->cbeg, cbeg));
         ctx->h_cbeg = cbeg;
     }
-    CU(ctx->partial.ensure((size_t)std::max(P.nchunk, 1) * std::max(ctx->total, 1)));
+    CU(ctx->partial.ensure((size_t)std::max({P.nchunk, P.nchunk4, 1}) * std::max(ctx->total, 1)));
 
     PairArgs& pa = P.pa;
     pa = PairArgs{};
@@ -739,14 +763,14 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.nseg = ctx->c4nseg;
             c.items = ctx->c4items.p;
             c.nitem = ctx->c4nitem;
-            c.chunks = ctx->chunks.p;
-            c.nchunk = P.nchunk;
+            c.chunks = ctx->chunks4.p;
+            c.nchunk = P.nchunk4;
             c.partial = ctx->partial.p;
             c.total = ctx->total;
             c.out_off = ctx->order_off[k];
             c.nout = o.n_lambda() * o.n_bins();
             c.chunk_counter = ctx->work.p + 1;
-            launch_contract4w(c, contract4w_blocks(ctx->nsm, P.nchunk), s);
+            launch_contract4w(c, contract4w_blocks(ctx->nsm, P.nchunk4), s);
         } else if (o.N == 5) {
             if (ctx->c5nrows == 0) continue;
             Contract5Args c{};
@@ -788,8 +812,9 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
     if (timed) CU(cudaEventRecord(ctx->ev[3], s));
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
-        launch_reduce(ctx->partial.p, ctx->cbeg.p, ncat, ctx->total, ctx->order_off[k], o.n_lambda() * o.n_bins(),
-                      ctx->zscale.p, ctx->zeta.p, s);
+        const bool coarse = o.N == 4 && ctx->prec == NPCF_FP32;
+        launch_reduce(ctx->partial.p, coarse ? ctx->cbeg4.p : ctx->cbeg.p, ncat, ctx->total, ctx->order_off[k],
+                      o.n_lambda() * o.n_bins(), ctx->zscale.p, ctx->zeta.p, s);
     }
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecord(ctx->ev[4], s));
@@ -829,6 +854,7 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
         (uintptr_t)ctx->count.p, (uintptr_t)ctx->start.p, (uintptr_t)ctx->cursor.p, (uintptr_t)ctx->work.p,
         (uintptr_t)ctx->partial.p, (uintptr_t)ctx->zeta.p, (uintptr_t)ctx->counts.p, (uintptr_t)ctx->sumw.p,
         (uintptr_t)ctx->d_off.p, (uintptr_t)ctx->chunks.p, (uintptr_t)ctx->cbeg.p, (uintptr_t)ctx->rows.p,
+        (uintptr_t)ctx->chunks4.p, (uintptr_t)ctx->cbeg4.p, (uintptr_t)P.nchunk4,
         (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.run, (uintptr_t)P.pa.cap,
         (uintptr_t)P.pa.cand_cap, (uintptr_t)P.pa.trim, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
     for (long long v : off) sig.push_back((uintptr_t)v);

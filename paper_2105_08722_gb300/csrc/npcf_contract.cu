@@ -78,12 +78,14 @@ __global__ void k_reduce(const double* __restrict__ partial, const int* __restri
     zeta[(size_t)k * total + e] += s * scale[e];
 }
 
-// Sum of weights of catalog blockIdx.x, in a fixed order (block tree), added to sumw[k].
+// Sum of weights of catalog blockIdx.y (the blocks along x share its range), added to
+// sumw[k] (only the normalisation uses it).
 __global__ void k_sumw(const float* __restrict__ w, const long long* __restrict__ off, double* sumw) {
-    const int k = blockIdx.x;
+    const int k = blockIdx.y;
     const long long i0 = off[k], i1 = off[k + 1];
     double s = 0.0;
-    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += w[i];
+    for (long long i = i0 + blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (long long)gridDim.x * blockDim.x)
+        s += w[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ double part[32];
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -91,7 +93,7 @@ __global__ void k_sumw(const float* __restrict__ w, const long long* __restrict_
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += part[q];
-        sumw[k] += t;
+        atomicAdd(&sumw[k], t);
     }
 }
 
@@ -112,7 +114,7 @@ void launch_reduce(const double* partial, const int* cbeg, int ncat, int total, 
 }
 
 void launch_sumw(const float* w, const long long* off, int ncat, double* sumw, cudaStream_t s) {
-    if (ncat > 0) k_sumw<<<ncat, 512, 0, s>>>(w, off, sumw);
+    if (ncat > 0) k_sumw<<<dim3(32, ncat), 512, 0, s>>>(w, off, sumw);
 }
 
 }  // namespace npcf
