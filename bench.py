@@ -116,12 +116,24 @@ def cpu_oracle_rate(wl, sample_n: int, seed: int = 77):
     return sample_n / dt, cores, "%d seeded primaries of the 200k catalog against all 200k secondaries" % sample_n
 
 
+def c2_workload(n_points):
+    """The 200k log-normal workload, or the same density and spectrum at n_points (box
+    scaled by (n/200k)^(1/3); a smaller case for profiling)."""
+    from paper_2105_08722_gb300 import catalogs
+    if not n_points or n_points == 200_000:
+        return catalogs.c2_lognormal_4pcf()
+    box = 1000.0 * (n_points / 200_000) ** (1.0 / 3.0)
+    pos = catalogs.lognormal_box(n_points, box, 256, seed=1002)
+    return catalogs.Workload("lognormal_%dk_L%d_4pcf3pcf_lmax5_nr10_20-160" % (n_points // 1000, round(box)), pos,
+                             np.ones(n_points, np.float32), catalogs.linear_edges(20.0, 160.0, 10), 5, (3, 4), box)
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return 0
     from paper_2105_08722_gb300 import catalogs
-    wl = catalogs.c2_lognormal_4pcf()
+    wl = c2_workload(args.n)
     sample_n = args.ref_sample
     times = []
     for step in range(args.warmup + args.steps):
@@ -135,7 +147,7 @@ def run_reference(args):
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_points": wl.n, "lmax": wl.lmax, "nr": 10,
+        "config": {"workload": WORKLOAD if wl.n == 200_000 else wl.name, "n_points": wl.n, "lmax": wl.lmax, "nr": 10,
                    "orders": [3, 4], "step": "%d primaries (bounded sample)" % sample_n},
         "cpu_baseline": {"value": value, "unit": "primaries/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
@@ -159,7 +171,7 @@ def run_gpu(args):
     build()
     from paper_2105_08722_gb300._lib import NPCF, FP32, SPLIT_BF16
 
-    wl = catalogs.c2_lognormal_4pcf()
+    wl = c2_workload(args.n)
     prec = SPLIT_BF16 if args.precision == "bf16" else FP32
     est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, prec)
     pos = torch.from_numpy(wl.pos).to(dev)
@@ -411,6 +423,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16"],
                     help="contraction arithmetic (default fp32; bf16 for the batch workload)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="points of the c2 workload at the same density (default 200,000)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
                     help="c2: one 200k log-normal catalog; c5: 64 catalogs in one batch")
     ap.add_argument("--cpu-sample", type=int, default=1500)
