@@ -35,6 +35,28 @@ PAIR_ALG_FLOP = 180                                  # per accepted pair at lmax
 N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 KERNELS_PER_STEP = 10  # k_sumw, 4 cell-list kernels, pair, contract3, contract4, one reduce per order
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu pass) on the
+# 200k workload, with the SHA-256 prefix of the kernel's source when they were taken; the
+# roofline reports them only while the source is unchanged (profiles/ has the captures).
+TRAFFIC = {
+    "pair": {"bytes": 8_026_112 + 284_108_800, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
+             "sha256": "752f4b3b89cee01b"},
+}
+
+
+def _traffic(kernel):
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    try:
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes"]
+
 
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
@@ -284,7 +306,8 @@ def run_gpu(args):
                       "reduction": float(st[3])},
         "pairs_per_step": npairs_per_step,
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": _traffic(dominant) if wl.n == 200_000 else None,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
         "clocks": clk,
         "other_precision": other,
@@ -415,6 +438,64 @@ def run_gpu_batch(args):
     return 0
 
 
+def run_gpu_c4(args):
+    """5PCF: 100k log-normal points, periodic 1000 Mpc/h, 8 shells 20-160, lmax 4 (all
+    5PCF multiplets with l12 <= 2 lmax). One step = one npcf_accumulate."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    wl = catalogs.c4_lognormal_5pcf()
+    est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, FP32)
+    pos = torch.from_numpy(wl.pos).to(dev)
+    w = torch.from_numpy(wl.w).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        est.accumulate(pos, w)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, st = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        est.accumulate(pos, w)
+        b.record(stream)
+        st.append(est.timings())
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    st = np.mean(np.array(st, dtype=np.float64), axis=0)
+    t = float(np.mean(ms))
+    # useful 5PCF flop per primary (SURVEY figures: P12 + P34 builds and the final products)
+    alg = wl.n * (543_200 * 2 + 1_110_200)
+    fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = alg / (st[2] * 1e-3) / 1e12
+    line = {
+        "metric": "primaries/sec for the 5PCF (lmax=4, 8 shells)", "value": wl.n / (t * 1e-3),
+        "unit": "primaries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "lognormal_100k_L1000_5pcf_lmax4_nr8_20-160", "n_points": wl.n,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
+        "gpu_launches": (KERNELS_PER_STEP - 2) * args.steps,
+        "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
+                      "reduction": float(st[3])},
+        "roofline": {"bound": "alu", "kernel": "contraction (5PCF)", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,8 +506,9 @@ def main():
                     help="contraction arithmetic (default fp32; bf16 for the batch workload)")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the c2 workload at the same density (default 200,000)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
-                    help="c2: one 200k log-normal catalog; c5: 64 catalogs in one batch")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+                    help="c2: one 200k log-normal catalog (4PCF + 3PCF); c4: 100k, 5PCF; "
+                         "c5: 64 catalogs in one batch")
     ap.add_argument("--cpu-sample", type=int, default=1500)
     ap.add_argument("--ref-sample", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -441,6 +523,8 @@ def main():
         return run_reference(args)
     if args.workload == "c5":
         return run_gpu_batch(args)
+    if args.workload == "c4":
+        return run_gpu_c4(args)
     return run_gpu(args)
 
 
