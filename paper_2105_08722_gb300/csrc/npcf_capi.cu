@@ -94,7 +94,8 @@ struct npcf_ctx {
     int tc_ngroup = 0, tc_ntile = 0, tc_ncombo = 0, tc_nbslab = 0, tc_maxcomp = 0;
     int off4 = 0, nb4 = 0;
     // 5PCF contraction tables
-    DevBuf<PairTerm> c5terms12, c5terms34;
+    DevBuf<float4> c5c12, c5c34;
+    DevBuf<uint32_t> c5i12, c5i34;
     DevBuf<int2> c5segs12, c5segs34, c5pairs;
     DevBuf<int> c5t12seg0, c5t34seg0, c5t34l12, c5blkt34;
     DevBuf<int4> c5rowsA, c5rowsB, c5blocks;
@@ -261,6 +262,7 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
     while (r < rows.size()) {
         const int first = (int)r;
         std::vector<int> trip;
+        std::vector<std::pair<Row, int>> blk;   // rows of this block with their local triple
         while (r < rows.size() && (int)(r - first) < 256) {
             int loc = -1;
             for (size_t q = 0; q < trip.size(); ++q)
@@ -270,13 +272,21 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
                 trip.push_back(rows[r].t34);
                 loc = (int)trip.size() - 1;
             }
-            const Row& R = rows[r];
+            blk.push_back({rows[r], loc});
+            ++r;
+        }
+        // by b2 within the block: a warp's rows then share the number of pairs after b2
+        std::stable_sort(blk.begin(), blk.end(), [](const std::pair<Row, int>& x, const std::pair<Row, int>& y) {
+            return x.first.b2 < y.first.b2;
+        });
+        for (const auto& br : blk) {
+            const Row& R = br.first;
+            const int loc = br.second;
             const int* L = &o.lam[(size_t)R.lam * 5];
             const int np = (nr - 1 - R.b2) * (nr - 2 - R.b2) / 2;
             rowsA.push_back(make_int4(R.lam, R.b1, R.b2, off + R.lam * o.n_bins() + bin_index(R.b1, R.b2, R.b2 + 1, R.b2 + 2)));
             rowsB.push_back(make_int4(R.t12, loc, pair_index(R.b2 + 1, R.b2 + 2), np));
             rowsC.push_back(make_float2((float)std::sqrt(2.0 * L[2] + 1.0), o.odd(R.lam) ? 1.f : 0.f));
-            ++r;
         }
         blocks.push_back(make_int4(first, (int)r - first, (int)trip.size(), 0));
         for (int q = 0; q < kMaxT34; ++q) blk_t34.push_back(q < (int)trip.size() ? trip[q] : 0);
@@ -294,8 +304,20 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
     ctx->c5nterms34 = (int)t.terms34.size();
     ctx->c5nseg12 = (int)s12.size();
     ctx->c5nseg34 = (int)s34.size();
-    CU(upload(ctx->c5terms12, t.terms12));
-    CU(upload(ctx->c5terms34, t.terms34));
+    std::vector<float4> c12, c34;
+    std::vector<uint32_t> i12, i34;
+    for (const PairTerm& q : t.terms12) {
+        c12.push_back(make_float4(q.cA, q.cB, q.cC, q.cD));
+        i12.push_back((uint32_t)q.lm1 | ((uint32_t)q.lm2 << 16));
+    }
+    for (const PairTerm& q : t.terms34) {
+        c34.push_back(make_float4(q.cA, q.cB, q.cC, q.cD));
+        i34.push_back((uint32_t)q.lm1 | ((uint32_t)q.lm2 << 16));
+    }
+    CU(upload(ctx->c5c12, c12));
+    CU(upload(ctx->c5i12, i12));
+    CU(upload(ctx->c5c34, c34));
+    CU(upload(ctx->c5i34, i34));
     CU(upload(ctx->c5segs12, s12));
     CU(upload(ctx->c5segs34, s34));
     CU(upload(ctx->c5pairs, pairs));
@@ -781,10 +803,12 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.nlm = ctx->nlm;
             c.chunks = ctx->chunks.p;
             c.nchunk = P.nchunk;
-            c.terms12 = ctx->c5terms12.p;
+            c.c12 = ctx->c5c12.p;
+            c.i12 = ctx->c5i12.p;
             c.segs12 = ctx->c5segs12.p;
             c.t12_seg0 = ctx->c5t12seg0.p;
-            c.terms34 = ctx->c5terms34.p;
+            c.c34 = ctx->c5c34.p;
+            c.i34 = ctx->c5i34.p;
             c.segs34 = ctx->c5segs34.p;
             c.t34_seg0 = ctx->c5t34seg0.p;
             c.t34_l12 = ctx->c5t34l12.p;

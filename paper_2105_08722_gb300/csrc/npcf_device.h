@@ -173,10 +173,12 @@ struct Contract5Args {
     int n, nr, nlm;
     const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
     int nchunk;
-    const PairTerm* terms12;
+    const float4* c12;         // coupling terms (cA, cB, cC, cD) of P12
+    const uint32_t* i12;       // their lm1 | lm2 << 16
     const int2* segs12;        // term ranges per (l1 l2 l12 triple, m12)
     const int* t12_seg0;       // first segment of each triple
-    const PairTerm* terms34;
+    const float4* c34;
+    const uint32_t* i34;
     const int2* segs34;
     const int* t34_seg0;
     const int* t34_l12;
