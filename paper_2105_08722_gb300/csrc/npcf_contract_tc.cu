@@ -25,7 +25,7 @@ namespace npcf {
 namespace {
 
 constexpr int kKStep = 16;        // primaries per K slab
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr uint32_t kIdesc = tc::idesc_bf16(128, 16);
 constexpr uint32_t kATerm = 4096, kASlab = 3 * kATerm;   // 128 x 16 bf16 per term
 constexpr uint32_t kBTerm = 512, kBSlab = 3 * kBTerm;    // 16 x 16 bf16 per term
