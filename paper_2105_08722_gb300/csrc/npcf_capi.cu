@@ -88,7 +88,8 @@ struct npcf_ctx {
     DevBuf<int> c4lamseg0;
     int c4nitem = 0, c4nterms = 0, c4nseg = 0, c4nlam = 0;
     // tensor-core (split bf16) 4PCF contraction tables
-    DevBuf<int4> tc_groups, tc_tiles;
+    DevBuf<int4> tc_groups, tc_tiles, tc_runs;
+    DevBuf<int> tc_tile_run0;
     DevBuf<int> tc_group_lams, tc_group_bslab, tc_combo_bin;
     DevBuf<int2> tc_combos;
     int tc_ngroup = 0, tc_ntile = 0, tc_ncombo = 0, tc_nbslab = 0, tc_maxcomp = 0;
@@ -209,6 +210,37 @@ npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTa
         return fail(ctx, NPCF_EUNSUPPORTED, "split-bf16 4PCF: %zu accumulator tiles exceed tensor memory "
                     "(at most 32; use fewer shells, a lower lmax or parity-even multiplets)", tiles.size());
     (void)nr;
+    // runs of a tile's rows sharing (multiplet, b1) with consecutive b2 (at most 4): the
+    // P-build loads coefficients and a^{b1} once per run
+    std::vector<int4> runs;
+    std::vector<int> tile_run0;
+    for (const int4& T : tiles) {
+        tile_run0.push_back((int)runs.size());
+        const int4& G = groups[T.x];
+        int4 cur = make_int4(-1, 0, -1, -1);
+        int prev_b2 = -1;
+        for (int rr = 0; rr < T.z; ++rr) {
+            const int grow = T.y + rr;
+            const int lam = glams[G.z + grow / (int)combos.size()];
+            const int2 bb = combos[grow % combos.size()];
+            const bool same = cur.x >= 0 && cur.z == lam && (cur.w & 0xff) == bb.x && bb.y == prev_b2 + 1 &&
+                              cur.y < 4;
+            if (same) {
+                ++cur.y;
+            } else {
+                if (cur.x >= 0) runs.push_back(cur);
+                cur = make_int4(rr, 1, lam, bb.x | (bb.y << 8));
+            }
+            prev_b2 = bb.y;
+        }
+        if (cur.x >= 0) runs.push_back(cur);
+        // longest first: groups take runs round-robin, so this keeps their row counts even
+        std::stable_sort(runs.begin() + tile_run0.back(), runs.end(),
+                         [](const int4& x, const int4& y) { return x.y > y.y; });
+    }
+    tile_run0.push_back((int)runs.size());
+    CU(upload(ctx->tc_runs, runs));
+    CU(upload(ctx->tc_tile_run0, tile_run0));
     ctx->tc_ngroup = (int)groups.size();
     ctx->tc_ntile = (int)tiles.size();
     ctx->tc_ncombo = (int)combos.size();
@@ -758,6 +790,8 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.ngroup = ctx->tc_ngroup;
             c.tiles = ctx->tc_tiles.p;
             c.ntile = ctx->tc_ntile;
+            c.runs = ctx->tc_runs.p;
+            c.tile_run0 = ctx->tc_tile_run0.p;
             c.combos = ctx->tc_combos.p;
             c.combo_bin = ctx->tc_combo_bin.p;
             c.ncombo = ctx->tc_ncombo;

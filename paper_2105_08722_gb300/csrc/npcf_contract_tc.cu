@@ -63,6 +63,50 @@ __device__ __forceinline__ void split_store(unsigned char* slab, uint32_t off, f
     *reinterpret_cast<__nv_bfloat16*>(slab + 2 * term + off) = lo;
 }
 
+// P of a run of N rows (multiplet L, b1, b2 = b2first .. b2first + N - 1) for primary k of
+// the step, every segment m3 of L, written as three bf16 terms into the A slabs: the
+// coupling term and a^{b1} are loaded once per term for all N rows.
+template <int N>
+__device__ __forceinline__ void p_run(const int4 R, const float2* __restrict__ X, int nlm, int k,
+                                      const float4* __restrict__ tcoef, const uint32_t* __restrict__ tidx,
+                                      const int4* __restrict__ segs, const int* __restrict__ lamseg,
+                                      unsigned char* Abuf, bool odd) {
+    const int b1 = R.w & 0xff, b2 = R.w >> 8;
+    const float2* A1 = X + (size_t)b1 * nlm * kKStep + k;
+    const float2* A2 = X + (size_t)b2 * nlm * kKStep + k;
+    const int lam = R.z, sg0 = lamseg[lam], sg1 = lamseg[lam + 1];
+    for (int sg = sg0; sg < sg1; ++sg) {
+        const int4 S = segs[sg];
+        float pr[N], pim[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) pr[j] = pim[j] = 0.f;
+        for (int q = S.x; q < S.y; ++q) {
+            const float4 c = tcoef[q];
+            const uint32_t id = tidx[q];
+            const float2 x1 = A1[(id & 0xffffu) * kKStep];
+            const float a0 = c.x * x1.x, a1 = c.y * x1.y, a2 = c.z * x1.y, a3 = c.w * x1.x;
+            const float2* B2 = A2 + (id >> 16) * kKStep;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const float2 x2 = B2[(size_t)j * nlm * kKStep];
+                pr[j] = fmaf(a0, x2.x, fmaf(a1, x2.y, pr[j]));
+                pim[j] = fmaf(a2, x2.x, fmaf(a3, x2.y, pim[j]));
+            }
+        }
+        const int m3 = sg - sg0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const uint32_t off = tc::kmajor16_offset(R.x + j, k);
+            if (m3 == 0) {
+                split_store(Abuf, off, odd ? pim[j] : pr[j], kATerm);
+            } else {
+                split_store(Abuf + (size_t)(2 * m3 - 1) * kASlab, off, pr[j], kATerm);
+                split_store(Abuf + (size_t)(2 * m3) * kASlab, off, pim[j], kATerm);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_contract4_tc(const Contract4TCArgs a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     const TCLayout lay = tc_layout(a);
@@ -181,40 +225,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract4_tc(const Contract4TCA
                     split_store(Bbuf + (size_t)j * kBSlab, tc::kmajor16_offset(n, kk), v, kBTerm);
                 }
             }
-            const int k = tid & 15;
-            for (int rr = tid >> 4; rr < 128; rr += kThreads / 16) {
-                const int grow = T.y + rr;
-                if (rr >= T.z) {
-                    for (int j = 0; j < ncomp; ++j)
-                        split_store(Abuf + (size_t)j * kASlab, tc::kmajor16_offset(rr, k), 0.f, kATerm);
-                    continue;
-                }
-                const int lam = a.group_lams[G.z + grow / a.ncombo];
-                const int2 bb = combos[grow % a.ncombo];
-                const float2* A1 = X + (size_t)bb.x * a.nlm * kKStep + k;
-                const float2* A2 = X + (size_t)bb.y * a.nlm * kKStep + k;
-                const int sg0 = lamseg[lam], sg1 = lamseg[lam + 1];
-                for (int sg = sg0; sg < sg1; ++sg) {
-                    const int4 S = segs[sg];
-                    float pr = 0.f, pim = 0.f;
-                    for (int q = S.x; q < S.y; ++q) {
-                        const float4 c = tcoef[q];
-                        const uint32_t id = tidx[q];
-                        const float2 x1 = A1[(id & 0xffffu) * kKStep];
-                        const float2 x2 = A2[(id >> 16) * kKStep];
-                        pr = fmaf(c.x * x1.x, x2.x, pr);
-                        pr = fmaf(c.y * x1.y, x2.y, pr);
-                        pim = fmaf(c.z * x1.y, x2.x, pim);
-                        pim = fmaf(c.w * x1.x, x2.y, pim);
-                    }
-                    const int m3 = sg - sg0;
-                    const uint32_t off = tc::kmajor16_offset(rr, k);
-                    if (m3 == 0) {
-                        split_store(Abuf, off, G.y ? pim : pr, kATerm);
-                    } else {
-                        split_store(Abuf + (size_t)(2 * m3 - 1) * kASlab, off, pr, kATerm);
-                        split_store(Abuf + (size_t)(2 * m3) * kASlab, off, pim, kATerm);
-                    }
+            // 16 lanes per group of threads, one primary (K column) each
+            const int k = tid & 15, g16 = tid >> 4;
+            for (int rr = T.z + g16; rr < 128; rr += kThreads / 16)   // rows past the tile's end
+                for (int j = 0; j < ncomp; ++j)
+                    split_store(Abuf + (size_t)j * kASlab, tc::kmajor16_offset(rr, k), 0.f, kATerm);
+            for (int r = a.tile_run0[t] + g16; r < a.tile_run0[t + 1]; r += kThreads / 16) {
+                const int4 R = a.runs[r];
+                switch (R.y) {
+                    case 1: p_run<1>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    case 2: p_run<2>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    case 3: p_run<3>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    case 4: p_run<4>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    case 5: p_run<5>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    case 6: p_run<6>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    case 7: p_run<7>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
+                    default: p_run<8>(R, X, a.nlm, k, tcoef, tidx, segs, lamseg, Abuf, G.y != 0); break;
                 }
             }
             tc::fence_proxy_async();

@@ -143,6 +143,8 @@ struct Contract4TCArgs {
     int ngroup;
     const int4* tiles;         // (group, first row in the group, rows, first B slab)
     int ntile;
+    const int4* runs;          // (first row in the tile, rows <= 8, multiplet, b1 | first b2 << 8)
+    const int* tile_run0;      // first run of each tile (ntile + 1)
     const int2* combos;        // (b1, b2), b1 < b2 <= nr - 2
     const int* combo_bin;      // bin-tuple index of (b1, b2, b2 + 1)
     int ncombo;
