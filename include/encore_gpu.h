@@ -171,7 +171,8 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
 
 /* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8; the cell
  * side of the neighbour grid is about r_max / key0), key 2 = contraction primaries
- * per chunk (0 = automatic), key 3 = pair-kernel neighbour-list capacity per block
+ * per chunk, rounded up to a multiple of 64, for every contraction kernel (0 = automatic:
+ * about n / (4 x SMs) for the 3PCF and 5PCF, n / SMs for the 4PCF), key 3 = pair-kernel neighbour-list capacity per block
  * (multiple of 256 in 1024..16384 entries; larger lists mean fewer slices for dense
  * primaries, smaller ones leave more shared memory for staging), key 4 = cap on the
  * neighbour points staged in shared memory per cell (0 = as many as fit; cells with

@@ -581,10 +581,9 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     CU(ctx->cursor.ensure(cells));
     CU(ctx->work.ensure(2));
 
-    // contraction chunks: ranges of about n / (waves x SMs) primaries (a multiple of the
-    // FP32 kernel's 64-primary tile), never crossing a catalog; the tensor-core kernel keeps
-    // its accumulators for a whole chunk, so it takes one wave
-    const int waves = ctx->prec == NPCF_SPLIT_BF16 ? 1 : 4;
+    // contraction chunks of the 3PCF and 5PCF kernels: ranges of about n / (4 x SMs)
+    // primaries (a multiple of 64), never crossing a catalog
+    const int waves = 4;
     long long C = ctx->chunk_target > 0 ? ctx->chunk_target : (n64 + (long long)waves * ctx->nsm - 1) /
                                                                    ((long long)waves * ctx->nsm);
     C = std::max(64LL, (C + 63) / 64 * 64);
@@ -596,10 +595,10 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         cbeg.push_back((int)chunks.size());
     }
     P.nchunk = (int)chunks.size();
-    // the FP32 4PCF kernel takes chunks dynamically and writes one FP64 row per chunk: a
-    // coarser table (about one chunk per SM and catalog, whole 64-primary tiles) keeps the
-    // rows few and the tiles full
-    const long long C4 = std::max(64LL, ((n64 + ctx->nsm - 1) / ctx->nsm + 63) / 64 * 64);
+    // the 4PCF kernels take a coarser table (about one chunk per SM and catalog, whole
+    // 64-primary tiles): the FP32 kernel takes chunks dynamically and writes one FP64 row
+    // per chunk, the tensor-core kernel keeps its accumulators for a whole chunk
+    const long long C4 = ctx->chunk_target > 0 ? C : std::max(64LL, ((n64 + ctx->nsm - 1) / ctx->nsm + 63) / 64 * 64);
     std::vector<int2> chunks4;
     std::vector<int> cbeg4(1, 0);
     for (int k = 0; k < ncat; ++k) {
@@ -778,7 +777,7 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.n = n;
             c.nr = ctx->nr;
             c.nlm = ctx->nlm;
-            c.chunks = ctx->chunks.p;
+            c.chunks = ctx->chunks4.p;
             c.terms = ctx->c4terms.p;
             c.nterms = ctx->c4nterms;
             c.segs = ctx->c4segs.p;
@@ -804,7 +803,7 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.partial = ctx->partial.p;
             c.total = ctx->total;
             c.err = ctx->errflag.p;
-            launch_contract4_tc(c, P.nchunk, s);
+            launch_contract4_tc(c, P.nchunk4, s);
         } else if (o.N == 4) {
             if (ctx->c4nitem == 0) continue;
             Contract4WArgs c{};
@@ -870,7 +869,7 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
     if (timed) CU(cudaEventRecord(ctx->ev[3], s));
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
-        const bool coarse = o.N == 4 && ctx->prec == NPCF_FP32;
+        const bool coarse = o.N == 4;   // both 4PCF kernels use the coarse chunk table
         launch_reduce(ctx->partial.p, coarse ? ctx->cbeg4.p : ctx->cbeg.p, ncat, ctx->total, ctx->order_off[k],
                       o.n_lambda() * o.n_bins(), ctx->zscale.p, ctx->zeta.p, s);
     }
