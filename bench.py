@@ -39,8 +39,12 @@ KERNELS_PER_STEP = 10  # k_sumw, 4 cell-list kernels, pair, contract3, contract4
 # 200k workload, with the SHA-256 prefix of the kernel's source when they were taken; the
 # roofline reports them only while the source is unchanged (profiles/ has the captures).
 TRAFFIC = {
-    "pair": {"bytes": 8_026_112 + 284_108_800, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
+    "pair": {"bytes": 5_853_696 + 283_596_288, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
              "sha256": "752f4b3b89cee01b"},
+    "contraction/fp32": {"bytes": 337_105_152 + 159_488, "source": "paper_2105_08722_gb300/csrc/npcf_contract4.cu",
+                         "sha256": "ec635d2be4d339ba"},
+    "contraction/bf16": {"bytes": 338_193_920 + 3_255_552,
+                         "source": "paper_2105_08722_gb300/csrc/npcf_contract_tc.cu", "sha256": "9e25cf7cd3089fa9"},
 }
 
 
@@ -307,7 +311,8 @@ def run_gpu(args):
         "pairs_per_step": npairs_per_step,
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": _traffic(dominant) if wl.n == 200_000 else None,
+                     "traffic": (_traffic(dominant if dominant == "pair" else "contraction/" + args.precision)
+                                 if wl.n == 200_000 else None),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
         "clocks": clk,
         "other_precision": other,
