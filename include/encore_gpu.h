@@ -135,6 +135,13 @@ npcf_status npcf_finalize(npcf_ctx* ctx, double* out, size_t out_len, int normal
 npcf_status npcf_accumulate_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w,
                                   const int64_t* offsets, int ncat, void* stream);
 
+/* Same as npcf_accumulate_batch with separate primary weights (as npcf_accumulate_ex):
+ * d_wprim device float32 [n], nullable (then d_w); primaries with weight 0 are skipped, so
+ * a seeded sample of primaries of every catalog can be evaluated against full catalogs. */
+npcf_status npcf_accumulate_batch_ex(npcf_ctx* ctx, const float* d_pos, const float* d_w,
+                                     const float* d_wprim, const int64_t* offsets, int ncat,
+                                     void* stream);
+
 /* Multiplets of every catalog, host out[ncat][npcf_output_size] (synchronises);
  * normalize as in npcf_finalize, catalog k with its own sum of weights. */
 npcf_status npcf_finalize_batch(npcf_ctx* ctx, double* out, size_t out_len, int normalize);

@@ -37,6 +37,7 @@ SIGNATURES = {
     "npcf_pair_counts_noalloc": (_i, [_vp, _i64, _i, _vp, _d, _vp, _vp]),
     "npcf_edge_correct": (_i, [_vp, _vp, _vp]),
     "npcf_accumulate_batch": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "npcf_accumulate_batch_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "npcf_finalize_batch": (_i, [_vp, _vp, _sz, _i]),
     "npcf_pair_counts_batch": (_i, [_vp, _vp, _sz]),
     "npcf_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64)]),
@@ -170,12 +171,18 @@ class NPCF:
         self._check(self._lib.npcf_finalize(self._h, out.ctypes.data, self.size, int(normalize)))
         return out
 
-    def accumulate_batch(self, pos, w, offsets, stream=None):
-        """Co-add a batch of catalogs (npcf_accumulate_batch): pos [n, 3] and w [n] CUDA
-        tensors, catalog k = rows offsets[k] .. offsets[k+1]-1."""
+    def accumulate_batch(self, pos, w, offsets, wprim=None, stream=None):
+        """Co-add a batch of catalogs (npcf_accumulate_batch[_ex]): pos [n, 3] and w [n]
+        CUDA tensors, catalog k = rows offsets[k] .. offsets[k+1]-1; wprim (optional, [n])
+        separate primary weights."""
         off = np.ascontiguousarray(offsets, dtype=np.int64)
-        self._check(self._lib.npcf_accumulate_batch(self._h, _ptr(pos), _ptr(w), off.ctypes.data, len(off) - 1,
-                                                    _stream_handle(stream)))
+        if wprim is None:
+            st = self._lib.npcf_accumulate_batch(self._h, _ptr(pos), _ptr(w), off.ctypes.data, len(off) - 1,
+                                                 _stream_handle(stream))
+        else:
+            st = self._lib.npcf_accumulate_batch_ex(self._h, _ptr(pos), _ptr(w), _ptr(wprim), off.ctypes.data,
+                                                    len(off) - 1, _stream_handle(stream))
+        self._check(st)
 
     def autotune(self, pos, w, stream=None) -> Dict[str, int]:
         """Pick the fastest pair-kernel and contraction settings for this catalog

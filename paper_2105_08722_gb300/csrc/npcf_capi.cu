@@ -892,8 +892,8 @@ npcf_status run_accumulate(npcf_ctx* ctx, const float* d_pos, const float* d_w, 
 // captured into a CUDA graph on the first call with a given shape; later calls with the
 // same pointers, offsets, tuning and context buffers replay the graph (one launch). The
 // legacy default stream cannot be captured: there the work is enqueued directly.
-npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const std::vector<long long>& off,
-                      cudaStream_t s) {
+npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim,
+                      const std::vector<long long>& off, cudaStream_t s) {
     if (!(ctx->box > 0))
         return fail(ctx, NPCF_EUNSUPPORTED, "batches take periodic boxes (one grid shape for every catalog)");
     for (size_t k = 0; k + 1 < off.size(); ++k)
@@ -903,10 +903,11 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
     npcf_status st = prepare(ctx, d_pos, d_w, off, s, P);
     if (st != NPCF_OK) return st;
     if (P.n == 0) return NPCF_OK;
-    if (s == 0 || s == cudaStreamLegacy || s == cudaStreamPerThread) return enqueue(ctx, d_pos, d_w, nullptr, P, s, false);
+    if (s == 0 || s == cudaStreamLegacy || s == cudaStreamPerThread)
+        return enqueue(ctx, d_pos, d_w, d_wprim, P, s, false);
     // everything the captured work depends on
     std::vector<uintptr_t> sig = {
-        (uintptr_t)d_pos, (uintptr_t)d_w, (uintptr_t)ctx->pts.p, (uintptr_t)ctx->wp.p, (uintptr_t)ctx->idx.p,
+        (uintptr_t)d_pos, (uintptr_t)d_w, (uintptr_t)d_wprim, (uintptr_t)ctx->pts.p, (uintptr_t)ctx->wp.p, (uintptr_t)ctx->idx.p,
         (uintptr_t)ctx->cell_of.p, (uintptr_t)ctx->cid.p, (uintptr_t)ctx->alm.p, (uintptr_t)ctx->cnt.p,
         (uintptr_t)ctx->count.p, (uintptr_t)ctx->start.p, (uintptr_t)ctx->cursor.p, (uintptr_t)ctx->work.p,
         (uintptr_t)ctx->partial.p, (uintptr_t)ctx->zeta.p, (uintptr_t)ctx->counts.p, (uintptr_t)ctx->sumw.p,
@@ -926,7 +927,7 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
         ctx->gsig.clear();
     }
     CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    st = enqueue(ctx, d_pos, d_w, nullptr, P, s, false);
+    st = enqueue(ctx, d_pos, d_w, d_wprim, P, s, false);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (st != NPCF_OK) {
@@ -1126,7 +1127,15 @@ npcf_status npcf_accumulate_batch(npcf_ctx* ctx, const float* d_pos, const float
     if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
     if (ncat < 1 || ncat > 65535 || !offsets) return fail(ctx, NPCF_EINVAL, "ncat must be in [1, 65535]");
     std::vector<long long> off(offsets, offsets + ncat + 1);
-    return run_batch(ctx, d_pos, d_w, off, (cudaStream_t)stream);
+    return run_batch(ctx, d_pos, d_w, nullptr, off, (cudaStream_t)stream);
+}
+
+npcf_status npcf_accumulate_batch_ex(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim,
+                                     const int64_t* offsets, int ncat, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (ncat < 1 || ncat > 65535 || !offsets) return fail(ctx, NPCF_EINVAL, "ncat must be in [1, 65535]");
+    std::vector<long long> off(offsets, offsets + ncat + 1);
+    return run_batch(ctx, d_pos, d_w, d_wprim, off, (cudaStream_t)stream);
 }
 
 npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream,

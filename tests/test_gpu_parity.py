@@ -593,3 +593,35 @@ def test_autotune_picks_candidates_and_leaves_sums_empty(torch_dev):
     got = est.finalize()
     _, want, _ = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 500.0)
     assert np.max(np.abs(got - want)) <= TOL_FP32 * np.sqrt(np.mean(want ** 2))
+
+
+def test_batched_mocks_full_size_sampled_primaries(torch_dev):
+    # the 64-catalog workload (6.46M points, split-bf16 as in the bench) in one batch; two
+    # seeded primaries in each of 8 catalogs are summed against their full catalogs and
+    # compared with the oracle; every other catalog has no primary and stays zero
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    cats, edges = catalogs.c5_batch()
+    sizes = np.array([len(c) for c in cats])
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(5005)
+    picked = np.sort(rng.choice(len(cats), 8, replace=False))
+    wp = np.zeros(off[-1], np.float32)
+    samples = {}
+    for k in picked:
+        samples[k] = np.sort(rng.choice(sizes[k], 2, replace=False))
+        wp[off[k] + samples[k]] = 1.0
+    pos = torch.from_numpy(np.ascontiguousarray(np.concatenate(cats), np.float32)).to(dev)
+    w = torch.ones(off[-1], device=dev)
+    est = NPCF(5, (3, 4), edges, 1000.0, 1)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        est.accumulate_batch(pos, w, off, wprim=torch.from_numpy(wp).to(dev), stream=stream)
+    stream.synchronize()
+    got = est.finalize_batch()
+    for k in range(len(cats)):
+        if k not in samples:
+            assert np.all(got[k] == 0), k
+            continue
+        want, _ = oracle.npcf(cats[k], np.ones(sizes[k], np.float32), (3, 4), 5, edges, 1000.0, prim=samples[k])
+        assert_orders_close(got[k], want, (3, 4), 5, 10, tol=TOL_BF16)
