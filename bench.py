@@ -142,6 +142,24 @@ def cpu_oracle_rate(wl, sample_n: int, seed: int = 77):
     return sample_n / dt, cores, "%d seeded primaries of the 200k catalog against all 200k secondaries" % sample_n
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest rank sets the
+    time of a step); identity on one rank."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def aggregate_rate(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processes its own replica of units_per_rank
+    (weak scaling), and the step takes the slowest rank's time ms."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def c2_workload(n_points):
     """The 200k log-normal workload, or the same density and spectrum at n_points (box
     scaled by (n/200k)^(1/3); a smaller case for profiling)."""
@@ -248,12 +266,7 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
 
-    ms = float(np.mean(step_ms))
-    e2e_ms = e2e_s * 1e3
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([float(np.mean(step_ms)), e2e_s * 1e3], world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -292,7 +305,7 @@ def run_gpu(args):
         oest.close()
     line = {
         "metric": METRIC,
-        "value": wl.n * world / (ms * 1e-3),
+        "value": aggregate_rate(wl.n, world, ms),
         "unit": "primaries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -302,7 +315,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "n_points": wl.n, "lmax": wl.lmax, "nr": 10, "orders": [3, 4],
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
-        "e2e": {"value": wl.n * world / (e2e_ms * 1e-3), "unit": "primaries/s",
+        "e2e": {"value": aggregate_rate(wl.n, world, e2e_ms), "unit": "primaries/s",
                 "h2d_bytes_per_step": int(wl.pos.nbytes + wl.w.nbytes),
                 "d2h_bytes_per_step": int(8 * e2e_est.size)},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
