@@ -97,12 +97,11 @@ struct npcf_ctx {
     // 5PCF contraction tables
     DevBuf<float4> c5c12, c5c34;
     DevBuf<uint32_t> c5i12, c5i34;
-    DevBuf<int2> c5segs12, c5segs34, c5pairs;
-    DevBuf<int> c5t12seg0, c5t34seg0, c5t34l12, c5blkt34;
-    DevBuf<int4> c5rowsA, c5rowsB, c5blocks;
-    DevBuf<float2> c5rowsC;
-    int c5nrows = 0, c5nblocks = 0, c5npairs = 0, c5l12max = 0;
-    int c5nt12 = 0, c5nt34 = 0, c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
+    DevBuf<int> c5binq;
+    DevBuf<int4> c5items;
+    int c5nitem = 0;
+    DevBuf<int2> c5segs12, c5segs34;
+    int c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
 
     // working buffers
     DevBuf<float4> pts;
@@ -255,112 +254,89 @@ npcf_status setup_tc_tables(npcf_ctx* ctx, const OrderTable& o, const ContractTa
     return NPCF_OK;
 }
 
-// Tables of the 5PCF contraction: rows (multiplet, b1, b2), b2 <= nr - 3, sorted by the
-// (l12 l3 l4) triple, cut into blocks of <= 256 rows using <= kMaxT34 distinct triples.
+// Tables of the 5PCF contraction: the P12 and P34 coupling terms with their offsets in the
+// staged tile, and items (multiplet, beta = b2 <= nr - 3) grouped by beta.
 npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
     const int nr = ctx->nr;
     if (nr > 10)
         return fail(ctx, NPCF_EUNSUPPORTED, "the 5PCF contraction supports at most 10 shells");
     ContractTable5 t = make_contract5(o);
-    std::vector<int2> pairs;
-    for (int b3 = 0; b3 < nr; ++b3)
-        for (int b4 = b3 + 1; b4 < nr; ++b4) pairs.push_back(make_int2(b3, b4));
-    auto pair_index = [&](int b3, int b4) {
-        for (size_t i = 0; i < pairs.size(); ++i)
-            if (pairs[i].x == b3 && pairs[i].y == b4) return (int)i;
-        return -1;
-    };
+    const int nb = o.n_bins();
     auto bin_index = [&](int b1, int b2, int b3, int b4) {
-        for (int b = 0; b < o.n_bins(); ++b) {
+        for (int b = 0; b < nb; ++b) {
             const int* B = &o.bins[4 * b];
             if (B[0] == b1 && B[1] == b2 && B[2] == b3 && B[3] == b4) return b;
         }
         return -1;
     };
-    struct Row { int t34, t12, lam, b1, b2; };
-    std::vector<Row> rows;
-    for (int a = 0; a < o.n_lambda(); ++a)
-        for (int b1 = 0; b1 < nr; ++b1)
-            for (int b2 = b1 + 1; b2 <= nr - 3; ++b2)
-                rows.push_back({t.lam_t34[a], t.lam_t12[a], a, b1, b2});
-    std::stable_sort(rows.begin(), rows.end(), [](const Row& x, const Row& y) {
-        if (x.t34 != y.t34) return x.t34 < y.t34;
-        return x.t12 < y.t12;
-    });
-    std::vector<int4> rowsA, rowsB, blocks;
-    std::vector<float2> rowsC;
-    std::vector<int> blk_t34;
-    size_t r = 0;
-    while (r < rows.size()) {
-        const int first = (int)r;
-        std::vector<int> trip;
-        std::vector<std::pair<Row, int>> blk;   // rows of this block with their local triple
-        while (r < rows.size() && (int)(r - first) < 256) {
-            int loc = -1;
-            for (size_t q = 0; q < trip.size(); ++q)
-                if (trip[q] == rows[r].t34) loc = (int)q;
-            if (loc < 0) {
-                if ((int)trip.size() == kMaxT34) break;
-                trip.push_back(rows[r].t34);
-                loc = (int)trip.size() - 1;
-            }
-            blk.push_back({rows[r], loc});
-            ++r;
+    // coupling terms with the offsets of their factors in the staged [lm][b][primary] tile
+    std::vector<float4> c12, c34;
+    std::vector<uint32_t> o12, o34;
+    auto pack = [&](const std::vector<PairTerm>& in, std::vector<float4>& c, std::vector<uint32_t>& o) {
+        for (const PairTerm& q : in) {
+            c.push_back(make_float4(q.cA, q.cB, q.cC, q.cD));
+            o.push_back((uint32_t)(q.lm1 * nr * kRS5) | ((uint32_t)(q.lm2 * nr * kRS5) << 16));
         }
-        // by b2 within the block: a warp's rows then share the number of pairs after b2
-        std::stable_sort(blk.begin(), blk.end(), [](const std::pair<Row, int>& x, const std::pair<Row, int>& y) {
-            return x.first.b2 < y.first.b2;
-        });
-        for (const auto& br : blk) {
-            const Row& R = br.first;
-            const int loc = br.second;
-            const int* L = &o.lam[(size_t)R.lam * 5];
-            const int np = (nr - 1 - R.b2) * (nr - 2 - R.b2) / 2;
-            rowsA.push_back(make_int4(R.lam, R.b1, R.b2, off + R.lam * o.n_bins() + bin_index(R.b1, R.b2, R.b2 + 1, R.b2 + 2)));
-            rowsB.push_back(make_int4(R.t12, loc, pair_index(R.b2 + 1, R.b2 + 2), np));
-            rowsC.push_back(make_float2((float)std::sqrt(2.0 * L[2] + 1.0), o.odd(R.lam) ? 1.f : 0.f));
-        }
-        blocks.push_back(make_int4(first, (int)r - first, (int)trip.size(), 0));
-        for (int q = 0; q < kMaxT34; ++q) blk_t34.push_back(q < (int)trip.size() ? trip[q] : 0);
-    }
+    };
+    pack(t.terms12, c12, o12);
+    pack(t.terms34, c34, o34);
     std::vector<int2> s12, s34;
     for (size_t i = 0; i < t.seg12_begin.size(); ++i) s12.push_back(make_int2(t.seg12_begin[i], t.seg12_end[i]));
     for (size_t i = 0; i < t.seg34_begin.size(); ++i) s34.push_back(make_int2(t.seg34_begin[i], t.seg34_end[i]));
-    ctx->c5nrows = (int)rowsA.size();
-    ctx->c5nblocks = (int)blocks.size();
-    ctx->c5npairs = (int)pairs.size();
-    ctx->c5l12max = t.l12max;
-    ctx->c5nt12 = (int)t.t12_seg0.size() - 1;
-    ctx->c5nt34 = (int)t.t34_seg0.size() - 1;
-    ctx->c5nterms12 = (int)t.terms12.size();
-    ctx->c5nterms34 = (int)t.terms34.size();
+    // bin of (b1, b2, b2 + 1, b2 + 2): the first of the (b3, b4) pairs after b2
+    std::vector<int> binq((size_t)nr * nr, 0);
+    for (int b2 = 1; b2 + 2 < nr; ++b2)
+        for (int b1 = 0; b1 < b2; ++b1) binq[(size_t)b1 * nr + b2] = bin_index(b1, b2, b2 + 1, b2 + 2);
+    // items (multiplet, beta = b2), grouped by beta (the kernel's specialisation), heaviest first
+    std::vector<std::pair<double, int4>> items;
+    for (int a = 0; a < o.n_lambda(); ++a) {
+        const int* L = &o.lam[(size_t)a * 5];
+        const int t12 = t.lam_t12[a], t34 = t.lam_t34[a], l12 = L[2];
+        for (int beta = 1; beta + 2 < nr; ++beta) {
+            const int m = nr - 1 - beta;
+            double cost = 0;
+            for (int m12 = 0; m12 <= l12; ++m12) {
+                const int k12 = t.seg12_end[t.t12_seg0[t12] + m12] - t.seg12_begin[t.t12_seg0[t12] + m12];
+                const int k34 = t.seg34_end[t.t34_seg0[t34] + m12] - t.seg34_begin[t.t34_seg0[t34] + m12];
+                cost += k12 * beta + k34 * m * (m - 1) / 2.0 + beta * m * (m - 1) / 2.0;
+            }
+            items.push_back({1e12 * beta + cost,
+                             make_int4(t.t12_seg0[t12], t.t34_seg0[t34], l12 | (beta << 8) | ((o.odd(a) ? 1 : 0) << 16),
+                                       off + a * nb)});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) { return x.first > y.first; });
+    std::vector<int4> it;
+    for (const auto& x : items) it.push_back(x.second);
+    {
+        Contract5WArgs c{};
+        c.nr = nr;
+        c.nlm = ctx->nlm;
+        c.nterms12 = (int)c12.size();
+        c.nterms34 = (int)c34.size();
+        c.nseg12 = (int)s12.size();
+        c.nseg34 = (int)s34.size();
+        int dev = 0, optin = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (!it.empty() && contract5w_smem_bytes(c) + 1024 > (size_t)optin)
+            return fail(ctx, NPCF_EUNSUPPORTED, "5PCF: coupling tables and staged harmonics need %zu B of shared "
+                        "memory (limit %d)", contract5w_smem_bytes(c), optin);
+    }
+    ctx->c5nitem = (int)it.size();
+    ctx->c5nterms12 = (int)c12.size();
+    ctx->c5nterms34 = (int)c34.size();
     ctx->c5nseg12 = (int)s12.size();
     ctx->c5nseg34 = (int)s34.size();
-    std::vector<float4> c12, c34;
-    std::vector<uint32_t> i12, i34;
-    for (const PairTerm& q : t.terms12) {
-        c12.push_back(make_float4(q.cA, q.cB, q.cC, q.cD));
-        i12.push_back((uint32_t)q.lm1 | ((uint32_t)q.lm2 << 16));
-    }
-    for (const PairTerm& q : t.terms34) {
-        c34.push_back(make_float4(q.cA, q.cB, q.cC, q.cD));
-        i34.push_back((uint32_t)q.lm1 | ((uint32_t)q.lm2 << 16));
-    }
     CU(upload(ctx->c5c12, c12));
-    CU(upload(ctx->c5i12, i12));
+    CU(upload(ctx->c5i12, o12));
     CU(upload(ctx->c5c34, c34));
-    CU(upload(ctx->c5i34, i34));
+    CU(upload(ctx->c5i34, o34));
     CU(upload(ctx->c5segs12, s12));
     CU(upload(ctx->c5segs34, s34));
-    CU(upload(ctx->c5pairs, pairs));
-    CU(upload(ctx->c5t12seg0, t.t12_seg0));
-    CU(upload(ctx->c5t34seg0, t.t34_seg0));
-    CU(upload(ctx->c5t34l12, t.t34_l12));
-    CU(upload(ctx->c5blkt34, blk_t34));
-    CU(upload(ctx->c5rowsA, rowsA));
-    CU(upload(ctx->c5rowsB, rowsB));
-    CU(upload(ctx->c5rowsC, rowsC));
-    CU(upload(ctx->c5blocks, blocks));
+    CU(upload(ctx->c5binq, binq));
+    CU(upload(ctx->c5items, it));
     return NPCF_OK;
 }
 
@@ -579,7 +555,7 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     CU(ctx->count.ensure(cells));
     CU(ctx->start.ensure(cells + 1));
     CU(ctx->cursor.ensure(cells));
-    CU(ctx->work.ensure(2));
+    CU(ctx->work.ensure(3));
 
     // contraction chunks of the 3PCF and 5PCF kernels: ranges of about n / (4 x SMs)
     // primaries (a multiple of 64), never crossing a catalog
@@ -719,7 +695,7 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
     const size_t cells = (size_t)g.ncell * ncat;
     if (timed) CU(cudaEventRecord(ctx->ev[0], s));
     CU(cudaMemsetAsync(ctx->count.p, 0, cells * sizeof(uint32_t), s));
-    CU(cudaMemsetAsync(ctx->work.p, 0, 2 * sizeof(int), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 3 * sizeof(int), s));
     launch_sumw(d_w, ctx->d_off.p, ncat, ctx->sumw.p, s);
 
     BinArgs b{};
@@ -827,42 +803,34 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.chunk_counter = ctx->work.p + 1;
             launch_contract4w(c, contract4w_blocks(ctx->nsm, P.nchunk4), s);
         } else if (o.N == 5) {
-            if (ctx->c5nrows == 0) continue;
-            Contract5Args c{};
+            if (ctx->c5nitem == 0) continue;
+            Contract5WArgs c{};
             c.alm = ctx->alm.p;
             c.wp = ctx->wp.p;
             c.n = n;
             c.nr = ctx->nr;
             c.nlm = ctx->nlm;
-            c.chunks = ctx->chunks.p;
-            c.nchunk = P.nchunk;
             c.c12 = ctx->c5c12.p;
-            c.i12 = ctx->c5i12.p;
-            c.segs12 = ctx->c5segs12.p;
-            c.t12_seg0 = ctx->c5t12seg0.p;
+            c.o12 = ctx->c5i12.p;
             c.c34 = ctx->c5c34.p;
-            c.i34 = ctx->c5i34.p;
+            c.o34 = ctx->c5i34.p;
+            c.segs12 = ctx->c5segs12.p;
             c.segs34 = ctx->c5segs34.p;
-            c.t34_seg0 = ctx->c5t34seg0.p;
-            c.t34_l12 = ctx->c5t34l12.p;
             c.nterms12 = ctx->c5nterms12;
             c.nterms34 = ctx->c5nterms34;
             c.nseg12 = ctx->c5nseg12;
             c.nseg34 = ctx->c5nseg34;
-            c.nt12 = ctx->c5nt12;
-            c.nt34 = ctx->c5nt34;
-            c.rowsA = ctx->c5rowsA.p;
-            c.rowsB = ctx->c5rowsB.p;
-            c.rowsC = ctx->c5rowsC.p;
-            c.blocks = ctx->c5blocks.p;
-            c.blk_t34 = ctx->c5blkt34.p;
-            c.nblocks = ctx->c5nblocks;
-            c.pairs = ctx->c5pairs.p;
-            c.npairs = ctx->c5npairs;
-            c.l12max = ctx->c5l12max;
+            c.binq = ctx->c5binq.p;
+            c.items = ctx->c5items.p;
+            c.nitem = ctx->c5nitem;
+            c.chunks = ctx->chunks.p;
+            c.nchunk = P.nchunk;
             c.partial = ctx->partial.p;
             c.total = ctx->total;
-            launch_contract5(c, s);
+            c.out_off = ctx->order_off[k];
+            c.nout = o.n_lambda() * o.n_bins();
+            c.chunk_counter = ctx->work.p + 2;
+            launch_contract5w(c, std::max(1, std::min(2 * ctx->nsm, P.nchunk)), s);
         }
         CU(cudaGetLastError());
     }

@@ -160,45 +160,37 @@ struct Contract4TCArgs {
 
 void launch_contract4_tc(const Contract4TCArgs& a, int nchunk, cudaStream_t s);
 
-// 5PCF contraction (FP32 CUDA cores). For multiplet L = (l1, l2, l12, l3, l4):
+
+// 5PCF contraction (FP32 CUDA cores, npcf_contract5w.cu). For L = (l1, l2, l12, l3, l4):
 //   P12^{m12}(b1,b2) = sum_{m1} (l1 l2 l12; m1, m12-m1, -m12) a^{b1}_{l1 m1} a^{b2}_{l2, m12-m1}
 //   P34^{m12}(b3,b4) = sum_{m3} (l12 l3 l4; m12, m3, -m12-m3) a^{b3}_{l3 m3} a^{b4}_{l4, -m12-m3}
 //   zeta_L(b1..b4) += u sqrt(2 l12 + 1) sum_{m12>=0} 2 S(m12) (-1)^{l12-m12} Q_L[P12 P34].
-// Rows (L, b1, b2) with b2 <= nr - 3 are sorted by the (l12, l3, l4) triple; each block of
-// rows lists the distinct triples it needs (at most kMaxT34), whose P34 the block tabulates
-// per primary in shared memory.
-constexpr int kMaxT34 = 16;
-constexpr int kMaxPairs5 = 28;   // (b3, b4) pairs after b2 held per thread (nr <= 10)
-struct Contract5Args {
-    const float2* alm;
+// Tiles of kT5 primaries staged as [lm][b][primary] with row stride kRS5; warps take
+// items (L, beta = b2), one primary per lane.
+constexpr int kT5 = 32;
+constexpr int kRS5 = kT5 + 1;
+struct Contract5WArgs {
+    const float2* alm;         // [n][nr][nlm]
     const float* wp;
     int n, nr, nlm;
-    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
-    int nchunk;
-    const float4* c12;         // coupling terms (cA, cB, cC, cD) of P12
-    const uint32_t* i12;       // their lm1 | lm2 << 16
-    const int2* segs12;        // term ranges per (l1 l2 l12 triple, m12)
-    const int* t12_seg0;       // first segment of each triple
+    const float4* c12;         // P12 terms (cA, cB, cC, cD)
+    const uint32_t* o12;       // staged offsets lm1 nr kRS5 | lm2 nr kRS5 << 16
     const float4* c34;
-    const uint32_t* i34;
+    const uint32_t* o34;
+    const int2* segs12;        // term range of each (l1 l2 l12 triple, m12)
     const int2* segs34;
-    const int* t34_seg0;
-    const int* t34_l12;
-    int nterms12, nterms34, nseg12, nseg34, nt12, nt34;
-    const int4* rowsA;         // (multiplet, b1, b2, first output entry)
-    const int4* rowsB;         // (l1 l2 l12 triple, local l3 l4 triple, first pair index, pairs)
-    const float2* rowsC;       // (sqrt(2 l12 + 1), parity-odd ? 1 : 0)
-    const int4* blocks;        // (first row, rows, number of triples, 0)
-    const int* blk_t34;        // [nblocks][kMaxT34] triples of each block
-    int nblocks;
-    const int2* pairs;         // (b3, b4) of every pair b3 < b4 (lexicographic)
-    int npairs;
-    int l12max;
-    double* partial;
-    int total;
+    int nterms12, nterms34, nseg12, nseg34;
+    const int* binq;           // [nr][nr]: bin index of (b1, b2, b2 + 1, b2 + 2)
+    const int4* items;         // (P12 segment of m12 = 0, P34 segment of m12 = 0, l12 | beta << 8 | odd << 16, first output of L)
+    int nitem;
+    const int2* chunks;        // primary ranges, none crossing a catalog
+    int nchunk;
+    double* partial;           // [nchunk][total]
+    int total, out_off, nout;
+    int* chunk_counter;        // zeroed before the launch
 };
-void launch_contract5(const Contract5Args& a, cudaStream_t s);
-size_t contract5_smem_bytes(const Contract5Args& a);
+void launch_contract5w(const Contract5WArgs& a, int nblocks, cudaStream_t s);
+size_t contract5w_smem_bytes(const Contract5WArgs& a);
 size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
