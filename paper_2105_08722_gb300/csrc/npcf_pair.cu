@@ -201,7 +201,7 @@ struct PairLayout {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Floats of one group's partial area: nr + kW - 1 slots for the slice's per-warp sums
-// (warp w's share of shell t goes to slot t + w: the warps' equal chunks of the
+// (warp w's share of shell t goes to slot t + w: the warps' equal runs of packets of the
 // shell-sorted slice are ordered, so these never collide) and nr per-shell sums.
 __host__ __device__ constexpr int part_floats(int nr, int nc) { return (2 * nr + kW - 1) * nc; }
 
@@ -229,6 +229,7 @@ struct GroupShared {
     uint32_t hist[kW][kMaxNr];     // per-warp shell counts of the current slice
     uint32_t base[kW][kMaxNr];     // where each warp scatters each shell
     uint32_t off[kMaxNr + 1];      // shell offsets of the sorted slice
+    uint32_t pk[kMaxNr + 1];       // first 32-entry packet of each shell (packets never straddle shells)
     uint32_t tot[kMaxNr];          // shell totals of the current primary
     int done[kW];
     int wtot[kW];                  // per-warp sums of the row-trimming prefix
@@ -497,13 +498,24 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                 const uint32_t y = __shfl_up_sync(kFull, incl, o);
                 if (lane >= o) incl += y;
             }
+            // packets of 32 entries per shell, and their prefix
+            const uint32_t npk = (tsum + 31u) / 32u;
+            uint32_t pincl = npk;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, pincl, o);
+                if (lane >= o) pincl += y;
+            }
             if (lane < nr) {
                 uint32_t bw = incl - tsum;
                 G.off[lane] = bw;
+                G.pk[lane] = pincl - npk;
                 for (int w = 0; w < kW; ++w) { G.base[w][lane] = bw; bw += G.hist[w][lane]; }
                 G.tot[lane] += tsum;
             }
-            if (lane == nr - 1) G.off[nr] = incl;
+            if (lane == nr - 1) {
+                G.off[nr] = incl;
+                G.pk[nr] = pincl;
+            }
         }
         group_sync(grp);
 
@@ -525,18 +537,22 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         }
         group_sync(grp);
 
-        // ---- accumulate an equal chunk of the sorted slice, per shell
+        // ---- accumulate an equal run of 32-entry packets of the sorted slice, per shell
+        // (a packet holds one shell's entries, so only a shell's last packet has idle lanes)
         {
-            const int ns = (int)G.off[nr];
-            const int chunk = (ns + kW - 1) / kW;
-            const int c0 = min(ns, warp * chunk), c1 = min(ns, c0 + chunk);
+            const int npk = (int)G.pk[nr];
+            const int per = (npk + kW - 1) / kW;
+            const int q0 = min(npk, warp * per), q1 = min(npk, q0 + per);
             for (int t = 0; t < nr; ++t) {
-                const int lo = max(c0, (int)G.off[t]), hi = min(c1, (int)G.off[t + 1]);
-                if (lo >= hi) continue;
+                const int pa = max(q0, (int)G.pk[t]), pb = min(q1, (int)G.pk[t + 1]);
+                if (pa >= pb) continue;
+                const int base = (int)G.off[t] - 32 * (int)G.pk[t], hi = (int)G.off[t + 1];
                 float acc[NC];
 #pragma unroll
                 for (int i = 0; i < NC; ++i) acc[i] = 0.f;
-                for (int k = lo + lane; k < hi; k += 32) {
+                for (int q = pa; q < pb; ++q) {
+                    const int k = base + 32 * q + lane;
+                    if (k >= hi) continue;
                     float dx, dy, dz, wj;
                     // accepted pairs are closer than r_max < L/3: the minimum image is the
                     // image the neighbour rule accepted
@@ -564,15 +580,15 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         // fold the slice's slots into the primary's sums, warps in order (deterministic);
         // the next slice writes slots only after its next group barrier
         {
-            const int ns = (int)G.off[nr];
-            const int chunk = (ns + kW - 1) / kW;
+            const int npk = (int)G.pk[nr];
+            const int per = (npk + kW - 1) / kW;
             for (int i = gt; i < nr * NC; i += kW * 32) {
                 const int t = i / NC, c = i - t * NC;
-                const int o0 = (int)G.off[t], o1 = (int)G.off[t + 1];
+                const int o0 = (int)G.pk[t], o1 = (int)G.pk[t + 1];
                 float v = 0.f;
                 for (int w = 0; w < kW; ++w) {
-                    const int c0 = min(ns, w * chunk), c1 = min(ns, c0 + chunk);
-                    if (max(c0, o0) < min(c1, o1)) v += slot[(t + w) * NC + c];
+                    const int q0 = min(npk, w * per), q1 = min(npk, q0 + per);
+                    if (max(q0, o0) < min(q1, o1)) v += slot[(t + w) * NC + c];
                 }
                 psum[i] += v;
             }
