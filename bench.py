@@ -39,8 +39,8 @@ KERNELS_PER_STEP = 10  # k_sumw, 4 cell-list kernels, pair, contract3, contract4
 # 200k workload, with the SHA-256 prefix of the kernel's source when they were taken; the
 # roofline reports them only while the source is unchanged (profiles/ has the captures).
 TRAFFIC = {
-    "pair": {"bytes": 5_853_696 + 283_596_288, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
-             "sha256": "752f4b3b89cee01b"},
+    "pair": {"bytes": 6_404_864 + 283_614_464, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
+             "sha256": "267671cf94f31b0d"},
     "contraction/fp32": {"bytes": 337_105_152 + 159_488, "source": "paper_2105_08722_gb300/csrc/npcf_contract4.cu",
                          "sha256": "ec635d2be4d339ba"},
     "contraction/bf16": {"bytes": 338_193_920 + 3_255_552,
@@ -456,6 +456,109 @@ def run_gpu_batch(args):
     return 0
 
 
+def _timed_steps(args, step, dev):
+    """W untimed warm-up steps, then K steps each timed with CUDA events on the current
+    stream (L2 flushed in between, untimed); returns (mean ms, clocks)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.mean(ms)), clocks.stop()
+
+
+def run_gpu_c1(args):
+    """3PCF: 4,096 uniform points in a periodic 250 Mpc/h cube, 10 shells 0-50, lmax 5."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    wl = catalogs.c1_uniform_3pcf()
+    est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, FP32)
+    pos, w = torch.from_numpy(wl.pos).to(dev), torch.from_numpy(wl.w).to(dev)
+    ms, clk = _timed_steps(args, lambda: est.accumulate(pos, w), dev)
+    st = est.timings()
+    line = {
+        "metric": "primaries/sec for the 3PCF (lmax=5, 10 shells)", "value": wl.n / (ms * 1e-3),
+        "unit": "primaries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uniform_4096_L250_3pcf_lmax5_nr10_0-50", "n_points": wl.n,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
+        "gpu_launches": (KERNELS_PER_STEP - 2) * args.steps,
+        "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
+                      "reduction": float(st[3])},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
+def run_gpu_c3(args):
+    """Survey D - R: 400k log-normal data + 1.6M randoms (weights +1, -N_D/N_R) inside a
+    60 degree cap, 600-1400 Mpc/h, non-periodic; the 1.6M randoms-only run; the GPU edge
+    correction. One step = both accumulate calls and the edge-correction solve."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32, SPLIT_BF16
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    dr, rr = catalogs.c3_survey()
+    prec = FP32 if args.precision == "fp32" else SPLIT_BF16
+    nest = NPCF(dr.lmax, dr.orders, dr.edges, 0.0, prec)
+    rest = NPCF(rr.lmax, rr.orders, rr.edges, 0.0, prec)
+    dpos, dw = torch.from_numpy(dr.pos).to(dev), torch.from_numpy(dr.w).to(dev)
+    rpos, rw = torch.from_numpy(rr.pos).to(dev), torch.from_numpy(rr.w).to(dev)
+    stages = []
+
+    def step():
+        nest.reset()
+        rest.reset()
+        nest.accumulate(dpos, dw)
+        rest.accumulate(rpos, rw)
+        nest.edge_correct(rest)
+        stages.append(np.array(nest.timings(), np.float64) + np.array(rest.timings(), np.float64))
+
+    ms, clk = _timed_steps(args, step, dev)
+    st = np.mean(np.array(stages[-args.steps:]), axis=0)
+    n = dr.n + rr.n
+    line = {
+        "metric": "primaries/sec for the survey D-R 4PCF + 3PCF with edge correction (lmax=5, 10 shells)",
+        "value": n / (ms * 1e-3), "unit": "primaries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == FP32 else "bf16x3", "data": "synthetic",
+        "config": {"workload": "survey_DmR_400k_1600k_plus_R_1600k_4pcf3pcf_lmax5_nr10_20-160_edge",
+                   "n_points": n, "precision": args.precision, "l2": "inputs larger than L2",
+                   "parallelism": "single GPU"},
+        "gpu_launches": 2 * KERNELS_PER_STEP * args.steps + 2 * args.steps,
+        "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
+                      "reduction": float(st[3])},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
 def run_gpu_c4(args):
     """5PCF: 100k log-normal points, periodic 1000 Mpc/h, 8 shells 20-160, lmax 4 (all
     5PCF multiplets with l12 <= 2 lmax). One step = one npcf_accumulate."""
@@ -524,9 +627,9 @@ def main():
                     help="contraction arithmetic (default fp32; bf16 for the batch workload)")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the c2 workload at the same density (default 200,000)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
-                    help="c2: one 200k log-normal catalog (4PCF + 3PCF); c4: 100k, 5PCF; "
-                         "c5: 64 catalogs in one batch")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c1: 4k uniform, 3PCF; c2: one 200k log-normal catalog (4PCF + 3PCF); c3: survey "
+                         "D-R + R with edge correction; c4: 100k, 5PCF; c5: 64 catalogs in one batch")
     ap.add_argument("--cpu-sample", type=int, default=1500)
     ap.add_argument("--ref-sample", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -543,6 +646,10 @@ def main():
         return run_gpu_batch(args)
     if args.workload == "c4":
         return run_gpu_c4(args)
+    if args.workload == "c1":
+        return run_gpu_c1(args)
+    if args.workload == "c3":
+        return run_gpu_c3(args)
     return run_gpu(args)
 
 
