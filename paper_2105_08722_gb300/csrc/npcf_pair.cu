@@ -93,6 +93,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 // The exact FP32 neighbour rule (same operations as shell_of in npcf_rules.cuh) followed
 // by the shell lookup; -1 for a rejected pair. No loops: the range test is a predicate
 // and linear edges take a direct estimate with one correction. e2lo = e2[0], e2hi = e2[nr].
+// (A variant that skips the edge loads when the estimate is far from an edge measured
+// slower: its branch keeps the independent candidates of a step from interleaving.)
 __device__ __forceinline__ int pair_shell_fast(const float4 pj, const float4 pi, float sx, float sy, float sz,
                                                const float* e2, int nr, float e2lo, float e2hi, int linear,
                                                float r0, float inv_w) {
@@ -195,7 +197,7 @@ constexpr int kShiftCodes = 64;   // 2 bits per axis
 // Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
 // cap is the neighbour-list capacity of one group in 16-bit entries.
 struct PairLayout {
-    size_t cand, segs, rows, tpref, tdelta, tcode, ulist, ushell, slist, part, total;
+    size_t cand, segs, rows, tpref, tdc, tstart, tcode, ulist, ushell, slist, part, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -210,10 +212,12 @@ __host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int c
     l.cand = 0;
     l.segs = align16(l.cand + (size_t)cand_cap * 16);
     l.rows = align16(l.segs + (size_t)2 * nrows * 16);
-    // per group: flat-index prefix, staging offset minus prefix, and shift code of each row
+    // per group: flat-index prefix and (staging offset minus prefix, shift code) of each
+    // kept row; per-row scratch of the cut (staging start, code and count)
     l.tpref = align16(l.rows + (size_t)nrows * 16);
-    l.tdelta = align16(l.tpref + (size_t)kG * (2 * nrows + 1) * 4);
-    l.tcode = align16(l.tdelta + (size_t)kG * 2 * nrows * 4);
+    l.tdc = align16(l.tpref + (size_t)kG * (2 * nrows + 1) * 4);
+    l.tstart = align16(l.tdc + (size_t)kG * 2 * nrows * 4);
+    l.tcode = align16(l.tstart + (size_t)kG * 2 * nrows * 4);
     l.ulist = align16(l.tcode + (size_t)kG * 2 * nrows * 4);
     l.ushell = align16(l.ulist + (size_t)kG * cap * 2);
     l.slist = align16(l.ushell + (size_t)kG * cap);
@@ -272,21 +276,23 @@ __device__ __forceinline__ int x_bound(const float4* cand, int base, int n, floa
     return lo;
 }
 
-// The part of every staged row this primary can reach, as one flat index space:
-// row s covers flat [tpref[s], tpref[s+1]) and staged index = flat + tdelta[s]. With
-// trim, a row keeps only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus a
-// margin) of the primary, d_yz the distance from the primary to the row's (y, z) cell
-// square; the exact FP32 rule is applied to what remains. Rows are sorted by x (cells
-// in x order, members sorted by x). Returns the flat total.
+// The part of every staged row this primary can reach, as one flat index space over
+// the rows left non-empty: row s covers flat [tpref[s], tpref[s+1]), its staged index is
+// flat + (tdc[s] >> 6) and its periodic shift code tdc[s] & 63. With trim, a row keeps
+// only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus a margin) of the
+// primary, d_yz the distance from the primary to the row's (y, z) cell square; the exact
+// FP32 rule is applied to what remains. Rows are sorted by x (cells in x order, members
+// sorted by x). tstart and tcode are scratch. Returns the flat total; *nrow = rows kept.
 template <int L>
 __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>& sh, const float4* cand,
-                                         const int4* segs, int nseg, const float4 pi, int* tpref, int* tdelta,
-                                         int* tcode, int* wtot, bool trim, int grp, int warp, int lane) {
+                                         const int4* segs, int nseg, const float4 pi, int* tpref, int* tdc,
+                                         int* tstart, int* tcode, int* wtot, bool trim, int grp, int warp,
+                                         int lane, int* nrow) {
     const int gt = warp * 32 + lane;
     const int per = (nseg + kW * 32 - 1) / (kW * 32);   // rows per thread
     const int s0 = min(nseg, gt * per), s1 = min(nseg, s0 + per);
     const float R2 = sh.e2[a.nr], m = a.trim_margin, c = a.cell;
-    int cnt_local = 0;
+    int cnt_local = 0, rows_local = 0;
     for (int s = s0; s < s1; ++s) {
         const int4 sg = segs[s];
         int lo = 0, hi = sg.y;
@@ -307,30 +313,38 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
                 hi = x_bound<true>(cand, sg.z, sg.y, xc + h);
             }
         }
-        tdelta[s] = sg.z + lo;                    // minus the prefix below
-        tcode[s] = (sg.w & 63) | ((hi - lo) << 8);  // the count rides along until then
+        tstart[s] = sg.z + lo;
+        tcode[s] = (sg.w & 63) | ((hi - lo) << 8);
         cnt_local += hi - lo;
+        rows_local += hi > lo ? 1 : 0;
     }
-    // exclusive prefix of the counts over the group's threads
-    int incl = cnt_local;
+    // exclusive prefix over the group's threads of (rows kept << 16 | points); both fit
+    // in 16 bits: points <= staging capacity, rows <= 2 nrows
+    const int v = (rows_local << 16) | cnt_local;
+    int incl = v;
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
     }
     if (lane == 31) wtot[warp] = incl;
     group_sync(grp);
-    int base = incl - cnt_local;
+    int base = incl - v;
     for (int w = 0; w < warp; ++w) base += wtot[w];
     int total = 0;
     for (int w = 0; w < kW; ++w) total += wtot[w];
+    int pb = base & 0xffff, rb = base >> 16;
     for (int s = s0; s < s1; ++s) {
         const int cs = tcode[s] >> 8;
-        tcode[s] &= 63;
-        tpref[s] = base;
-        tdelta[s] -= base;
-        base += cs;
+        if (cs > 0) {
+            tpref[rb] = pb;
+            tdc[rb] = ((tstart[s] - pb) << 6) | (tcode[s] & 63);   // staged start >= flat start
+            ++rb;
+            pb += cs;
+        }
     }
-    if (gt == 0) tpref[nseg] = total;
+    *nrow = total >> 16;
+    total &= 0xffff;
+    if (gt == 0) tpref[*nrow] = total;
     group_sync(grp);
     return total;
 }
@@ -338,7 +352,7 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
 template <int L, bool STAGED>
 __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
                                             const int4* segs, int nseg, int total,
-                                            int* tpref, int* tdelta, int* tcode, bool trim,
+                                            int* tpref, int* tdc, int* tstart, int* tcode, bool trim,
                                             uint16_t* ulist, uint8_t* ushell, uint16_t* slist, float* part,
                                             int p, int cat, int grp, int warp, int lane, const int* slot_org) {
     constexpr int NC = ncomp(L);
@@ -370,8 +384,9 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     const float e2lo = sh.e2[0], e2hi = sh.e2[nr];
     uint32_t* sl32 = reinterpret_cast<uint32_t*>(slist);
     // staged: the rows cut to this primary's x-window, one flat index space split evenly
-    const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, pi, tpref, tdelta, tcode, G.wtot, trim, grp,
-                                        warp, lane)
+    int nrow = 0;
+    const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, pi, tpref, tdc, tstart, tcode, G.wtot, trim,
+                                        grp, warp, lane, &nrow)
                          : total;
     const int per = (T + kW - 1) / kW;
     int cursor = STAGED ? min(T, warp * per) : 0;
@@ -384,7 +399,7 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     float4 ssf = make_float4(0.f, 0.f, 0.f, 0.f);
     if (STAGED && cursor + lane < kend) {
         const int k0 = cursor + lane;
-        int lo = 0, n = nseg;
+        int lo = 0, n = nrow;
         while (n > 0) {
             const int half = n >> 1;
             if (tpref[lo + half + 1] <= k0) {
@@ -396,8 +411,9 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         }
         srow = lo;
         snext = tpref[srow + 1];
-        sdelta = tdelta[srow];
-        ssf = sh.shift[tcode[srow]];
+        const int dc = tdc[srow];
+        sdelta = dc >> 6;
+        ssf = sh.shift[dc & 63];
     }
     group_sync(grp);   // partials zeroed before any warp adds to them
 
@@ -407,15 +423,22 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         if (lane < kMaxNr) G.hist[warp][lane] = 0u;
         __syncwarp();
         if (STAGED) {
-            // two batches of 32 candidates per step while both still fit in the sub-list
+            // KC batches of 32 candidates per step while all still fit in the sub-list.
+            // locate moves a lane to the row of flat index k: rows are non-empty, so the
+            // next row's end and start/shift word load together and the loop rarely repeats
+            // (k < T = tpref[nrow] keeps r + 1 <= nrow)
             auto locate = [&](int k) {
                 if (k >= snext) {
-                    do {
-                        ++srow;
-                        snext = tpref[srow + 1];
-                    } while (k >= snext);
-                    sdelta = tdelta[srow];
-                    ssf = sh.shift[tcode[srow]];
+                    int r = srow + 1, nx = tpref[r + 1], dc = tdc[r];
+                    while (k >= nx) {
+                        ++r;
+                        nx = tpref[r + 1];
+                        dc = tdc[r];
+                    }
+                    srow = r;
+                    snext = nx;
+                    sdelta = dc >> 6;
+                    ssf = sh.shift[dc & 63];
                 }
             };
             // candidates per lane per step (independent chains). A step appends up to
@@ -548,6 +571,7 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                 if (pa >= pb) continue;
                 const int base = (int)G.off[t] - 32 * (int)G.pk[t], hi = (int)G.off[t + 1];
                 float acc[NC];
+                const float invL = 1.f / g.L;
 #pragma unroll
                 for (int i = 0; i < NC; ++i) acc[i] = 0.f;
                 for (int q = pa; q < pb; ++q) {
@@ -555,16 +579,16 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                     if (k >= hi) continue;
                     float dx, dy, dz, wj;
                     // accepted pairs are closer than r_max < L/3: the minimum image is the
-                    // image the neighbour rule accepted
+                    // image the neighbour rule accepted (taken without branches)
                     const float4 pj = STAGED ? cand[slist[k]] : a.pts[sl32[k]];
                     dx = pj.x - pi.x;
                     dy = pj.y - pi.y;
                     dz = pj.z - pi.z;
                     wj = pj.w;
                     if (g.periodic) {
-                        dx = dx > g.hL ? dx - g.L : (dx < -g.hL ? dx + g.L : dx);
-                        dy = dy > g.hL ? dy - g.L : (dy < -g.hL ? dy + g.L : dy);
-                        dz = dz > g.hL ? dz - g.L : (dz < -g.hL ? dz + g.L : dz);
+                        dx = fmaf(-g.L, rintf(dx * invL), dx);
+                        dy = fmaf(-g.L, rintf(dy * invL), dy);
+                        dz = fmaf(-g.L, rintf(dz * invL), dz);
                     }
                     const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                     harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, wj);
@@ -654,7 +678,8 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist) + (size_t)grp * a.cap;
     float* part = reinterpret_cast<float*>(dsm + lay.part) + (size_t)grp * part_floats(a.nr, ncomp(L));
     int* tpref = reinterpret_cast<int*>(dsm + lay.tpref) + (size_t)grp * (2 * a.nrows + 1);
-    int* tdelta = reinterpret_cast<int*>(dsm + lay.tdelta) + (size_t)grp * 2 * a.nrows;
+    int* tdc = reinterpret_cast<int*>(dsm + lay.tdc) + (size_t)grp * 2 * a.nrows;
+    int* tstart = reinterpret_cast<int*>(dsm + lay.tstart) + (size_t)grp * 2 * a.nrows;
     int* tcode = reinterpret_cast<int*>(dsm + lay.tcode) + (size_t)grp * 2 * a.nrows;
     // the x-window cut needs every cell sorted by x (binning flags bit 8 otherwise)
     const bool trim = a.trim != 0 && (*(volatile int*)a.err & 8) == 0;
@@ -715,10 +740,10 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
         }
         for (int p = pbeg + grp; p < pend; p += kG) {
             if (staged)
-                one_primary<L, true>(a, sh, cand, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
+                one_primary<L, true>(a, sh, cand, segs, nseg, total, tpref, tdc, tstart, tcode, trim, ulist,
                                      ushell, slist, part, p, cat, grp, warp, lane, slot_org);
             else
-                one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdelta, tcode, trim, ulist,
+                one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdc, tstart, tcode, trim, ulist,
                                       ushell, slist, part, p, cat, grp, warp, lane, slot_org);
         }
         __syncthreads();   // both groups are done with the staged points of this unit
