@@ -260,20 +260,21 @@ __device__ __forceinline__ void group_sync(int grp) {
 // at the end. Sub-lists that fill up end the slice early, and the scan resumes where it
 // stopped.
 // First index in [0, n) of the staged row at 'base' whose x is >= v (upper: > v).
-template <bool UPPER>
-__device__ __forceinline__ int x_bound(const float4* cand, int base, int n, float v) {
-    int lo = 0;
-    while (n > 0) {
-        const int half = n >> 1;
-        const float x = cand[base + lo + half].x;
-        if (UPPER ? !(x > v) : (x < v)) {
-            lo += half + 1;
-            n -= half + 1;
-        } else {
-            n = half;
+// Both ends of the staged row at 'base' (n points, sorted by x) that fall in [vlo, vhi]:
+// the first index with x >= vlo and the first with x > vhi. The two searches run in
+// lockstep without branches: the answer is built bit by bit from the highest power of
+// two <= n, each bit kept if the predicate holds at the probed index.
+__device__ __forceinline__ int2 x_bounds(const float4* cand, int base, int n, float vlo, float vhi) {
+    int a = 0, b = 0;
+    if (n > 0) {
+        for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
+            const float xa = cand[base + min(a + step, n) - 1].x;
+            const float xb = cand[base + min(b + step, n) - 1].x;
+            a += (a + step <= n && xa < vlo) ? step : 0;
+            b += (b + step <= n && !(xb > vhi)) ? step : 0;
         }
     }
-    return lo;
+    return make_int2(a, b);
 }
 
 // The part of every staged row this primary can reach, as one flat index space over
@@ -309,8 +310,9 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
             } else {
                 const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
                 const float xc = pi.x + sf.x;
-                lo = x_bound<false>(cand, sg.z, sg.y, xc - h);
-                hi = x_bound<true>(cand, sg.z, sg.y, xc + h);
+                const int2 ab = x_bounds(cand, sg.z, sg.y, xc - h, xc + h);
+                lo = ab.x;
+                hi = ab.y;
             }
         }
         tstart[s] = sg.z + lo;
@@ -393,12 +395,11 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     const int kend = STAGED ? min(T, cursor + per) : 0;
     int seg = warp, segpos = 0;   // global-memory path: segments warp, warp + kW, ...
     const unsigned lt = (1u << lane) - 1u;
-    // staged: the row of flat index cursor + lane (first s with tpref[s + 1] > it), its end,
-    // its staged offset and its periodic shift
-    int srow = 0, snext = 0, sdelta = 0;
-    float4 ssf = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (STAGED && cursor + lane < kend) {
-        const int k0 = cursor + lane;
+    // staged: the row of flat index cursor (first s with tpref[s + 1] > cursor), the same
+    // in every lane
+    int srow = 0;
+    if (STAGED && cursor < kend) {
+        const int k0 = cursor;
         int lo = 0, n = nrow;
         while (n > 0) {
             const int half = n >> 1;
@@ -410,10 +411,6 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
             }
         }
         srow = lo;
-        snext = tpref[srow + 1];
-        const int dc = tdc[srow];
-        sdelta = dc >> 6;
-        ssf = sh.shift[dc & 63];
     }
     group_sync(grp);   // partials zeroed before any warp adds to them
 
@@ -423,41 +420,35 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         if (lane < kMaxNr) G.hist[warp][lane] = 0u;
         __syncwarp();
         if (STAGED) {
-            // KC batches of 32 candidates per step while all still fit in the sub-list.
-            // locate moves a lane to the row of flat index k: rows are non-empty, so the
-            // next row's end and start/shift word load together and the loop rarely repeats
-            // (k < T = tpref[nrow] keeps r + 1 <= nrow)
-            auto locate = [&](int k) {
-                if (k >= snext) {
-                    int r = srow + 1, nx = tpref[r + 1], dc = tdc[r];
-                    while (k >= nx) {
-                        ++r;
-                        nx = tpref[r + 1];
-                        dc = tdc[r];
-                    }
-                    srow = r;
-                    snext = nx;
-                    sdelta = dc >> 6;
-                    ssf = sh.shift[dc & 63];
-                }
-            };
             // candidates per lane per step (independent chains). A step appends up to
             // 32 KC entries, so capw >= 32 KC is required for progress: the host admits
             // list capacities of at least 1024 (capw >= 128).
             constexpr int KC = 4;
             while (cw + 32 * KC <= capw && cursor < kend) {
-                int q[KC], b[KC];
-                float4 sf[KC];
+                // Rows of the step's flat indices cursor + o, o < 32 KC, without per-lane
+                // searches: lane i loads the end of row srow + i (rows are non-empty, so the
+                // ends increase strictly); a bitmap of the ends' offsets in the step gives
+                // each offset's row as srow + the ends at or below it. The step stops at the
+                // last loaded end, so no row beyond the loaded ones is met.
+                const int d = tpref[min(srow + 1 + lane, nrow)] - cursor;   // >= 1
+                const int lim = min(min(32 * KC, kend - cursor), __shfl_sync(kFull, d, 31));
+                unsigned W[KC];
 #pragma unroll
                 for (int j = 0; j < KC; ++j) {
-                    const int k = cursor + 32 * j + lane;
-                    q[j] = 0;
-                    sf[j] = ssf;
-                    if (k < kend) {
-                        locate(k);
-                        q[j] = k + sdelta;
-                        sf[j] = ssf;
-                    }
+                    const unsigned o = (unsigned)(d - 32 * j);
+                    W[j] = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
+                }
+                const unsigned le = 0xffffffffu >> (31 - lane);   // offsets 32 j .. 32 j + lane
+                int q[KC], b[KC];
+                float4 sf[KC];
+                int below = 0;
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    const int row = min(srow + below + __popc(W[j] & le), nrow - 1);
+                    below += __popc(W[j]);
+                    const int dc = tdc[row];
+                    q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + (dc >> 6) : 0;
+                    sf[j] = sh.shift[dc & 63];
                 }
                 float4 c[KC];
 #pragma unroll
@@ -466,7 +457,7 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                 for (int j = 0; j < KC; ++j) {
                     const int r = pair_shell_fast(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.e2, nr, e2lo, e2hi,
                                                   a.linear, a.lin_r0, a.lin_inv_w);
-                    b[j] = (cursor + 32 * j + lane < kend) ? r : -1;
+                    b[j] = (32 * j + lane < lim) ? r : -1;
                 }
 #pragma unroll
                 for (int j = 0; j < KC; ++j) {
@@ -480,9 +471,9 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                     const unsigned gm = __match_any_sync(kFull, b[j]);
                     if (b[j] >= 0 && lane == __ffs(gm) - 1) atomicAdd(&G.hist[warp][b[j]], (uint32_t)__popc(gm));
                 }
-                cursor += 32 * KC;
+                srow += __popc(__ballot_sync(kFull, d <= lim));   // the row of cursor + lim
+                cursor += lim;
             }
-            cursor = min(cursor, kend);
         } else {
             while (seg < nseg && cw + 32 <= capw) {
                 const int4 sg = segs[seg];
