@@ -100,6 +100,8 @@ struct npcf_ctx {
     DevBuf<int> c5binq;
     DevBuf<int4> c5items;
     int c5nitem = 0;
+    DevBuf<int4> c5parts;        // multiplets of each item
+    int c5npart = 0;
     DevBuf<int2> c5segs12, c5segs34;
     int c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
 
@@ -287,28 +289,56 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
     std::vector<int> binq((size_t)nr * nr, 0);
     for (int b2 = 1; b2 + 2 < nr; ++b2)
         for (int b1 = 0; b1 < b2; ++b1) binq[(size_t)b1 * nr + b2] = bin_index(b1, b2, b2 + 1, b2 + 2);
-    // items (multiplet, beta = b2), grouped by beta (the kernel's specialisation), heaviest first
-    std::vector<std::pair<double, int4>> items;
+    // items (up to c5_group multiplets sharing (l12 l3 l4), beta = b2), grouped by beta
+    // (the kernel's specialisation), heaviest first
+    std::vector<std::vector<int>> by34;
     for (int a = 0; a < o.n_lambda(); ++a) {
-        const int* L = &o.lam[(size_t)a * 5];
-        const int t12 = t.lam_t12[a], t34 = t.lam_t34[a], l12 = L[2];
+        const int t34 = t.lam_t34[a];
+        if ((int)by34.size() <= t34) by34.resize(t34 + 1);
+        by34[t34].push_back(a);
+    }
+    struct Item5 {
+        double key;
+        int4 head;
+        std::vector<int4> parts;
+    };
+    std::vector<Item5> items;
+    for (int t34 = 0; t34 < (int)by34.size(); ++t34) {
+        const std::vector<int>& mult = by34[t34];
+        if (mult.empty()) continue;
+        const int l12 = o.lam[(size_t)mult[0] * 5 + 2];
         for (int beta = 1; beta + 2 < nr; ++beta) {
-            const int m = nr - 1 - beta;
-            double cost = 0;
-            for (int m12 = 0; m12 <= l12; ++m12) {
-                const int k12 = t.seg12_end[t.t12_seg0[t12] + m12] - t.seg12_begin[t.t12_seg0[t12] + m12];
-                const int k34 = t.seg34_end[t.t34_seg0[t34] + m12] - t.seg34_begin[t.t34_seg0[t34] + m12];
-                cost += k12 * beta + k34 * m * (m - 1) / 2.0 + beta * m * (m - 1) / 2.0;
+            const int m = nr - 1 - beta, G = c5_group(beta, m);
+            for (size_t h0 = 0; h0 < mult.size(); h0 += G) {
+                Item5 I;
+                I.key = 0;
+                const size_t h1 = std::min(mult.size(), h0 + G);
+                for (int m12 = 0; m12 <= l12; ++m12) {
+                    const int k34 = t.seg34_end[t.t34_seg0[t34] + m12] - t.seg34_begin[t.t34_seg0[t34] + m12];
+                    I.key += k34 * m * (m - 1) / 2.0;
+                    for (size_t h = h0; h < h1; ++h) {
+                        const int t12 = t.lam_t12[mult[h]];
+                        const int k12 = t.seg12_end[t.t12_seg0[t12] + m12] - t.seg12_begin[t.t12_seg0[t12] + m12];
+                        I.key += k12 * beta + beta * m * (m - 1) / 2.0;
+                    }
+                }
+                I.key += 1e12 * beta;
+                I.head = make_int4(t.t34_seg0[t34], l12 | (beta << 8) | ((int)(h1 - h0) << 16), 0, 0);
+                for (size_t h = h0; h < h1; ++h) {
+                    const int a = mult[h];
+                    I.parts.push_back(make_int4(t.t12_seg0[t.lam_t12[a]], off + a * nb, o.odd(a) ? 1 : 0, 0));
+                }
+                items.push_back(std::move(I));
             }
-            items.push_back({1e12 * beta + cost,
-                             make_int4(t.t12_seg0[t12], t.t34_seg0[t34], l12 | (beta << 8) | ((o.odd(a) ? 1 : 0) << 16),
-                                       off + a * nb)});
         }
     }
-    std::stable_sort(items.begin(), items.end(),
-                     [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) { return x.first > y.first; });
-    std::vector<int4> it;
-    for (const auto& x : items) it.push_back(x.second);
+    std::stable_sort(items.begin(), items.end(), [](const Item5& x, const Item5& y) { return x.key > y.key; });
+    std::vector<int4> it, parts;
+    for (Item5& x : items) {
+        x.head.z = (int)parts.size();
+        it.push_back(x.head);
+        parts.insert(parts.end(), x.parts.begin(), x.parts.end());
+    }
     {
         Contract5WArgs c{};
         c.nr = nr;
@@ -325,6 +355,8 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
                         "memory (limit %d)", contract5w_smem_bytes(c), optin);
     }
     ctx->c5nitem = (int)it.size();
+    ctx->c5npart = (int)parts.size();
+    CU(upload(ctx->c5parts, parts));
     ctx->c5nterms12 = (int)c12.size();
     ctx->c5nterms34 = (int)c34.size();
     ctx->c5nseg12 = (int)s12.size();
@@ -823,6 +855,8 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.binq = ctx->c5binq.p;
             c.items = ctx->c5items.p;
             c.nitem = ctx->c5nitem;
+            c.partners = ctx->c5parts.p;
+            c.npartner = ctx->c5npart;
             c.chunks = ctx->chunks.p;
             c.nchunk = P.nchunk;
             c.partial = ctx->partial.p;

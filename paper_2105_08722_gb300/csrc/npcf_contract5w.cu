@@ -8,9 +8,10 @@
 // with only m12 >= 0 summed (App. B: 2 S(m12) and Q_L = Re / Im).
 //
 // A block stages the a_lm of 32 primaries as [lm][b][primary]; its warps take items
-// (L, beta) with b2 = beta. For an item each lane (one primary) builds in registers
-// P12^{m12}(b1, beta) for every b1 < beta and P34^{m12}(b3, b4) for every beta < b3 < b4,
-// and accumulates their products over m12 into the item's (b1, b3, b4) sums. Coupling
+// (up to G multiplets L that share (l12 l3 l4), beta) with b2 = beta. For an item each lane
+// (one primary) builds in registers P34^{m12}(b3, b4) for every beta < b3 < b4 once, then
+// for each of the item's multiplets P12^{m12}(b1, beta) for every b1 < beta, and
+// accumulates their products over m12 into that multiplet's (b1, b3, b4) sums. Coupling
 // terms (in shared memory), loop bounds and branches are the same on every lane. After the
 // tile the warp reduces its sums across lanes and adds them to the chunk's FP64 row.
 #include "npcf_device.h"
@@ -43,6 +44,7 @@ __host__ __device__ inline C5Layout c5_layout(int nr, int nlm, int nt12, int nt3
 }
 
 struct C5Shared {
+    const int4* partners;
     const float2* X;
     const float* su;
     const float4* c12;
@@ -54,47 +56,41 @@ struct C5Shared {
     const int* binq;
 };
 
-// Item (L, beta) for one tile: NB = beta rows b1 < beta, M = nr - 1 - beta shells after
-// beta (NP = M (M - 1) / 2 pairs b3 < b4). item = (first P12 segment of (l1 l2 l12), first
-// P34 segment of (l12 l3 l4), l12 | beta << 8 | odd << 16, first output of L).
+// Item for one tile: NB = beta rows b1 < beta, M = nr - 1 - beta shells after beta (NP =
+// M (M - 1) / 2 pairs b3 < b4), g <= G multiplets sharing (l12 l3 l4). item = (first P34
+// segment of (l12 l3 l4), l12 | beta << 8 | g << 16, first partner, 0); partner = (first
+// P12 segment of (l1 l2 l12), first output of L, odd, 0).
 template <int NB, int M>
 __device__ __forceinline__ void c5_item(const int4 item, const C5Shared& s, int nr, double* __restrict__ dst,
                                         int lane) {
     constexpr int NP = M * (M - 1) / 2;
     constexpr int NOUT = NB * NP;
-    const int l12 = item.z & 0xff;
-    const bool odd = ((item.z >> 16) & 1) != 0;
+    constexpr int G = c5_group(NB, M);
+    const int l12 = item.y & 0xff;
+    const int g = (item.y >> 16) & 0xff;
     const float rcf = sqrtf((float)(2 * l12 + 1));
     const float2* Xl = s.X + lane;
     const float u = s.su[lane];
-    float acc[NOUT];
+    int seg12[G], out0[G];
+    bool odd[G];
 #pragma unroll
-    for (int i = 0; i < NOUT; ++i) acc[i] = 0.f;
+    for (int h = 0; h < G; ++h) {
+        const int4 P = h < g ? s.partners[item.z + h] : make_int4(0, 0, 0, 0);
+        seg12[h] = P.x;
+        out0[h] = P.y;
+        odd[h] = P.z != 0;
+    }
+    float acc[G][NOUT];
+#pragma unroll
+    for (int h = 0; h < G; ++h)
+#pragma unroll
+        for (int i = 0; i < NOUT; ++i) acc[h][i] = 0.f;
     for (int m12 = 0; m12 <= l12; ++m12) {
-        // P12(b1, beta) for b1 < beta; the b2 factor is the same for every b1
-        float p12r[NB], p12i[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) p12r[j] = p12i[j] = 0.f;
-        const int2 S12 = s.s12[item.x + m12];
-        for (int k = S12.x; k < S12.y; ++k) {
-            const float4 c = s.c12[k];
-            const uint32_t o = s.o12[k];
-            const float2 x2 = Xl[(o >> 16) + NB * kRS5];
-            // re += cA x1 x2 + cB y1 y2 ; im += cC y1 x2 + cD x1 y2 (conjugations folded in c)
-            const float a0 = c.x * x2.x, a1 = c.y * x2.y, a2 = c.z * x2.x, a3 = c.w * x2.y;
-            const float2* X1 = Xl + (o & 0xffffu);
-#pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                const float2 x1 = X1[j * kRS5];
-                p12r[j] = fmaf(a0, x1.x, fmaf(a1, x1.y, p12r[j]));
-                p12i[j] = fmaf(a2, x1.y, fmaf(a3, x1.x, p12i[j]));
-            }
-        }
         // P34(b3, b4) for beta < b3 < b4, pairs in lexicographic order
         float p34r[NP], p34i[NP];
 #pragma unroll
         for (int p = 0; p < NP; ++p) p34r[p] = p34i[p] = 0.f;
-        const int2 S34 = s.s34[item.y + m12];
+        const int2 S34 = s.s34[item.x + m12];
         for (int k = S34.x; k < S34.y; ++k) {
             const float4 c = s.c34[k];
             const uint32_t o = s.o34[k];
@@ -115,24 +111,53 @@ __device__ __forceinline__ void c5_item(const int4 item, const C5Shared& s, int 
                 }
             }
         }
-        // u 2 S(m12) (-1)^{l12 - m12} sqrt(2 l12 + 1), then Re (even L) or Im (odd L) of P12 P34
+        // u 2 S(m12) (-1)^{l12 - m12} sqrt(2 l12 + 1)
         const float cm = u * (m12 == 0 ? 1.f : 2.f) * (((l12 - m12) & 1) ? -1.f : 1.f) * rcf;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const float A = cm * (odd ? p12i[j] : p12r[j]);
-            const float B = cm * (odd ? p12r[j] : -p12i[j]);
+        for (int h = 0; h < G; ++h) {
+            if (h >= g) break;
+            // P12(b1, beta) for b1 < beta; the b2 factor is the same for every b1
+            float p12r[NB], p12i[NB];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) acc[j * NP + p] = fmaf(A, p34r[p], fmaf(B, p34i[p], acc[j * NP + p]));
+            for (int j = 0; j < NB; ++j) p12r[j] = p12i[j] = 0.f;
+            const int2 S12 = s.s12[seg12[h] + m12];
+            for (int k = S12.x; k < S12.y; ++k) {
+                const float4 c = s.c12[k];
+                const uint32_t o = s.o12[k];
+                const float2 x2 = Xl[(o >> 16) + NB * kRS5];
+                // re += cA x1 x2 + cB y1 y2 ; im += cC y1 x2 + cD x1 y2 (conjugations folded in c)
+                const float a0 = c.x * x2.x, a1 = c.y * x2.y, a2 = c.z * x2.x, a3 = c.w * x2.y;
+                const float2* X1 = Xl + (o & 0xffffu);
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const float2 x1 = X1[j * kRS5];
+                    p12r[j] = fmaf(a0, x1.x, fmaf(a1, x1.y, p12r[j]));
+                    p12i[j] = fmaf(a2, x1.y, fmaf(a3, x1.x, p12i[j]));
+                }
+            }
+            // Re (even L) or Im (odd L) of P12 P34
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const float A = cm * (odd[h] ? p12i[j] : p12r[j]);
+                const float B = cm * (odd[h] ? p12r[j] : -p12i[j]);
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    acc[h][j * NP + p] = fmaf(A, p34r[p], fmaf(B, p34i[p], acc[h][j * NP + p]));
+            }
         }
     }
     using R = warp::TR<NOUT>;
-    R::run(acc, lane);
 #pragma unroll
-    for (int i = 0; i < R::F; ++i) {
-        const int e = R::origin(i, lane);
-        if (e >= 0) {
-            const int j = e / NP, p = e - j * NP;
-            dst[item.w + s.binq[j * nr + NB] + p] += (double)acc[i];
+    for (int h = 0; h < G; ++h) {
+        if (h >= g) break;
+        R::run(acc[h], lane);
+#pragma unroll
+        for (int i = 0; i < R::F; ++i) {
+            const int e = R::origin(i, lane);
+            if (e >= 0) {
+                const int j = e / NP, p = e - j * NP;
+                dst[out0[h] + s.binq[j * nr + NB] + p] += (double)acc[h][i];
+            }
         }
     }
 }
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(256, 2) k_contract5w(const Contract5WArgs a) {
     for (int i = tid; i < a.nseg12; i += blockDim.x) s12[i] = a.segs12[i];
     for (int i = tid; i < a.nseg34; i += blockDim.x) s34[i] = a.segs34[i];
     for (int i = tid; i < NR * NR; i += blockDim.x) binq[i] = a.binq[i];
-    const C5Shared sh{X, su, c12, o12, c34, o34, s12, s34, binq};
+    const C5Shared sh{a.partners, X, su, c12, o12, c34, o34, s12, s34, binq};
     const int rows = NR * a.nlm;
 
     // chunks (primary ranges of one catalog) taken dynamically; chunk c sums into row c
@@ -187,7 +212,7 @@ __global__ void __launch_bounds__(256, 2) k_contract5w(const Contract5WArgs a) {
                 it = __shfl_sync(warp::kFullMask, it, 0);
                 if (it >= a.nitem) break;
                 const int4 item = a.items[it];
-                switch ((item.z >> 8) & 0xff) {   // beta
+                switch ((item.y >> 8) & 0xff) {   // beta
 #define NPCF_C5_CASE(B) \
     case B:             \
         if (B <= NR - 3) c5_item<(B <= NR - 3 ? B : 1), (B <= NR - 3 ? NR - 1 - B : 2)>(item, sh, NR, dst, lane); \

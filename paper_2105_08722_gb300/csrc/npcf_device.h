@@ -181,14 +181,23 @@ struct Contract5WArgs {
     const int2* segs34;
     int nterms12, nterms34, nseg12, nseg34;
     const int* binq;           // [nr][nr]: bin index of (b1, b2, b2 + 1, b2 + 2)
-    const int4* items;         // (P12 segment of m12 = 0, P34 segment of m12 = 0, l12 | beta << 8 | odd << 16, first output of L)
+    const int4* items;         // (P34 segment of m12 = 0, l12 | beta << 8 | partners << 16, first partner, 0)
     int nitem;
+    const int4* partners;      // (P12 segment of m12 = 0, first output of L, odd, 0) per multiplet L of an item
+    int npartner;
     const int2* chunks;        // primary ranges, none crossing a catalog
     int nchunk;
     double* partial;           // [nchunk][total]
     int total, out_off, nout;
     int* chunk_counter;        // zeroed before the launch
 };
+// Multiplets (l1 l2 l12 l3 l4) of one 5PCF item: they share (l12 l3 l4) and so the P34
+// build. Two while their sums fit in 64 registers, else one (measured: three or four per
+// item ran slower, the kernel's register cap of 128 leaving too little room).
+__host__ __device__ constexpr int c5_group(int nb, int m) {
+    const int g = 64 / (nb * m * (m - 1) / 2);
+    return g < 1 ? 1 : (g > 2 ? 2 : g);
+}
 void launch_contract5w(const Contract5WArgs& a, int nblocks, cudaStream_t s);
 size_t contract5w_smem_bytes(const Contract5WArgs& a);
 size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);

@@ -359,6 +359,18 @@ def test_5pcf_periodic_lmax3(torch_dev):
     assert_orders_close(got, want, (5,), 3, 6)
 
 
+@pytest.mark.parametrize("nr", [9, 10])
+def test_5pcf_many_shells(torch_dev, nr):
+    # 9 and 10 shells take items of 1 to 4 multiplets sharing (l12 l3 l4), by b2
+    pos = catalogs.lognormal_box(700, 150.0, 32, seed=53)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(4.0, 40.0, nr + 1)
+    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 3, edges, 150.0)
+    want, wcounts = oracle.npcf(pos, w, (5,), 3, edges, 150.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (5,), 3, nr)
+
+
 def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev):
     pos, w = _catalog(500, 80.0, 52)
     w = w - np.float32(0.8)
