@@ -126,9 +126,9 @@ __device__ __forceinline__ int pair_shell_fast(const float4 pj, const float4 pi,
 // code bits 0-5: periodic shift, 2 bits per axis; bits 6-18: the row's y cell; bits 19-31:
 // its z cell. Computed by one warp; the totals go to shared memory.
 __device__ void build_segments(const PairArgs& a, const int4* rows, int cbase, int cx, int cy, int cz, int run,
-                               int4* segs, int* out_nseg, int* out_total, int lane) {
+                               int4* segs, int* out_nseg, int* out_total, int* out_maxseg, int lane) {
     const GridInfo& g = a.g;
-    int nseg = 0, total = 0;
+    int nseg = 0, total = 0, maxseg = 0;
     for (int r0 = 0; r0 < a.nrows; r0 += 32) {
         const int r = r0 + lane;
         int cnt[2] = {0, 0}, beg[2] = {0, 0}, code[2] = {0, 0}, ns = 0;
@@ -173,7 +173,14 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cbase, i
         // drop empty segments, then a warp scan of segment and point counts
         int k = 0, pts = 0;
         for (int q = 0; q < ns; ++q)
-            if (cnt[q] > 0) { beg[k] = beg[q]; cnt[k] = cnt[q]; code[k] = code[q]; pts += cnt[q]; ++k; }
+            if (cnt[q] > 0) {
+                beg[k] = beg[q];
+                cnt[k] = cnt[q];
+                code[k] = code[q];
+                pts += cnt[q];
+                maxseg = max(maxseg, cnt[q]);
+                ++k;
+            }
         int ks = k, ps = pts;
         for (int o = 1; o < 32; o <<= 1) {
             int a1 = __shfl_up_sync(kFull, ks, o), a2 = __shfl_up_sync(kFull, ps, o);
@@ -187,7 +194,8 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cbase, i
         nseg += __shfl_sync(kFull, ks, 31);
         total += __shfl_sync(kFull, ps, 31);
     }
-    if (lane == 0) { *out_nseg = nseg; *out_total = total; }
+    for (int o = 16; o > 0; o >>= 1) maxseg = max(maxseg, __shfl_xor_sync(kFull, maxseg, o));
+    if (lane == 0) { *out_nseg = nseg; *out_total = total; *out_maxseg = maxseg; }
 }
 
 constexpr int kW = 8;             // warps per group; a group works on one primary
@@ -245,7 +253,7 @@ struct PairShared {
     float kmat[nlmc(L) * (L + 1)];
     float e2[kMaxNr + 1];
     GroupShared grp[kG];
-    int unit[4];
+    int unit[6];
 };
 
 __device__ __forceinline__ void group_sync(int grp) {
@@ -356,7 +364,8 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
                                             const int4* segs, int nseg, int total,
                                             int* tpref, int* tdc, int* tstart, int* tcode, bool trim,
                                             uint16_t* ulist, uint8_t* ushell, uint16_t* slist, float* part,
-                                            int p, int cat, int grp, int warp, int lane, const int* slot_org) {
+                                            int p, int cat, bool add, int grp, int warp, int lane,
+                                            const int* slot_org) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
     using R = TR<NC>;
@@ -367,8 +376,10 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     float2* out = a.alm + (size_t)p * nr * NLM;
     const float u = a.wp[p];
     if (u == 0.f) {  // primary not evaluated
-        for (int i = gt; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
-        if (gt < nr) a.cnt[(size_t)p * nr + gt] = 0u;
+        if (!add) {
+            for (int i = gt; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
+            if (gt < nr) a.cnt[(size_t)p * nr + gt] = 0u;
+        }
         return;
     }
     const float4 pi = a.pts[p];
@@ -626,11 +637,16 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
             re = fmaf(kk, sr, re);
             im = fmaf(kk, sim, im);
         }
+        if (add) {   // a later staging pass of the unit: a_lm is linear in the sums
+            const float2 o = out[i];
+            re += o.x;
+            im += o.y;
+        }
         out[i] = make_float2(re, im);
     }
     if (gt < nr) {
         const uint32_t c = G.tot[gt];
-        a.cnt[(size_t)p * nr + gt] = c;
+        a.cnt[(size_t)p * nr + gt] = add ? a.cnt[(size_t)p * nr + gt] + c : c;
         if (c) atomicAdd(&a.counts[(size_t)cat * nr + gt], (unsigned long long)c);
     }
     group_sync(grp);   // partials and totals are reset by the next primary
@@ -699,45 +715,82 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
             __syncthreads();
             continue;
         }
-        if (wblk == 0) build_segments(a, rows, cbase, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], lane);
+        if (wblk == 0)
+            build_segments(a, rows, cbase, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], &sh.unit[3], lane);
         __syncthreads();
         const int nseg = sh.unit[1], total = sh.unit[2];
-        const bool staged = total <= a.cand_cap;
-        if (staged && total > 0) {
-            // stage the neighbour points with bulk asynchronous copies (one mbarrier)
+        if (sh.unit[3] > a.cand_cap) {
+            // a row longer than the staging buffer: neighbours straight from global memory
+            for (int p = pbeg + grp; p < pend; p += kG)
+                one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdc, tstart, tcode, trim, ulist,
+                                      ushell, slist, part, p, cat, false, grp, warp, lane, slot_org);
+            __syncthreads();
+            continue;
+        }
+        // Staged in passes of consecutive rows that fit the staging buffer (one pass unless
+        // the unit's neighbourhood is larger); each pass adds its sums to the primaries'
+        // a_lm and counts. A pass of the rows [s0, s1) is staged with bulk asynchronous
+        // copies (one mbarrier), its rows' offsets rebased to the buffer.
+        bool failed = false;
+        for (int s0 = 0, pass = 0; pass == 0 || s0 < nseg; ++pass) {
             if (threadIdx.x == 0) {
-                const uint32_t b = smem_u32(&bar);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                             "r"((uint32_t)total * 16u)
-                             : "memory");
-                for (int s = 0; s < nseg; ++s) {
-                    const int4 sg = segs[s];
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-                            "r"(smem_u32(cand + sg.z)),
-                        "l"(a.pts + sg.x), "r"((uint32_t)sg.y * 16u), "r"(b)
-                        : "memory");
+                int s1 = s0, ptotal = 0;
+                if (s0 < nseg) {
+                    // the most rows from s0 whose points fit (staging offsets increase)
+                    const int base = segs[s0].z;
+                    int lo = s0 + 1, n = nseg - s0 - 1;   // answer in [s0 + 1, nseg]
+                    while (n > 0) {
+                        const int half = n >> 1;
+                        const int4 sg = segs[lo + half];
+                        if (sg.z + sg.y - base <= a.cand_cap) {
+                            lo += half + 1;
+                            n -= half + 1;
+                        } else {
+                            n = half;
+                        }
+                    }
+                    s1 = lo;
+                    for (int q = s0; q < s1; ++q) segs[q].z -= base;
+                    ptotal = segs[s1 - 1].z + segs[s1 - 1].y;
+                }
+                sh.unit[4] = s1;
+                sh.unit[5] = ptotal;
+                if (ptotal > 0) {
+                    const uint32_t b = smem_u32(&bar);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                                 "r"((uint32_t)ptotal * 16u)
+                                 : "memory");
+                    for (int q = s0; q < s1; ++q) {
+                        const int4 sg = segs[q];
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                            "[%3];" ::"r"(smem_u32(cand + sg.z)),
+                            "l"(a.pts + sg.x), "r"((uint32_t)sg.y * 16u), "r"(b)
+                            : "memory");
+                    }
                 }
             }
-            const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
-            // the whole block leaves together if any thread's wait gave up
-            if (__syncthreads_or(ok ? 0 : 1)) {
-                if (threadIdx.x == 0) atomicOr(a.err, 2);
-                mbar_wait_bounded(smem_u32(&bar), parity);  // give in-flight copies a last chance to land
-                break;
+            __syncthreads();
+            const int s1 = sh.unit[4], ptotal = sh.unit[5];
+            if (ptotal > 0) {
+                const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
+                // the whole block leaves together if any thread's wait gave up
+                if (__syncthreads_or(ok ? 0 : 1)) {
+                    if (threadIdx.x == 0) atomicOr(a.err, 2);
+                    mbar_wait_bounded(smem_u32(&bar), parity);  // give in-flight copies a last chance to land
+                    failed = true;
+                    break;
+                }
+                parity ^= 1u;
             }
-            parity ^= 1u;
+            for (int p = pbeg + grp; p < pend; p += kG)
+                one_primary<L, true>(a, sh, cand, segs + s0, s1 - s0, ptotal, tpref, tdc, tstart, tcode, trim,
+                                     ulist, ushell, slist, part, p, cat, pass > 0, grp, warp, lane, slot_org);
+            __syncthreads();   // both groups are done with this pass's staged points
+            s0 = s1;
         }
-        for (int p = pbeg + grp; p < pend; p += kG) {
-            if (staged)
-                one_primary<L, true>(a, sh, cand, segs, nseg, total, tpref, tdc, tstart, tcode, trim, ulist,
-                                     ushell, slist, part, p, cat, grp, warp, lane, slot_org);
-            else
-                one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdc, tstart, tcode, trim, ulist,
-                                      ushell, slist, part, p, cat, grp, warp, lane, slot_org);
-        }
-        __syncthreads();   // both groups are done with the staged points of this unit
+        if (failed) break;
     }
 }
 

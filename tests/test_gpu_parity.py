@@ -198,18 +198,33 @@ def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
 @pytest.mark.parametrize("tuning", [
     {},                 # staged neighbour cells, one list slice per primary
     {3: 1024},          # staged, several list slices per primary
-    {4: 256},           # neighbour cells too large to stage: global-memory path
-    {3: 1024, 4: 256},  # global-memory path with several list slices
+    {4: 256},           # neighbourhood larger than the staging buffer: staged in passes
+    {3: 1024, 4: 256},  # several staging passes, each with several list slices
+    {4: 16},            # rows longer than the staging buffer: global-memory path
+    {3: 1024, 4: 16},   # global-memory path with several list slices
 ])
 def test_dense_primaries_staged_and_global_paths(torch_dev, tuning):
     # ~1000 neighbours per primary: with a list capacity of 1024 every primary takes
-    # several slices
+    # several slices; rows of ~30 points and neighbourhoods of ~3000 points per unit
     pos, w = _catalog(9000, 60.0, 61)
     edges = np.linspace(2.0, 18.0, 5)
     _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0, tuning=tuning)
     want, wcounts = oracle.npcf(pos, w, (3, 4), 3, edges, 60.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (3, 4), 3, 4)
+
+
+def test_non_periodic_signed_weights_staged_in_passes(torch_dev):
+    # data-minus-randoms style weights in an open box; a staging limit of 128 points splits
+    # every unit's neighbourhood into many passes, also at the box faces
+    pos, w = _catalog(4000, 60.0, 62)
+    w = np.where(np.arange(len(w)) % 4 == 0, np.float32(-0.25), w).astype(np.float32)
+    edges = np.linspace(3.0, 15.0, 5)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 3, edges, 0.0)
+    for tuning in ({}, {4: 128}):
+        _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 0.0, tuning=tuning)
+        assert np.array_equal(counts, wcounts), tuning
+        assert_orders_close(got, want, (3, 4), 3, 4)
 
 
 def test_accumulate_coadds_and_reset(torch_dev):
