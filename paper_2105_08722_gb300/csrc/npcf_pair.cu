@@ -253,7 +253,7 @@ struct PairShared {
     float kmat[nlmc(L) * (L + 1)];
     float e2[kMaxNr + 1];
     GroupShared grp[kG];
-    int unit[6];
+    int unit[4];
 };
 
 __device__ __forceinline__ void group_sync(int grp) {
@@ -294,9 +294,9 @@ __device__ __forceinline__ int2 x_bounds(const float4* cand, int base, int n, fl
 // sorted by x). tstart and tcode are scratch. Returns the flat total; *nrow = rows kept.
 template <int L>
 __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>& sh, const float4* cand,
-                                         const int4* segs, int nseg, const float4 pi, int* tpref, int* tdc,
-                                         int* tstart, int* tcode, int* wtot, bool trim, int grp, int warp,
-                                         int lane, int* nrow) {
+                                         const int4* segs, int nseg, int zbase, const float4 pi, int* tpref,
+                                         int* tdc, int* tstart, int* tcode, int* wtot, bool trim, int grp,
+                                         int warp, int lane, int* nrow) {
     const int gt = warp * 32 + lane;
     const int per = (nseg + kW * 32 - 1) / (kW * 32);   // rows per thread
     const int s0 = min(nseg, gt * per), s1 = min(nseg, s0 + per);
@@ -318,12 +318,12 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
             } else {
                 const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
                 const float xc = pi.x + sf.x;
-                const int2 ab = x_bounds(cand, sg.z, sg.y, xc - h, xc + h);
+                const int2 ab = x_bounds(cand, sg.z - zbase, sg.y, xc - h, xc + h);
                 lo = ab.x;
                 hi = ab.y;
             }
         }
-        tstart[s] = sg.z + lo;
+        tstart[s] = sg.z - zbase + lo;
         tcode[s] = (sg.w & 63) | ((hi - lo) << 8);
         cnt_local += hi - lo;
         rows_local += hi > lo ? 1 : 0;
@@ -361,7 +361,7 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
 
 template <int L, bool STAGED>
 __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
-                                            const int4* segs, int nseg, int total,
+                                            const int4* segs, int nseg, int zbase, int total,
                                             int* tpref, int* tdc, int* tstart, int* tcode, bool trim,
                                             uint16_t* ulist, uint8_t* ushell, uint16_t* slist, float* part,
                                             int p, int cat, bool add, int grp, int warp, int lane,
@@ -398,8 +398,8 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     uint32_t* sl32 = reinterpret_cast<uint32_t*>(slist);
     // staged: the rows cut to this primary's x-window, one flat index space split evenly
     int nrow = 0;
-    const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, pi, tpref, tdc, tstart, tcode, G.wtot, trim,
-                                        grp, warp, lane, &nrow)
+    const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, zbase, pi, tpref, tdc, tstart, tcode, G.wtot,
+                                        trim, grp, warp, lane, &nrow)
                          : total;
     const int per = (T + kW - 1) / kW;
     int cursor = STAGED ? min(T, warp * per) : 0;
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
         if (sh.unit[3] > a.cand_cap) {
             // a row longer than the staging buffer: neighbours straight from global memory
             for (int p = pbeg + grp; p < pend; p += kG)
-                one_primary<L, false>(a, sh, cand, segs, nseg, total, tpref, tdc, tstart, tcode, trim, ulist,
+                one_primary<L, false>(a, sh, cand, segs, nseg, 0, total, tpref, tdc, tstart, tcode, trim, ulist,
                                       ushell, slist, part, p, cat, false, grp, warp, lane, slot_org);
             __syncthreads();
             continue;
@@ -730,49 +730,43 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
         // Staged in passes of consecutive rows that fit the staging buffer (one pass unless
         // the unit's neighbourhood is larger); each pass adds its sums to the primaries'
         // a_lm and counts. A pass of the rows [s0, s1) is staged with bulk asynchronous
-        // copies (one mbarrier), its rows' offsets rebased to the buffer.
+        // copies (one mbarrier); row s sits at sg.z - segs[s0].z in the buffer.
         bool failed = false;
         for (int s0 = 0, pass = 0; pass == 0 || s0 < nseg; ++pass) {
-            if (threadIdx.x == 0) {
-                int s1 = s0, ptotal = 0;
-                if (s0 < nseg) {
-                    // the most rows from s0 whose points fit (staging offsets increase)
-                    const int base = segs[s0].z;
-                    int lo = s0 + 1, n = nseg - s0 - 1;   // answer in [s0 + 1, nseg]
-                    while (n > 0) {
-                        const int half = n >> 1;
-                        const int4 sg = segs[lo + half];
-                        if (sg.z + sg.y - base <= a.cand_cap) {
-                            lo += half + 1;
-                            n -= half + 1;
-                        } else {
-                            n = half;
-                        }
+            // every thread plans the pass (the same search over the shared row list)
+            int s1 = s0, ptotal = 0;
+            const int zbase = s0 < nseg ? segs[s0].z : 0;
+            if (s0 < nseg) {
+                // the most rows from s0 whose points fit (staging offsets increase)
+                int lo = s0 + 1, n = nseg - s0 - 1;   // answer in [s0 + 1, nseg]
+                while (n > 0) {
+                    const int half = n >> 1;
+                    const int4 sg = segs[lo + half];
+                    if (sg.z + sg.y - zbase <= a.cand_cap) {
+                        lo += half + 1;
+                        n -= half + 1;
+                    } else {
+                        n = half;
                     }
-                    s1 = lo;
-                    for (int q = s0; q < s1; ++q) segs[q].z -= base;
-                    ptotal = segs[s1 - 1].z + segs[s1 - 1].y;
                 }
-                sh.unit[4] = s1;
-                sh.unit[5] = ptotal;
-                if (ptotal > 0) {
-                    const uint32_t b = smem_u32(&bar);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                                 "r"((uint32_t)ptotal * 16u)
-                                 : "memory");
-                    for (int q = s0; q < s1; ++q) {
-                        const int4 sg = segs[q];
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                            "[%3];" ::"r"(smem_u32(cand + sg.z)),
-                            "l"(a.pts + sg.x), "r"((uint32_t)sg.y * 16u), "r"(b)
-                            : "memory");
-                    }
+                s1 = lo;
+                ptotal = segs[s1 - 1].z + segs[s1 - 1].y - zbase;
+            }
+            if (threadIdx.x == 0 && ptotal > 0) {
+                const uint32_t b = smem_u32(&bar);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                             "r"((uint32_t)ptotal * 16u)
+                             : "memory");
+                for (int q = s0; q < s1; ++q) {
+                    const int4 sg = segs[q];
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                        "[%3];" ::"r"(smem_u32(cand + (sg.z - zbase))),
+                        "l"(a.pts + sg.x), "r"((uint32_t)sg.y * 16u), "r"(b)
+                        : "memory");
                 }
             }
-            __syncthreads();
-            const int s1 = sh.unit[4], ptotal = sh.unit[5];
             if (ptotal > 0) {
                 const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
                 // the whole block leaves together if any thread's wait gave up
@@ -785,8 +779,9 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
                 parity ^= 1u;
             }
             for (int p = pbeg + grp; p < pend; p += kG)
-                one_primary<L, true>(a, sh, cand, segs + s0, s1 - s0, ptotal, tpref, tdc, tstart, tcode, trim,
-                                     ulist, ushell, slist, part, p, cat, pass > 0, grp, warp, lane, slot_org);
+                one_primary<L, true>(a, sh, cand, segs + s0, s1 - s0, zbase, ptotal, tpref, tdc, tstart, tcode,
+                                     trim, ulist, ushell, slist, part, p, cat, pass > 0, grp, warp, lane,
+                                     slot_org);
             __syncthreads();   // both groups are done with this pass's staged points
             s0 = s1;
         }
