@@ -121,10 +121,10 @@ def test_pair_counts_on_exact_edges_and_duplicates(torch_dev):
 
 # ------------------------------------------------------------------ a_lm
 
-def test_alm_of_sampled_primaries(torch_dev):
+@pytest.mark.parametrize("lmax", [6, 8, 10])
+def test_alm_of_sampled_primaries(torch_dev, lmax):
     pos, w = _catalog(4000, 150.0, 7)
     edges = np.linspace(5.0, 40.0, 8)
-    lmax = 6
     est, _, _ = gpu_run(torch_dev, pos, w, (3,), lmax, edges, 150.0)
     sample = np.array([0, 1, 17, 500, 1999, 3998, 3999])
     a_gpu, c_gpu = est.debug_alm(sample)
@@ -167,6 +167,30 @@ def test_4pcf_3pcf_periodic_lmax5_10_shells(torch_dev):
     want, wcounts = oracle.npcf(pos, w, (3, 4), 5, edges, 300.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (3, 4), 5, 10)
+
+
+@pytest.mark.parametrize("lmax", [6, 8, 10])
+def test_high_lmax_3pcf_and_4pcf_or_refusal(torch_dev, lmax):
+    # the paper's lmax = 10 setting on a small catalog. The 3PCF takes any lmax <= 10; the
+    # 4PCF contractions stage the coupling terms and a tile of a_lm (split-bf16: also one
+    # 128-row operand slab per m3) in shared memory and are refused at create (or
+    # accumulate) where those exceed it: FP32 beyond lmax 6, split-bf16 beyond lmax 5
+    from paper_2105_08722_gb300._lib import NPCFError
+    pos = catalogs.lognormal_box(400, 100.0, 32, seed=81)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(5.0, 30.0, 5)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), lmax, edges, 100.0)
+    want3, _ = oracle.npcf(pos, w, (3,), lmax, edges, 100.0)
+    _, got3, counts = gpu_run(torch_dev, pos, w, (3,), lmax, edges, 100.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got3, want3, (3,), lmax, 4)
+    for prec, tol, lmax_ok in ((0, TOL_FP32, 6), (1, TOL_BF16, 5)):
+        try:
+            _, got, _ = gpu_run(torch_dev, pos, w, (3, 4), lmax, edges, 100.0, prec=prec)
+        except NPCFError as e:
+            assert lmax > lmax_ok and "memory" in str(e), str(e)
+        else:
+            assert_orders_close(got, want, (3, 4), lmax, 4, tol=tol)
 
 
 def test_4pcf_all_parity_non_periodic_weighted(torch_dev):
