@@ -510,6 +510,50 @@ def run_gpu_c1(args):
     return 0
 
 
+# The paper's own timings on its Table 2 catalog (16-core CPU), as primaries/s = 5e4 / T
+PAPER_TABLE2_CPU = {4: 5.0e4 / 4.8, 5: 5.0e4 / 741.8}
+
+
+def run_gpu_paper(args, order):
+    """The paper's timing setting (Table 2): 5e4 uniform points, periodic 1500 Mpc/h box,
+    10 shells to 200 Mpc/h, lmax 5; order 4 (with the 3PCF) or order 5."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32, SPLIT_BF16
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    orders = (3, 4) if order == 4 else (5,)
+    wl = catalogs.paper_uniform_1500(orders=orders)
+    prec = SPLIT_BF16 if (args.precision == "bf16" and order == 4) else FP32
+    est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, prec)
+    pos, w = torch.from_numpy(wl.pos).to(dev), torch.from_numpy(wl.w).to(dev)
+    ms, clk = _timed_steps(args, lambda: est.accumulate(pos, w), dev)
+    st = est.timings()   # stages of the last timed step
+    value = wl.n / (ms * 1e-3)
+    name = "4PCF (with the 3PCF)" if order == 4 else "5PCF"
+    line = {
+        "metric": "primaries/sec for the %s (lmax=5, 10 shells) on the paper's timing catalog" % name,
+        "value": value, "unit": "primaries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_TABLE2_CPU[order],
+        "dtype": "bf16x3" if prec == SPLIT_BF16 else "f32", "data": "synthetic",
+        "config": {"workload": "uniform_50k_L1500_%s_lmax5_nr10_0-200" % ("4pcf3pcf" if order == 4 else "5pcf"),
+                   "n_points": wl.n, "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU",
+                   "baseline": "the paper's 16-core CPU time on this catalog (Table 2): %.4g primaries/s"
+                               % PAPER_TABLE2_CPU[order]},
+        "gpu_launches": (KERNELS_PER_STEP - (0 if order == 4 else 2)) * args.steps,
+        "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
+                      "reduction": float(st[3])},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
 def run_gpu_c3(args):
     """Survey D - R: 400k log-normal data + 1.6M randoms (weights +1, -N_D/N_R) inside a
     60 degree cap, 600-1400 Mpc/h, non-periodic; the 1.6M randoms-only run; the GPU edge
@@ -627,9 +671,10 @@ def main():
                     help="contraction arithmetic (default fp32; bf16 for the batch workload)")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the c2 workload at the same density (default 200,000)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "paper4", "paper5"],
                     help="c1: 4k uniform, 3PCF; c2: one 200k log-normal catalog (4PCF + 3PCF); c3: survey "
-                         "D-R + R with edge correction; c4: 100k, 5PCF; c5: 64 catalogs in one batch")
+                         "D-R + R with edge correction; c4: 100k, 5PCF; c5: 64 catalogs in one batch; "
+                         "paper4 / paper5: the paper's timing catalog (5e4 uniform, L 1500), 4PCF / 5PCF")
     ap.add_argument("--cpu-sample", type=int, default=1500)
     ap.add_argument("--ref-sample", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -648,6 +693,8 @@ def main():
         return run_gpu_c4(args)
     if args.workload == "c1":
         return run_gpu_c1(args)
+    if args.workload in ("paper4", "paper5"):
+        return run_gpu_paper(args, 4 if args.workload == "paper4" else 5)
     if args.workload == "c3":
         return run_gpu_c3(args)
     return run_gpu(args)

@@ -164,6 +164,14 @@ def c1_uniform_3pcf(n: int = 4096) -> Workload:
                     linear_edges(0.0, 50.0, 10), 5, (3,), 250.0)
 
 
+def paper_uniform_1500(n: int = 50_000, lmax: int = 5, orders=(3, 4)) -> Workload:
+    """The paper's timing catalog (Table 2): about 5e4 uniform points in a periodic
+    1500 Mpc/h box, pairs up to r_max = 200 Mpc/h in 10 shells (r_min = 0)."""
+    pos = uniform_box(n, 1500.0, seed=1500)
+    return Workload("uniform_%dk_L1500" % (n // 1000), pos, np.ones(n, np.float32),
+                    linear_edges(0.0, 200.0, 10), lmax, tuple(orders), 1500.0)
+
+
 def c2_lognormal_4pcf(n: int = 200_000, mesh: int = 256) -> Workload:
     """200k log-normal points, periodic 1000 Mpc/h cube, 10 shells 20-160, lmax 5, 3+4PCF."""
     pos = lognormal_box(n, 1000.0, mesh, seed=1002)
