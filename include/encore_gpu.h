@@ -151,7 +151,7 @@ npcf_status npcf_pair_counts_batch(npcf_ctx* ctx, uint64_t* out, size_t out_len)
 
 /* Autotuner: runs the pipeline on the catalog (d_pos, d_w, n as in npcf_accumulate) for
  * candidate settings and keeps the fastest: pair kernel (median of three timed runs after a
- * warm-up) over cells per r_max {4, 5, 6} x cells per work unit {2, 3, 4} x list capacity
+ * warm-up) over cells per r_max {2, ..., 6} x cells per work unit {2, 3, 4} x list capacity
  * {4096, 6144}, then the contractions over primaries per chunk (1, 2, 4 or 8 waves of
  * chunks over the SMs). The accumulators must be empty (fresh context or npcf_reset) and
  * are reset afterwards. chosen (nullable, host int[4]) receives the settings: tuning keys
@@ -177,13 +177,15 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
                            uint32_t* counts);
 
 /* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8; the cell
- * side of the neighbour grid is about r_max / key0), key 2 = contraction primaries
+ * side of the neighbour grid is about r_max / key0; 0, the default, picks 2, 3 or 5 from
+ * the mean number of neighbours within r_max: below ~630, ~2,500, or more), key 2 = contraction primaries
  * per chunk, rounded up to a multiple of 64, for every contraction kernel (0 = automatic:
  * about n / (4 x SMs) for the 3PCF and 5PCF, n / SMs for the 4PCF), key 3 = pair-kernel neighbour-list capacity per block
  * (multiple of 256 in 1024..16384 entries; larger lists mean fewer slices for dense
  * primaries, smaller ones leave more shared memory for staging), key 4 = cap on the
- * neighbour points staged in shared memory per cell (0 = as many as fit; cells with
- * more neighbours read them from global memory instead), key 5 = x-adjacent cells
+ * neighbour points staged in shared memory at a time (0 = as many as fit; a larger
+ * neighbourhood is staged in several passes, and a work unit with a single row of cells
+ * longer than the cap reads its neighbours from global memory), key 5 = x-adjacent cells
  * per pair-kernel work unit (1..4), key 6 = split-bf16 contraction: steps of 16 primaries
  * between drains of the tensor-memory accumulators into FP64 (>= 1; fewer steps bound the
  * accumulation error of the tensor cores more tightly), key 7 = pair kernel: cut each staged

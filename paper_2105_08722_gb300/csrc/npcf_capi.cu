@@ -66,7 +66,7 @@ struct npcf_ctx {
     int nlm = 0;
 
     // cell-list tuning and geometry
-    int cells_per_rmax = 5;
+    int cells_per_rmax = 0;    // 0: chosen per call from the catalog's density
     int cell_run = 3;          // x-adjacent cells per pair-kernel work unit
     int pair_cap = 6144;       // per group of the pair kernel
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
@@ -493,12 +493,28 @@ npcf_status check_ctx(npcf_ctx* ctx) {
 }
 
 // Grid and neighbour rows for the current geometry.
-npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s) {
+// Cells per r_max when tuning key 0 is 0, from the mean number of neighbours within r_max
+// of a primary, nbar 4/3 pi r_max^3 (nbar: points per catalog / volume). Coarse cells mean
+// fewer neighbour rows per primary and per work unit, which is what a sparse catalog pays
+// for; in a dense one they make a unit's neighbourhood outgrow the staging buffer (staged
+// in several passes) and cut the rows to the x-window less tightly. Measured on the pair
+// kernel (log-normal and uniform catalogs from 137 to 3,400 neighbours per primary, lmax 4
+// and 5): 2 was best below ~600 neighbours, 3 from ~850 to ~1,700, 5 at ~3,400.
+int auto_cells_per_rmax(double points, double volume, double rmax) {
+    if (!(volume > 0) || !(points > 0)) return 5;
+    const double nb = points / volume * (4.0 / 3.0) * M_PI * rmax * rmax * rmax;
+    return nb < 630.0 ? 2 : (nb < 2500.0 ? 3 : 5);
+}
+
+npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, int ncat, cudaStream_t s) {
     const double rmax = ctx->edges[ctx->nr];
+    const double per_cat = (double)n / std::max(ncat, 1);
     GridInfo g{};
     std::vector<int> rows;
     if (ctx->box > 0) {
-        if (!plan_periodic_grid(ctx->box, rmax, ctx->cells_per_rmax, 1 << 27, &g, &rows))
+        const int k = ctx->cells_per_rmax > 0 ? ctx->cells_per_rmax
+                                              : auto_cells_per_rmax(per_cat, ctx->box * ctx->box * ctx->box, rmax);
+        if (!plan_periodic_grid(ctx->box, rmax, k, 1 << 27, &g, &rows))
             return fail(ctx, NPCF_EINVAL, "box %.6g too small for r_max %.6g", ctx->box, rmax);
     } else {
         // bounding box of the catalog (one stream synchronisation)
@@ -520,7 +536,10 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, cudaStream_t s)
             if (!std::isfinite(mn[a]) || !std::isfinite(mx[a]))
                 return fail(ctx, NPCF_EINVAL, "non-finite positions");
         }
-        plan_open_grid(mn, mx, rmax, ctx->cells_per_rmax, 1 << 24, &g, &rows);
+        double vol = 1.0;   // the bounding box (at least r_max on a side)
+        for (int a = 0; a < 3; ++a) vol *= std::max((double)mx[a] - (double)mn[a], rmax);
+        const int k = ctx->cells_per_rmax > 0 ? ctx->cells_per_rmax : auto_cells_per_rmax(per_cat, vol, rmax);
+        plan_open_grid(mn, mx, rmax, k, 1 << 24, &g, &rows);
     }
     if (rows != ctx->rows_host) {
         ctx->rows_host = rows;
@@ -571,7 +590,7 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         CU(cudaMemset(ctx->sumw.p, 0, ncat * sizeof(double)));
         ctx->ncat = ncat;
     }
-    npcf_status st = setup_grid(ctx, d_pos, n, s);
+    npcf_status st = setup_grid(ctx, d_pos, n, ncat, s);
     if (st != NPCF_OK) return st;
     const GridInfo& g = ctx->grid;
     const size_t cells = (size_t)g.ncell * ncat;
@@ -1165,7 +1184,7 @@ npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, i
     int best[4] = {keep[0], keep[1], keep[2], keep[3]};
     float best_ms = 1e30f;
     // pair kernel: grid cell size, cells per work unit, neighbour-list capacity
-    for (int k : {4, 5, 6})
+    for (int k : {2, 3, 4, 5, 6})
         for (int run : {2, 3, 4})
             for (int cap : {4096, 6144}) {
                 ctx->cells_per_rmax = k;
@@ -1360,7 +1379,8 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
     if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
     switch (key) {
         case 0:
-            if (value < 1 || value > 8) return fail(ctx, NPCF_EINVAL, "cells per r_max in [1, 8]");
+            if (value < 0 || value > 8)
+                return fail(ctx, NPCF_EINVAL, "cells per r_max in [1, 8], or 0 for the density rule");
             ctx->cells_per_rmax = value;
             return NPCF_OK;
         case 2:
