@@ -12,15 +12,21 @@
 // The Chebyshev basis keeps the conversion coefficients O(1), so FP32 sums do not lose
 // accuracy to cancellation at high l as plain powers z^k would.
 //
-// One warp owns one primary at a time (dynamic schedule over cell-sorted primaries):
-//   pass 0: scan the neighbour cells, apply the exact FP32 neighbour/shell rule and
-//           count neighbours per shell;
-//   pass 1: scan again and write neighbour indices into a shared-memory list ordered
-//           by shell (only as many as fit; primaries with more neighbours repeat
-//           pass 1 for the next slice);
-//   accumulate: per shell, lanes take neighbours in parallel and accumulate the
-//           S_{m,k} in registers; a shuffle transpose-reduction gives the per-shell
-//           sums, which are converted to a_lm and written once per (primary, shell).
+// A persistent block (2 groups of 8 warps) takes work units, runs of x-adjacent cells of
+// one catalog's grid, from a device counter. For a unit, warp 0 lists the neighbour rows
+// (rows of cells within r_max of the run) and one thread stages their points into shared
+// memory with bulk asynchronous copies, in passes of rows that fit the buffer. A group
+// then takes the unit's primaries one at a time:
+//   cut: every staged row is cut to the primary's x-window and the kept rows form one
+//        flat index space, split evenly over the group's warps;
+//   scan: each lane tests candidates with the exact FP32 neighbour/shell rule; accepted
+//        pairs go to the warp's sub-list (16-bit staged index, shell), shells counted;
+//   sort: a counting sort orders the group's slice by shell (a full sub-list ends the
+//        slice early; the scan then resumes where it stopped);
+//   accumulate: each warp takes an equal run of 32-entry packets of the sorted slice,
+//        accumulates the S_{m,k} of each shell in registers and reduces them across
+//        lanes with a shuffle transpose-reduction; the per-shell sums, folded in warp
+//        order, are converted to a_lm (added to the earlier passes' a_lm, if any).
 #include "npcf_device.h"
 #include "npcf_rules.cuh"
 #include "npcf_warp.cuh"
