@@ -40,7 +40,7 @@ KERNELS_PER_STEP = 10  # k_sumw, 4 cell-list kernels, pair, contract3, contract4
 # roofline reports them only while the source is unchanged (profiles/ has the captures).
 TRAFFIC = {
     "pair": {"bytes": 7_390_976 + 284_114_944, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
-             "sha256": "c2f6e8f7333394dc"},
+             "sha256": "9375143f7f912fdf"},
     "contraction/fp32": {"bytes": 337_105_152 + 159_488, "source": "paper_2105_08722_gb300/csrc/npcf_contract4.cu",
                          "sha256": "ec635d2be4d339ba"},
     "contraction/bf16": {"bytes": 338_193_920 + 3_255_552,

@@ -266,14 +266,6 @@ __device__ __forceinline__ void group_sync(int grp) {
     asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kW * 32) : "memory");
 }
 
-// One primary, processed by one group of kW warps. Neighbours are split evenly over the
-// warps (flat staged range, or segments round-robin for the global-memory path); each
-// warp appends accepted neighbours (index, shell) to its own sub-list; a counting sort
-// orders the slice by shell (ranks from __match_any_sync); the sorted slice is cut into
-// kW equal chunks whose per-shell sums go to per-warp partials; the partials give a_lm
-// at the end. Sub-lists that fill up end the slice early, and the scan resumes where it
-// stopped.
-// First index in [0, n) of the staged row at 'base' whose x is >= v (upper: > v).
 // Both ends of the staged row at 'base' (n points, sorted by x) that fall in [vlo, vhi]:
 // the first index with x >= vlo and the first with x > vhi. The two searches run in
 // lockstep without branches: the answer is built bit by bit from the highest power of
@@ -365,6 +357,14 @@ __device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>&
     return total;
 }
 
+// One primary, processed by one group of kW warps. Neighbours are split evenly over the
+// warps (flat index space of the cut staged rows, or segments round-robin for the
+// global-memory path); each warp appends accepted neighbours (index, shell) to its own
+// sub-list; a counting sort orders the slice by shell (ranks from __match_any_sync); each
+// warp takes an equal run of 32-entry packets of the sorted slice and its per-shell sums
+// go to per-warp partials, which give a_lm at the end (added to the a_lm of earlier
+// staging passes when add is set). Sub-lists that fill up end the slice early, and the
+// scan resumes where it stopped.
 template <int L, bool STAGED>
 __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
                                             const int4* segs, int nseg, int zbase, int total,
