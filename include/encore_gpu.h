@@ -230,6 +230,20 @@ npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, int nr, cons
  * the call returns NPCF_EINVAL. Synchronises the device. */
 npcf_status npcf_edge_correct(npcf_ctx* nctx, npcf_ctx* rctx, double* out);
 
+/* Truncation to a smaller lmax (Sec. 3.3: N and R are measured with an lmax one larger than
+ * the output's, so that the edge correction of the multiplets near the output lmax is
+ * accurate). in: host double[in_len] in this context's output layout (npcf_finalize,
+ * one catalog's row of npcf_finalize_batch, or npcf_edge_correct); out: host
+ * double[out_len] in the layout a context with lmax_out (same orders, shells, parity)
+ * would have: of every order, the multiplets whose l's are all <= lmax_out (for the 5PCF
+ * also l12 <= 2 lmax_out), in the same order, with all their bin tuples. in_len must be
+ * npcf_output_size(ctx). out_len: with out == NULL it receives the length of the smaller
+ * layout (in may then be NULL too); otherwise it must hold that length. NPCF_EINVAL for a
+ * length mismatch or an lmax_out that is negative or above the context's lmax. Host only;
+ * does not touch the device. */
+npcf_status npcf_truncate(const npcf_ctx* ctx, const double* in, size_t in_len, int lmax_out, double* out,
+                          size_t* out_len);
+
 /* Generalized Gaunt integral G^{L1 L2 L3} = int dR P_L1 P_L2 P_L3 (Eq. generalized-gaunt-def)
  * from the closed forms of App. A (Wigner 3-j and 9-j symbols), the values the edge
  * correction uses. Host-only (no device work). L1, L2, L3: host int multiplets of order

@@ -43,6 +43,7 @@ SIGNATURES = {
     "npcf_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64)]),
     "npcf_autotune": (_i, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "npcf_gaunt": (_i, [_i, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "npcf_truncate": (_i, [_vp, _vp, _sz, _i, _vp, ctypes.POINTER(_sz)]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
 }
@@ -215,6 +216,17 @@ class NPCF:
         data-minus-randoms sums, ``randoms`` the randoms-only sums."""
         out = np.zeros(self.size, dtype=np.float64)
         self._check(self._lib.npcf_edge_correct(self._h, randoms._h, out.ctypes.data))
+        return out
+
+    def truncate(self, flat: np.ndarray, lmax_out: int) -> np.ndarray:
+        """This context's output (finalize, one catalog of finalize_batch or edge_correct)
+        cut to the multiplets of an lmax_out context (npcf_truncate)."""
+        flat = np.ascontiguousarray(flat, dtype=np.float64)
+        n = _sz()
+        self._check(self._lib.npcf_truncate(self._h, None, flat.size, int(lmax_out), None, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.float64)
+        self._check(self._lib.npcf_truncate(self._h, flat.ctypes.data, flat.size, int(lmax_out),
+                                            out.ctypes.data, ctypes.byref(n)))
         return out
 
     def pair_counts(self) -> np.ndarray:

@@ -1065,6 +1065,40 @@ npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len) {
     return NPCF_OK;
 }
 
+npcf_status npcf_truncate(const npcf_ctx* ctx, const double* in, size_t in_len, int lmax_out, double* out,
+                          size_t* out_len) {
+    if (!ctx || !out_len) return NPCF_EINVAL;
+    if (lmax_out < 0 || lmax_out > ctx->lmax) return NPCF_EINVAL;
+    // the multiplets an lmax_out context holds are those of this one whose l's fit
+    auto keep = [&](const OrderTable& o, int a) {
+        const int* L = &o.lam[(size_t)a * o.width];
+        for (int k = 0; k < o.width; ++k) {
+            const int cap = (o.N == 5 && k == 2) ? 2 * lmax_out : lmax_out;   // l12 couples two l's
+            if (L[k] > cap) return false;
+        }
+        return true;
+    };
+    size_t need = 0;
+    for (const OrderTable& o : ctx->orders)
+        for (int a = 0; a < o.n_lambda(); ++a)
+            if (keep(o, a)) need += (size_t)o.n_bins();
+    if (!out) {
+        *out_len = need;
+        return NPCF_OK;
+    }
+    if (!in || in_len != (size_t)ctx->total || *out_len != need) return NPCF_EINVAL;
+    size_t src = 0, dst = 0;
+    for (const OrderTable& o : ctx->orders) {
+        const size_t nb = (size_t)o.n_bins();
+        for (int a = 0; a < o.n_lambda(); ++a, src += nb)
+            if (keep(o, a)) {
+                std::memcpy(out + dst, in + src, nb * sizeof(double));
+                dst += nb;
+            }
+    }
+    return NPCF_OK;
+}
+
 npcf_status npcf_layout(const npcf_ctx* ctx, int order, int* n_lambda, int* n_bins, int* lambdas, int* bins) {
     if (!ctx) return NPCF_EINVAL;
     for (const OrderTable& o : ctx->orders) {

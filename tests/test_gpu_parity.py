@@ -504,6 +504,78 @@ def test_edge_correction_end_to_end_against_oracle(torch_dev):
         assert err <= 100 * TOL_FP32, (N, err)
 
 
+def _oracle_truncate(per_order, N, lmax, lmax_out):
+    lam = oracle.multiplets(N, lmax)
+    keep = np.all(lam <= lmax_out, axis=1)
+    return per_order[keep]
+
+
+def test_truncate_matches_a_context_at_the_smaller_lmax(torch_dev):
+    from paper_2105_08722_gb300._lib import NPCFError
+    pos, w = _catalog(1200, 90.0, 73)
+    edges = np.linspace(4.0, 28.0, 6)
+    for orders, allparity, lmax in (((3, 4), False, 4), ((3, 4, 5), True, 3)):
+        big, zbig, _ = gpu_run(torch_dev, pos, w, orders, lmax, edges, 90.0, allparity=allparity)
+        _, zsmall, _ = gpu_run(torch_dev, pos, w, orders, lmax - 1, edges, 90.0, allparity=allparity)
+        cut = big.truncate(zbig, lmax - 1)
+        assert cut.shape == zsmall.shape
+        scale = np.sqrt(np.mean(zsmall ** 2))
+        assert np.max(np.abs(cut - zsmall)) <= 1e-6 * scale
+        assert np.array_equal(big.truncate(zbig, lmax), zbig)
+        with pytest.raises(NPCFError):
+            big.truncate(zbig, lmax + 1)
+        with pytest.raises(NPCFError):
+            big.truncate(zbig[:-1], lmax - 1)
+
+
+def test_edge_correction_at_lmax_plus_one_truncated(torch_dev):
+    # Sec. 3.3: N and R measured one lmax higher than the output, corrected, then cut
+    pos, w, rpos, rw = _ball_catalogs(74)
+    lmax, edges = 3, np.linspace(5.0, 30.0, 6)
+    nr = len(edges) - 1
+    nctx, rctx, _, _ = _edge_contexts(torch_dev, pos, w, rpos, rw, lmax + 1, edges)
+    got = oracle.split_orders(nctx.truncate(nctx.edge_correct(rctx), lmax), (3, 4), lmax, nr)
+    nraw, _ = oracle.npcf(pos, w, (3, 4), lmax + 1, edges, 0.0)
+    rraw, _ = oracle.npcf(rpos, rw, (3, 4), lmax + 1, edges, 0.0)
+    n = oracle.split_orders(nraw, (3, 4), lmax + 1, nr)
+    r = oracle.split_orders(rraw, (3, 4), lmax + 1, nr)
+    for N in (3, 4):
+        want = _oracle_truncate(oracle.edge_correct(N, lmax + 1, nr, n[N], r[N]), N, lmax + 1, lmax)
+        scale = np.sqrt(np.mean(want ** 2))
+        assert np.max(np.abs(got[N] - want)) / scale <= 100 * TOL_FP32, N
+
+
+def test_edge_correction_of_coadded_random_splits(torch_dev):
+    # two random splits: N = (D - R1) + (D - R2) and R = R1 + R2 co-added by repeated
+    # accumulate calls, then corrected (the paper's split randoms)
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    pos, w, rpos, rw = _ball_catalogs(75, n_rand=3000)
+    nd = int(np.sum(w > 0))
+    d = pos[:nd]
+    halves = (rpos[:1500], rpos[1500:])
+    lmax, edges = 3, np.linspace(5.0, 30.0, 6)
+    nr = len(edges) - 1
+    nctx, rctx = NPCF(lmax, (3, 4), edges, 0.0), NPCF(lmax, (3, 4), edges, 0.0)
+    nsum = rsum = 0.0
+    for rk in halves:
+        ratio = nd / len(rk)
+        dm = np.concatenate([d, rk]).astype(np.float32)
+        wm = np.concatenate([np.ones(nd), np.full(len(rk), -ratio)]).astype(np.float32)
+        wr = np.full(len(rk), ratio, np.float32)
+        nctx.accumulate(torch.from_numpy(dm).to(dev), torch.from_numpy(wm).to(dev))
+        rctx.accumulate(torch.from_numpy(rk).to(dev), torch.from_numpy(wr).to(dev))
+        nsum = nsum + oracle.npcf(dm, wm, (3, 4), lmax, edges, 0.0)[0]
+        rsum = rsum + oracle.npcf(rk, wr, (3, 4), lmax, edges, 0.0)[0]
+    got = oracle.split_orders(nctx.edge_correct(rctx), (3, 4), lmax, nr)
+    n = oracle.split_orders(nsum, (3, 4), lmax, nr)
+    r = oracle.split_orders(rsum, (3, 4), lmax, nr)
+    for N in (3, 4):
+        want = oracle.edge_correct(N, lmax, nr, n[N], r[N])
+        scale = np.sqrt(np.mean(want ** 2))
+        assert np.max(np.abs(got[N] - want)) / scale <= 100 * TOL_FP32, N
+
+
 def test_edge_correction_rejects_mismatched_or_unsupported_contexts(torch_dev):
     from paper_2105_08722_gb300._lib import NPCF, NPCFError
     edges = np.linspace(5.0, 30.0, 6)
