@@ -52,6 +52,8 @@ def lib():
         L.orc_ylm.argtypes = [c_int, c_double, c_double, c_double, vp, vp]
         L.orc_multiplets.restype = c_int
         L.orc_multiplets.argtypes = [c_int, c_int, c_int, vp]
+        L.orc_multiplets_cap.restype = c_int
+        L.orc_multiplets_cap.argtypes = [c_int, c_int, c_int, c_int, vp]
         L.orc_bins.restype = c_int
         L.orc_bins.argtypes = [c_int, c_int, vp]
         L.orc_coupling.restype = c_double
@@ -91,11 +93,24 @@ def ylm(lmax: int, v) -> np.ndarray:
     return re + 1j * im
 
 
+WIDTH = {3: 2, 4: 3, 5: 5, 6: 7}   # ints per multiplet, intermediates included
+
+
 def multiplets(N: int, lmax: int, allparity: bool = False) -> np.ndarray:
     n = lib().orc_multiplets(N, lmax, int(allparity), None)
-    width = {3: 2, 4: 3, 5: 5}[N]
+    width = WIDTH[N]
     out = np.zeros(n * width, dtype=np.int32)
     lib().orc_multiplets(N, lmax, int(allparity), _p(out))
+    return out.reshape(n, width)
+
+
+def multiplets_cap(N: int, lmax: int, icap: int, allparity: bool = False) -> np.ndarray:
+    """Multiplets whose intermediate l's (l12, l123) are at most icap (2 lmax is their
+    natural range and gives multiplets())."""
+    n = lib().orc_multiplets_cap(N, lmax, icap, int(allparity), None)
+    width = WIDTH[N]
+    out = np.zeros(n * width, dtype=np.int32)
+    lib().orc_multiplets_cap(N, lmax, icap, int(allparity), _p(out))
     return out.reshape(n, width)
 
 

@@ -12,8 +12,13 @@
  *   orc_ylm         Condon-Shortley spherical harmonics (Sec. 2.1) from the
  *                   associated-Legendre three-term recurrence in cos(theta) and
  *                   e^{i m phi} from atan2 -- the textbook route.
- *   orc_coupling    C^L_M: Eq. (N=3-coeff), Eq. (N=4-coeff) and, for N=5, the
- *                   general Eq. (basis-coupling) with its sqrt(2 l12 + 1) factor.
+ *   orc_multiplets  the multiplets L of orders 3 to 6 (Sec. 2.2: triangle conditions
+ *                   of the 3-j symbols, parity-even unless allparity), in the order
+ *                   "last element varied first" (Sec. 5.1); orc_multiplets_cap bounds
+ *                   the intermediate l's.
+ *   orc_coupling    C^L_M: Eq. (N=3-coeff), Eq. (N=4-coeff) and, for N=5 and N=6,
+ *                   the general Eq. (basis-coupling) with its sqrt(2 l12 + 1) (and
+ *                   sqrt(2 l123 + 1)) factors.
  *   orc_alm         a^b_lm(s_i) = sum_j w_j Y_lm(unit(r_j - s_i)) Theta^b,
  *                   Eq. (binned-discrete-alm) without 1/v_b.
  *   orc_npcf        zeta^B_L = sum_i u_i sum_M E(L) C^L_M prod_k a^{b_k}_{l_k m_k},
@@ -103,9 +108,12 @@ void orc_ylm(int lmax, double x, double y, double z, double* re, double* im) {
     free(P);
 }
 
-static int n_ell(int N) { return N == 3 ? 2 : (N == 4 ? 3 : 5); }
+static int n_ell(int N) { return N == 3 ? 2 : (N == 4 ? 3 : (N == 5 ? 5 : 7)); }
 
-int orc_multiplets(int N, int lmax, int allparity, int* out) {
+/* Multiplets in lexicographic order, last element varied first (Sec. 5.1). icap bounds
+ * the intermediate l's (l12, l123); their natural range (triangle conditions with every
+ * principal l <= lmax) is 2 lmax, which orc_multiplets uses. */
+int orc_multiplets_cap(int N, int lmax, int icap, int allparity, int* out) {
     int c = 0;
     if (N == 3) {
         for (int l = 0; l <= lmax; ++l) {
@@ -123,7 +131,7 @@ int orc_multiplets(int N, int lmax, int allparity, int* out) {
     } else if (N == 5) {
         for (int l1 = 0; l1 <= lmax; ++l1)
             for (int l2 = 0; l2 <= lmax; ++l2)
-                for (int l12 = abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                for (int l12 = abs(l1 - l2); l12 <= imin(l1 + l2, icap); ++l12)
                     for (int l3 = 0; l3 <= lmax; ++l3)
                         for (int l4 = abs(l12 - l3); l4 <= imin(l12 + l3, lmax); ++l4) {
                             if (!allparity && ((l1 + l2 + l3 + l4) & 1)) continue;
@@ -133,10 +141,32 @@ int orc_multiplets(int N, int lmax, int allparity, int* out) {
                             }
                             ++c;
                         }
+    } else if (N == 6) {
+        /* L = (l1, l2, (l12), l3, (l123), l4, l5): Eq. (basis-coupling) with two
+         * intermediates, each bounded by the triangle conditions of its 3-j symbols */
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = 0; l2 <= lmax; ++l2)
+                for (int l12 = abs(l1 - l2); l12 <= imin(l1 + l2, icap); ++l12)
+                    for (int l3 = 0; l3 <= lmax; ++l3)
+                        for (int l123 = abs(l12 - l3); l123 <= imin(l12 + l3, icap); ++l123)
+                            for (int l4 = 0; l4 <= lmax; ++l4)
+                                for (int l5 = abs(l123 - l4); l5 <= imin(l123 + l4, lmax); ++l5) {
+                                    if (!allparity && ((l1 + l2 + l3 + l4 + l5) & 1)) continue;
+                                    if (out) {
+                                        int* o = out + 7 * c;
+                                        o[0] = l1; o[1] = l2; o[2] = l12; o[3] = l3;
+                                        o[4] = l123; o[5] = l4; o[6] = l5;
+                                    }
+                                    ++c;
+                                }
     } else {
         return -1;
     }
     return c;
+}
+
+int orc_multiplets(int N, int lmax, int allparity, int* out) {
+    return orc_multiplets_cap(N, lmax, 2 * lmax, allparity, out);
 }
 
 int orc_bins(int N, int nr, int* out) {
@@ -179,6 +209,20 @@ double orc_coupling(int N, const int* L, const int* M) {
         return parity_sign(l1 + l2 + l3 + l4) * sqrt(2.0 * l12 + 1.0) *
                parity_sign(l12 - m12) * v;
     }
+    if (N == 6) {
+        /* Eq. (basis-coupling) at N=6: E sqrt(2 l12 + 1) sqrt(2 l123 + 1)
+         * sum_{m12, m123} (-1)^{l12-m12+l123-m123} (l1 l2 l12; m1 m2 -m12)
+         * (l12 l3 l123; m12 m3 -m123)(l123 l4 l5; m123 m4 m5); the 3-j symbols force
+         * m12 = m1 + m2 and m123 = m12 + m3. */
+        int l1 = L[0], l2 = L[1], l12 = L[2], l3 = L[3], l123 = L[4], l4 = L[5], l5 = L[6];
+        int m12 = M[0] + M[1], m123 = m12 + M[2];
+        if (abs(m12) > l12 || abs(m123) > l123) return 0.0;
+        double v = orc_wigner3j(l1, l2, l12, M[0], M[1], -m12) *
+                   orc_wigner3j(l12, l3, l123, m12, M[2], -m123) *
+                   orc_wigner3j(l123, l4, l5, m123, M[3], M[4]);
+        return parity_sign(l1 + l2 + l3 + l4 + l5) * sqrt(2.0 * l12 + 1.0) * sqrt(2.0 * l123 + 1.0) *
+               parity_sign(l12 - m12 + l123 - m123) * v;
+    }
     return 0.0;
 }
 
@@ -186,7 +230,8 @@ double orc_coupling(int N, const int* L, const int* M) {
 static void principal(int N, const int* L, int* ell) {
     if (N == 3) { ell[0] = L[0]; ell[1] = L[1]; }
     else if (N == 4) { ell[0] = L[0]; ell[1] = L[1]; ell[2] = L[2]; }
-    else { ell[0] = L[0]; ell[1] = L[1]; ell[2] = L[3]; ell[3] = L[4]; }
+    else if (N == 5) { ell[0] = L[0]; ell[1] = L[1]; ell[2] = L[3]; ell[3] = L[4]; }
+    else { ell[0] = L[0]; ell[1] = L[1]; ell[2] = L[3]; ell[3] = L[5]; ell[4] = L[6]; }
 }
 
 /* Terms of one multiplet: every M over the full range with C^L_M != 0. */
@@ -197,7 +242,7 @@ typedef struct {
 } term_list;
 
 static void build_terms(int N, const int* L, term_list* t) {
-    int ell[4];
+    int ell[5];
     int k = N - 1;
     principal(N, L, ell);
     int sumell = 0;
@@ -208,7 +253,7 @@ static void build_terms(int N, const int* L, term_list* t) {
     t->m = (int*)malloc(sizeof(int) * (size_t)(cap * k));
     t->coef = (double*)malloc(sizeof(double) * (size_t)cap);
     t->nterm = 0;
-    int M[4];
+    int M[5];
     for (int idx = 0; idx < cap; ++idx) {
         int r = idx, s = 0;
         for (int i = 0; i < k - 1; ++i) {
@@ -374,7 +419,7 @@ static void build_order(int N, int lmax, int nr, int allparity, order_tab* o) {
     o->terms = (term_list*)malloc(sizeof(term_list) * (size_t)o->nl);
     o->odd = (int*)malloc(sizeof(int) * (size_t)o->nl);
     for (int a = 0; a < o->nl; ++a) {
-        int ell[4], s = 0;
+        int ell[5], s = 0;
         principal(N, o->lam + a * o->nL, ell);
         for (int i = 0; i < N - 1; ++i) s += ell[i];
         o->odd[a] = s & 1;
@@ -393,7 +438,7 @@ static void add_primary(const order_tab* o, int lmax, const double* are, const d
     int nlm = (lmax + 1) * (lmax + 1);
     int k = o->N - 1;
     for (int a = 0; a < o->nl; ++a) {
-        int ell[4];
+        int ell[5];
         principal(o->N, o->lam + a * o->nL, ell);
         const term_list* t = &o->terms[a];
         for (int bb = 0; bb < o->nb; ++bb) {
@@ -422,9 +467,9 @@ static void add_primary(const order_tab* o, int lmax, const double* are, const d
 int orc_npcf(int64_t n, const float* pos, const float* w, const float* wprim, const int64_t* prim,
              int64_t n_prim, int orders_mask, int lmax, int nr, const double* edges, double box,
              int allparity, int nthreads, double* zeta, double* resid, uint64_t* counts) {
-    order_tab ord[3];
+    order_tab ord[4];
     int nord = 0;
-    for (int N = 3; N <= 5; ++N)
+    for (int N = 3; N <= 6; ++N)
         if (orders_mask & (1 << N)) build_order(N, lmax, nr, allparity, &ord[nord++]);
     size_t total = 0;
     for (int o = 0; o < nord; ++o) total += (size_t)ord[o].nl * (size_t)ord[o].nb;
@@ -507,7 +552,7 @@ static double gaunt3(int l1, int l2, int l3, int m1, int m2, int m3) {
 /* C^L_M of one multiplet on a dense grid over (m_1, ..., m_{N-1}). */
 typedef struct {
     int k;
-    int ell[4];
+    int ell[5];
     double* c;
 } dense_coupling;
 
@@ -517,7 +562,7 @@ static void build_dense(int N, const int* L, dense_coupling* d) {
     int size = 1;
     for (int i = 0; i < d->k; ++i) size *= 2 * d->ell[i] + 1;
     d->c = (double*)calloc((size_t)size, sizeof(double));
-    int M[4];
+    int M[5];
     for (int idx = 0; idx < size; ++idx) {
         int r = idx;
         for (int i = d->k - 1; i >= 0; --i) {
@@ -549,7 +594,7 @@ static double gaunt_dense(const dense_coupling* d1, const dense_coupling* d2,
     int s1 = 1, s2 = 1;
     for (int i = 0; i < k; ++i) { s1 *= 2 * d1->ell[i] + 1; s2 *= 2 * d2->ell[i] + 1; }
     double total = 0.0;
-    int M1[4], M2[4], M3[4];
+    int M1[5], M2[5], M3[5];
     for (int p = 0; p < s1; ++p) {
         if (d1->c[p] == 0.0) continue;
         int r = p;

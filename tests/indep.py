@@ -38,7 +38,7 @@ def w9j(*a) -> float:
 
 
 def coupling_sympy(N: int, L, M) -> float:
-    """C^L_M from Eq. (N=3-coeff), Eq. (N=4-coeff) and Eq. (basis-coupling) at N=5."""
+    """C^L_M from Eq. (N=3-coeff), Eq. (N=4-coeff) and Eq. (basis-coupling) at N=5, 6."""
     if N == 3:
         l = L[0]
         if L[0] != L[1] or M[0] != -M[1] or abs(M[0]) > l:
@@ -46,16 +46,31 @@ def coupling_sympy(N: int, L, M) -> float:
         return (-1) ** (l - M[0]) / math.sqrt(2 * l + 1)
     if N == 4:
         return (-1) ** sum(L) * w3j(L[0], L[1], L[2], M[0], M[1], M[2])
-    l1, l2, l12, l3, l4 = L
+    if N == 5:
+        l1, l2, l12, l3, l4 = L
+        m12 = M[0] + M[1]
+        if abs(m12) > l12:
+            return 0.0
+        return ((-1) ** (l1 + l2 + l3 + l4) * math.sqrt(2 * l12 + 1) * (-1) ** (l12 - m12)
+                * w3j(l1, l2, l12, M[0], M[1], -m12) * w3j(l12, l3, l4, m12, M[2], M[3]))
+    # N = 6: two intermediates, the sums over m12 and m123 fixed by the 3-j symbols
+    l1, l2, l12, l3, l123, l4, l5 = L
     m12 = M[0] + M[1]
-    if abs(m12) > l12:
+    m123 = m12 + M[2]
+    if abs(m12) > l12 or abs(m123) > l123:
         return 0.0
-    return ((-1) ** (l1 + l2 + l3 + l4) * math.sqrt(2 * l12 + 1) * (-1) ** (l12 - m12)
-            * w3j(l1, l2, l12, M[0], M[1], -m12) * w3j(l12, l3, l4, m12, M[2], M[3]))
+    return ((-1) ** (l1 + l2 + l3 + l4 + l5) * math.sqrt((2 * l12 + 1) * (2 * l123 + 1))
+            * (-1) ** (l12 - m12 + l123 - m123)
+            * w3j(l1, l2, l12, M[0], M[1], -m12) * w3j(l12, l3, l123, m12, M[2], -m123)
+            * w3j(l123, l4, l5, m123, M[3], M[4]))
 
 
 def principal(N, L):
-    return list(L) if N in (3, 4) else [L[0], L[1], L[3], L[4]]
+    if N in (3, 4):
+        return list(L)
+    if N == 5:
+        return [L[0], L[1], L[3], L[4]]
+    return [L[0], L[1], L[3], L[5], L[6]]
 
 
 def basis_terms(N, L):

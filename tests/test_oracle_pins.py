@@ -40,6 +40,9 @@ def test_printed_dimension_counts():
             assert len(oracle.multiplets(N, int(lmax))) * len(oracle.bins(N, 10)) == val
         elif q == "bins":
             assert len(oracle.bins(N, 10)) == val
+        elif q == "multiplets_icap":
+            lm = int(lmax)
+            assert len(oracle.multiplets_cap(N, lm, lm, bool(int(ap)))) == val, (q, N, lmax)
 
 
 def test_bins_are_strictly_ordered_tuples():
@@ -59,6 +62,17 @@ def test_multiplets_triangle_and_parity():
         l1, l2, l12, l3, l4 = L
         assert abs(l1 - l2) <= l12 <= l1 + l2 and abs(l12 - l3) <= l4 <= l12 + l3
         assert (l1 + l2 + l3 + l4) % 2 == 0
+    lam6 = oracle.multiplets(6, 3, False)
+    for L in lam6:
+        l1, l2, l12, l3, l123, l4, l5 = L
+        assert abs(l1 - l2) <= l12 <= l1 + l2 and abs(l12 - l3) <= l123 <= l12 + l3
+        assert abs(l123 - l4) <= l5 <= l123 + l4 and max(l1, l2, l3, l4, l5) <= 3
+        assert (l1 + l2 + l3 + l4 + l5) % 2 == 0
+    # the natural range of the intermediates is 2 lmax: a cap there changes nothing, and
+    # every capped multiplet is one of the uncapped ones
+    assert np.array_equal(oracle.multiplets_cap(6, 3, 6), lam6)
+    capped = {tuple(x) for x in oracle.multiplets_cap(6, 3, 3)}
+    assert capped <= {tuple(x) for x in lam6} and all(max(L[2], L[4]) <= 3 for L in capped)
 
 
 # ---------------------------------------------------------------- 3-j symbols
@@ -153,8 +167,9 @@ def test_ylm_orthonormal_by_quadrature():
 
 def test_coupling_orthonormality():
     # Eq. (basis-orthogonality) with orthonormal Y's: sum_M C^L_M C^L'_M = delta_{LL'}.
-    # For N=5 this fixes the sqrt(2 l12 + 1) factor of Eq. (basis-coupling).
-    for N, lmax in [(3, 6), (4, 3), (5, 2)]:
+    # For N=5 and 6 this fixes the sqrt(2 l12 + 1) (sqrt(2 l123 + 1)) factors of
+    # Eq. (basis-coupling); for N=6 it also separates multiplets that differ only in l123.
+    for N, lmax in [(3, 6), (4, 3), (5, 2), (6, 1)]:
         lam = oracle.multiplets(N, lmax, True)
         ell = [indep.principal(N, L) for L in lam]
         for a, La in enumerate(lam):
@@ -171,7 +186,7 @@ def test_coupling_orthonormality():
 
 def test_coupling_matches_sympy_definition():
     pytest.importorskip("sympy")
-    for N, lmax in [(3, 4), (4, 3), (5, 2)]:
+    for N, lmax in [(3, 4), (4, 3), (5, 2), (6, 1)]:
         for L in oracle.multiplets(N, lmax, True):
             for M, c in indep.basis_terms(N, tuple(int(x) for x in L)):
                 assert oracle.coupling(N, L, M) == pytest.approx(c, abs=1e-14)
@@ -179,7 +194,7 @@ def test_coupling_matches_sympy_definition():
 
 def test_coupling_M_inversion():
     # Eq. (basis-coupling-M-inversion): C^L_{-M} = E(L) C^L_M
-    for N, lmax in [(4, 4), (5, 3)]:
+    for N, lmax in [(4, 4), (5, 3), (6, 1)]:
         for L in oracle.multiplets(N, lmax, True):
             ell = indep.principal(N, L)
             E = (-1) ** sum(ell)
@@ -188,6 +203,21 @@ def test_coupling_M_inversion():
                     continue
                 assert oracle.coupling(N, L, [-m for m in M]) == pytest.approx(
                     E * oracle.coupling(N, L, M), abs=1e-15)
+
+
+def test_n5_coupling_is_n6_with_l5_zero():
+    # Eq. (basis-coupling): with l5 = 0 the last 3-j symbol forces l123 = l4, m123 = -m4 and
+    # equals (-1)^{l4+m4} / sqrt(2 l4 + 1), which cancels the sqrt(2 l123 + 1) factor and
+    # the (-1)^{l123 - m123} phase: the N=6 coefficient is the N=5 one
+    for L in oracle.multiplets(5, 2, True):
+        l1, l2, l12, l3, l4 = (int(x) for x in L)
+        L6 = [l1, l2, l12, l3, l4, l4, 0]
+        for M in itertools.product(*[range(-l, l + 1) for l in (l1, l2, l3)]):
+            m4 = -sum(M)
+            if abs(m4) > l4:
+                continue
+            assert oracle.coupling(6, L6, list(M) + [m4, 0]) == pytest.approx(
+                oracle.coupling(5, L, list(M) + [m4]), abs=1e-14)
 
 
 def test_n3_coupling_is_n4_with_l3_zero():
@@ -371,6 +401,25 @@ def test_npcf5_brute_force_tuples():
     assert np.max(np.abs(z - want)) <= 1e-12 * scale
 
 
+def test_npcf6_brute_force_tuples():
+    # Sec. 5.2 brute force for the 6PCF: every 5-tuple of secondaries in distinct shells,
+    # P_L from scipy Y's and sympy 3-j symbols (all parities, lmax 1)
+    pytest.importorskip("sympy")
+    pos, w = _small_catalog(36, 30.0, 19)
+    edges = np.array([2.0, 5.0, 8.0, 11.0, 14.0, 17.0])
+    lmax = 1
+    lam = oracle.multiplets(6, lmax, True)
+    bins = oracle.bins(6, 5)
+    z, _ = oracle.npcf(pos, w, (6,), lmax, edges, 0.0, allparity=True)
+    z = z.reshape(len(lam), len(bins))
+    bf = indep.brute_force_npcf(pos, w, 6, lmax, edges, lam, bins)
+    odd = np.array([(L[0] + L[1] + L[3] + L[5] + L[6]) % 2 for L in lam], bool)
+    want = np.where(odd[:, None], bf.imag, bf.real)
+    scale = np.sqrt(np.mean(want ** 2))
+    assert scale > 0
+    assert np.max(np.abs(z - want)) <= 1e-12 * scale
+
+
 def _pair_weights(pos, w, edges, box):
     """W_b(i) = sum of secondary weights of i in shell b (a weighted pair count)."""
     nr = len(edges) - 1
@@ -388,9 +437,9 @@ def test_l0_multiplets_are_pair_count_products():
     edges = np.linspace(4.0, 20.0, 6)
     box = 60.0
     W = _pair_weights(pos, w, edges, box)
-    z, _ = oracle.npcf(pos, w, (3, 4, 5), 2, edges, box)
-    parts = oracle.split_orders(z, (3, 4, 5), 2, 5)
-    for N in (3, 4, 5):
+    z, _ = oracle.npcf(pos, w, (3, 4, 5, 6), 2, edges, box)
+    parts = oracle.split_orders(z, (3, 4, 5, 6), 2, 5)
+    for N in (3, 4, 5, 6):
         want = np.array([np.sum(w.astype(np.float64) * np.prod(W[:, list(B)], axis=1))
                          for B in oracle.bins(N, 5)]) * FOURPI ** (-(N - 1) / 2)
         assert np.allclose(parts[N][0], want, rtol=1e-12, atol=0)
@@ -442,10 +491,11 @@ def test_rotation_invariance_non_periodic():
     from scipy.spatial.transform import Rotation
     pos, w = _small_catalog(150, 40.0, 15)
     pos = pos - 20.0
-    edges = _edges_avoiding(pos, 4.0, 16.0, 4)
+    edges4 = _edges_avoiding(pos, 4.0, 16.0, 4)
+    edges5 = _edges_avoiding(pos, 4.0, 18.0, 5)   # the 6PCF needs five shells
     R = Rotation.random(random_state=16).as_matrix()
     rpos = (pos.astype(np.float64) @ R.T).astype(np.float32)
-    for orders, lmax in [((3, 4), 3), ((5,), 2)]:
+    for orders, lmax, edges in [((3, 4), 3, edges4), ((5,), 2, edges4), ((6,), 1, edges5)]:
         z, c = oracle.npcf(pos, w, orders, lmax, edges, 0.0, allparity=True)
         zr, cr = oracle.npcf(rpos, w, orders, lmax, edges, 0.0, allparity=True)
         assert np.array_equal(c, cr)
