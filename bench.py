@@ -7,7 +7,7 @@ npcf_accumulate of the whole catalog: cell list, pair kernel (a_lm of every prim
 3PCF and 4PCF contraction, FP64 reduction. Metric: primaries per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
-    python bench.py --workload c5 ...      # 64 catalogs in one batch (CUDA graph)
+    python bench.py --workload batch64 ...  # 64 catalogs in one batch (CUDA graph)
     python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
 """
 from __future__ import annotations
@@ -160,12 +160,12 @@ def aggregate_rate(units_per_rank, world, ms):
     return units_per_rank * world / (ms * 1e-3)
 
 
-def c2_workload(n_points):
+def lognormal_workload(n_points):
     """The 200k log-normal workload, or the same density and spectrum at n_points (box
     scaled by (n/200k)^(1/3); a smaller case for profiling)."""
     from paper_2105_08722_gb300 import catalogs
     if not n_points or n_points == 200_000:
-        return catalogs.c2_lognormal_4pcf()
+        return catalogs.lognormal200k_4pcf()
     box = 1000.0 * (n_points / 200_000) ** (1.0 / 3.0)
     pos = catalogs.lognormal_box(n_points, box, 256, seed=1002)
     return catalogs.Workload("lognormal_%dk_L%d_4pcf3pcf_lmax5_nr10_20-160" % (n_points // 1000, round(box)), pos,
@@ -177,7 +177,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2105_08722_gb300 import catalogs
-    wl = c2_workload(args.n)
+    wl = lognormal_workload(args.n)
     sample_n = args.ref_sample
     times = []
     for step in range(args.warmup + args.steps):
@@ -215,7 +215,7 @@ def run_gpu(args):
     build()
     from paper_2105_08722_gb300._lib import NPCF, FP32, SPLIT_BF16
 
-    wl = c2_workload(args.n)
+    wl = lognormal_workload(args.n)
     prec = SPLIT_BF16 if args.precision == "bf16" else FP32
     est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, prec)
     pos = torch.from_numpy(wl.pos).to(dev)
@@ -355,7 +355,7 @@ def run_gpu_batch(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    cats, edges = catalogs.c5_batch()
+    cats, edges = catalogs.batch64_lognormal()
     sizes = np.array([len(c) for c in cats])
     off = np.concatenate([[0], np.cumsum(sizes)])
     n = int(off[-1])
@@ -479,7 +479,7 @@ def _timed_steps(args, step, dev):
     return float(np.mean(ms)), clocks.stop()
 
 
-def run_gpu_c1(args):
+def run_gpu_uniform4k(args):
     """3PCF: 4,096 uniform points in a periodic 250 Mpc/h cube, 10 shells 0-50, lmax 5."""
     import torch
 
@@ -489,7 +489,7 @@ def run_gpu_c1(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    wl = catalogs.c1_uniform_3pcf()
+    wl = catalogs.uniform4k_3pcf()
     est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, FP32)
     pos, w = torch.from_numpy(wl.pos).to(dev), torch.from_numpy(wl.w).to(dev)
     ms, clk = _timed_steps(args, lambda: est.accumulate(pos, w), dev)
@@ -554,7 +554,7 @@ def run_gpu_paper(args, order):
     return 0
 
 
-def run_gpu_c3(args):
+def run_gpu_survey(args):
     """Survey D - R: 400k log-normal data + 1.6M randoms (weights +1, -N_D/N_R) inside a
     60 degree cap, 600-1400 Mpc/h, non-periodic; the 1.6M randoms-only run; the GPU edge
     correction. One step = both accumulate calls and the edge-correction solve."""
@@ -566,7 +566,7 @@ def run_gpu_c3(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    dr, rr = catalogs.c3_survey()
+    dr, rr = catalogs.survey_dmr_and_randoms()
     prec = FP32 if args.precision == "fp32" else SPLIT_BF16
     nest = NPCF(dr.lmax, dr.orders, dr.edges, 0.0, prec)
     rest = NPCF(rr.lmax, rr.orders, rr.edges, 0.0, prec)
@@ -603,7 +603,7 @@ def run_gpu_c3(args):
     return 0
 
 
-def run_gpu_c4(args):
+def run_gpu_5pcf(args):
     """5PCF: 100k log-normal points, periodic 1000 Mpc/h, 8 shells 20-160, lmax 4 (all
     5PCF multiplets with l12 <= 2 lmax). One step = one npcf_accumulate."""
     import torch
@@ -614,7 +614,7 @@ def run_gpu_c4(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    wl = catalogs.c4_lognormal_5pcf()
+    wl = catalogs.lognormal100k_5pcf()
     est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, FP32)
     pos = torch.from_numpy(wl.pos).to(dev)
     w = torch.from_numpy(wl.w).to(dev)
@@ -638,7 +638,7 @@ def run_gpu_c4(args):
     clk = clocks.stop()
     st = np.mean(np.array(st, dtype=np.float64), axis=0)
     t = float(np.mean(ms))
-    # useful 5PCF flop per primary (SURVEY figures: P12 + P34 builds and the final products)
+    # algorithmic 5PCF flop per primary: the P12 and P34 builds and the final products
     alg = wl.n * (543_200 * 2 + 1_110_200)
     fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = alg / (st[2] * 1e-3) / 1e12
@@ -670,10 +670,13 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16"],
                     help="contraction arithmetic (default fp32; bf16 for the batch workload)")
     ap.add_argument("--n", type=int, default=0,
-                    help="points of the c2 workload at the same density (default 200,000)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "paper4", "paper5"],
-                    help="c1: 4k uniform, 3PCF; c2: one 200k log-normal catalog (4PCF + 3PCF); c3: survey "
-                         "D-R + R with edge correction; c4: 100k, 5PCF; c5: 64 catalogs in one batch; "
+                    help="points of the 200k log-normal workload at the same density (default 200,000)")
+    ap.add_argument("--workload", default="lognormal200k",
+                    choices=["uniform4k", "lognormal200k", "survey", "lognormal100k-5pcf", "batch64", "paper4",
+                             "paper5"],
+                    help="uniform4k: 4,096 uniform points, 3PCF; lognormal200k: one 200k log-normal catalog "
+                         "(4PCF + 3PCF); survey: 400k data + 1.6M randoms (D-R and R runs) with edge correction; "
+                         "lognormal100k-5pcf: 100k points, 5PCF; batch64: 64 catalogs in one batch; "
                          "paper4 / paper5: the paper's timing catalog (5e4 uniform, L 1500), 4PCF / 5PCF")
     ap.add_argument("--cpu-sample", type=int, default=1500)
     ap.add_argument("--ref-sample", type=int, default=400)
@@ -684,19 +687,19 @@ def main():
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.precision is None:
-        args.precision = "bf16" if args.workload == "c5" else "fp32"
+        args.precision = "bf16" if args.workload == "batch64" else "fp32"
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "c5":
+    if args.workload == "batch64":
         return run_gpu_batch(args)
-    if args.workload == "c4":
-        return run_gpu_c4(args)
-    if args.workload == "c1":
-        return run_gpu_c1(args)
+    if args.workload == "lognormal100k-5pcf":
+        return run_gpu_5pcf(args)
+    if args.workload == "uniform4k":
+        return run_gpu_uniform4k(args)
     if args.workload in ("paper4", "paper5"):
         return run_gpu_paper(args, 4 if args.workload == "paper4" else 5)
-    if args.workload == "c3":
-        return run_gpu_c3(args)
+    if args.workload == "survey":
+        return run_gpu_survey(args)
     return run_gpu(args)
 
 

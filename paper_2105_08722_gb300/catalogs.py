@@ -157,7 +157,7 @@ def linear_edges(rmin: float, rmax: float, nr: int) -> np.ndarray:
     return np.linspace(rmin, rmax, nr + 1)
 
 
-def c1_uniform_3pcf(n: int = 4096) -> Workload:
+def uniform4k_3pcf(n: int = 4096) -> Workload:
     """4,096 uniform points, periodic 250 Mpc/h cube, 10 shells 0-50, lmax 5, 3PCF."""
     pos = uniform_box(n, 250.0, seed=1001)
     return Workload("3pcf_uniform_4096_L250", pos, np.ones(n, np.float32),
@@ -172,21 +172,21 @@ def paper_uniform_1500(n: int = 50_000, lmax: int = 5, orders=(3, 4)) -> Workloa
                     linear_edges(0.0, 200.0, 10), lmax, tuple(orders), 1500.0)
 
 
-def c2_lognormal_4pcf(n: int = 200_000, mesh: int = 256) -> Workload:
+def lognormal200k_4pcf(n: int = 200_000, mesh: int = 256) -> Workload:
     """200k log-normal points, periodic 1000 Mpc/h cube, 10 shells 20-160, lmax 5, 3+4PCF."""
     pos = lognormal_box(n, 1000.0, mesh, seed=1002)
     return Workload("4pcf3pcf_lognormal_200k_L1000", pos, np.ones(n, np.float32),
                     linear_edges(20.0, 160.0, 10), 5, (3, 4), 1000.0)
 
 
-def c4_lognormal_5pcf(n: int = 100_000, mesh: int = 256) -> Workload:
+def lognormal100k_5pcf(n: int = 100_000, mesh: int = 256) -> Workload:
     """100k log-normal points, periodic 1000 Mpc/h cube, 8 shells 20-160, lmax 4, 5PCF."""
     pos = lognormal_box(n, 1000.0, mesh, seed=1004)
     return Workload("5pcf_lognormal_100k_L1000", pos, np.ones(n, np.float32),
                     linear_edges(20.0, 160.0, 8), 4, (5,), 1000.0)
 
 
-def c3_survey(n_data: int = 400_000, n_rand: int = 1_600_000, mesh: int = 256):
+def survey_dmr_and_randoms(n_data: int = 400_000, n_rand: int = 1_600_000, mesh: int = 256):
     """D-R catalog (data +1, randoms -N_D/N_R) and the R-only catalog (randoms +N_D/N_R)."""
     d = survey_data(n_data, seed=1003, mesh=mesh)
     r = survey_randoms(n_rand, seed=2003)
@@ -201,7 +201,7 @@ def c3_survey(n_data: int = 400_000, n_rand: int = 1_600_000, mesh: int = 256):
     return dr, rr
 
 
-def c3_subset(dr: "Workload", rr: "Workload", n_data: int = 4000, n_rand: int = 16000,
+def survey_subset(dr: "Workload", rr: "Workload", n_data: int = 4000, n_rand: int = 16000,
               seed: int = 3003):
     """Seeded subset of the survey catalogs (n_data data points, n_rand randoms), with the
     randoms re-weighted to -n_data/n_rand (D-R) and +n_data/n_rand (R only)."""
@@ -219,14 +219,14 @@ def c3_subset(dr: "Workload", rr: "Workload", n_data: int = 4000, n_rand: int = 
     return sub_dr, sub_rr
 
 
-def c5_batch_sizes(ncat: int = 64) -> np.ndarray:
+def batch64_sizes(ncat: int = 64) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(5000))
     return np.round(np.exp(rng.uniform(math.log(2e4), math.log(3e5), size=ncat))).astype(np.int64)
 
 
-def c5_batch(ncat: int = 64, mesh: int = 128, sizes: Optional[np.ndarray] = None):
+def batch64_lognormal(ncat: int = 64, mesh: int = 128, sizes: Optional[np.ndarray] = None):
     """64 log-normal periodic catalogs with sizes log-uniform in [2e4, 3e5]."""
     if sizes is None:
-        sizes = c5_batch_sizes(ncat)
+        sizes = batch64_sizes(ncat)
     cats = [lognormal_box(int(s), 1000.0, mesh, seed=5000 + k) for k, s in enumerate(sizes)]
     return cats, linear_edges(20.0, 160.0, 10)

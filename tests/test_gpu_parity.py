@@ -141,7 +141,7 @@ def test_alm_of_sampled_primaries(torch_dev, lmax):
 # ------------------------------------------------------------------ multiplets
 
 def test_3pcf_uniform_4096_box250_full(torch_dev):
-    wl = catalogs.c1_uniform_3pcf()
+    wl = catalogs.uniform4k_3pcf()
     _, got, counts = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box)
     want, wcounts = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box)
     assert np.array_equal(counts, wcounts)
@@ -311,14 +311,14 @@ def test_periodic_normalisation(torch_dev):
 # ------------------------------------------------------------------ full-size workload
 
 @pytest.fixture(scope="module")
-def c2_workload():
-    return catalogs.c2_lognormal_4pcf()
+def lognormal_workload():
+    return catalogs.lognormal200k_4pcf()
 
 
-def test_lognormal_200k_4pcf_sampled_primaries(torch_dev, c2_workload):
+def test_lognormal_200k_4pcf_sampled_primaries(torch_dev, lognormal_workload):
     """The 200k log-normal 4PCF+3PCF workload at full size, in the bench's launch
     configuration; the oracle evaluates a seeded sample of primaries one by one."""
-    wl = c2_workload
+    wl = lognormal_workload
     rng = np.random.default_rng(2024)
     sample = np.sort(rng.choice(wl.n, 48, replace=False))
     wp = np.zeros(wl.n, np.float32)
@@ -331,8 +331,8 @@ def test_lognormal_200k_4pcf_sampled_primaries(torch_dev, c2_workload):
     assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
 
 
-def test_lognormal_200k_full_run_is_sum_of_complementary_samples(torch_dev, c2_workload):
-    wl = c2_workload
+def test_lognormal_200k_full_run_is_sum_of_complementary_samples(torch_dev, lognormal_workload):
+    wl = lognormal_workload
     _, full, cfull = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box)
     mask = (np.arange(wl.n) % 3 == 0).astype(np.float32)
     _, a, ca = gpu_run(torch_dev, wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, wprim=wl.w * mask)
@@ -375,8 +375,8 @@ def test_split_bf16_and_fp32_paths_agree_on_ragged_chunks(torch_dev):
         assert_orders_close(a, b, (4,), 3, 8, tol=TOL_BF16)
 
 
-def test_lognormal_200k_split_bf16_sampled_primaries(torch_dev, c2_workload):
-    wl = c2_workload
+def test_lognormal_200k_split_bf16_sampled_primaries(torch_dev, lognormal_workload):
+    wl = lognormal_workload
     rng = np.random.default_rng(2025)
     sample = np.sort(rng.choice(wl.n, 48, replace=False))
     wp = np.zeros(wl.n, np.float32)
@@ -433,7 +433,7 @@ def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev):
 
 
 def test_lognormal_100k_5pcf_lmax4_sampled_primaries(torch_dev):
-    wl = catalogs.c4_lognormal_5pcf()
+    wl = catalogs.lognormal100k_5pcf()
     rng = np.random.default_rng(2026)
     sample = np.sort(rng.choice(wl.n, 16, replace=False))
     wp = np.zeros(wl.n, np.float32)
@@ -597,13 +597,13 @@ def test_edge_correction_rejects_mismatched_or_unsupported_contexts(torch_dev):
 
 @pytest.fixture(scope="module")
 def survey():
-    return catalogs.c3_survey()
+    return catalogs.survey_dmr_and_randoms()
 
 
 def test_survey_subset_dmr_multiplets_and_edge_correction(torch_dev, survey):
     # the seeded 20k subset (4k data, 16k randoms) of the 400k + 1.6M survey catalogs:
     # raw D - R and R multiplets, then the edge-corrected ones, against the oracle
-    dr, rr = catalogs.c3_subset(*survey)
+    dr, rr = catalogs.survey_subset(*survey)
     nr = len(dr.edges) - 1
     nctx, nraw, ncnt = gpu_run(torch_dev, dr.pos, dr.w, dr.orders, dr.lmax, dr.edges, 0.0)
     rctx, rraw, _ = gpu_run(torch_dev, rr.pos, rr.w, rr.orders, rr.lmax, rr.edges, 0.0)
@@ -736,7 +736,7 @@ def test_batched_mocks_full_size_sampled_primaries(torch_dev):
     # compared with the oracle; every other catalog has no primary and stays zero
     torch, dev = torch_dev
     from paper_2105_08722_gb300._lib import NPCF
-    cats, edges = catalogs.c5_batch()
+    cats, edges = catalogs.batch64_lognormal()
     sizes = np.array([len(c) for c in cats])
     off = np.concatenate([[0], np.cumsum(sizes)])
     rng = np.random.default_rng(5005)
