@@ -251,6 +251,21 @@ npcf_status npcf_truncate(const npcf_ctx* ctx, const double* in, size_t in_len, 
  * {l1, l2, l12, l3, l4}); *out receives the value. */
 npcf_status npcf_gaunt(int N, const int* L1, const int* L2, const int* L3, double* out);
 
+/* Multiplets L of order N = 3..6 (Sec. 2.2: the triangle conditions of the 3-j symbols of
+ * Eq. basis-coupling, principal l's <= lmax, intermediates over their natural range; the
+ * parity-even ones, sum of principal l's even, unless allparity), in the output order of
+ * npcf_finalize ("last element varied first", Sec. 5.1). Layout per multiplet: {l, l},
+ * {l1, l2, l3}, {l1, l2, l12, l3, l4}, {l1, l2, l12, l3, l123, l4, l5}. *count receives
+ * their number; out (nullable) receives count x (2, 3, 5, 7) ints. Host-only. The 6PCF
+ * has no GPU contraction yet: npcf_create takes orders 3 to 5. lmax in [0, 10]. */
+npcf_status npcf_multiplets(int N, int lmax, int allparity, int* count, int* out);
+
+/* Coupling coefficient C^L_M of Eq. basis-coupling (Eq. N=3-coeff and N=4-coeff for N = 3,
+ * 4; one intermediate for N = 5, two for N = 6); L laid out as npcf_multiplets gives it,
+ * M = {m_1, ..., m_{N-1}} (host ints). *out receives the value (0 where the 3-j symbols
+ * vanish). Host-only; NPCF_EINVAL for N outside 3..6 or an l outside [0, 40]. */
+npcf_status npcf_coupling(int N, const int* L, const int* M, double* out);
+
 /* Message of the last failed call on ctx; with ctx == NULL, of the last failed
  * npcf_create or npcf_pair_counts_noalloc on this thread. */
 const char* npcf_last_error(const npcf_ctx* ctx);

@@ -44,6 +44,8 @@ SIGNATURES = {
     "npcf_autotune": (_i, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "npcf_gaunt": (_i, [_i, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "npcf_truncate": (_i, [_vp, _vp, _sz, _i, _vp, ctypes.POINTER(_sz)]),
+    "npcf_multiplets": (_i, [_i, _i, _i, ctypes.POINTER(_i), _vp]),
+    "npcf_coupling": (_i, [_i, _vp, _vp, ctypes.POINTER(_d)]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
 }
@@ -87,6 +89,30 @@ def gaunt(N: int, L1, L2, L3) -> float:
     st = lib.npcf_gaunt(int(N), a.ctypes.data, b.ctypes.data, c.ctypes.data, ctypes.byref(out))
     if st != NPCF_OK:
         raise NPCFError(st, "npcf_gaunt: bad arguments")
+    return out.value
+
+
+def multiplets(N: int, lmax: int, allparity: bool = False) -> np.ndarray:
+    """Multiplets of order N (npcf_multiplets), one row each."""
+    lib = load()
+    n = _i()
+    st = lib.npcf_multiplets(int(N), int(lmax), int(bool(allparity)), ctypes.byref(n), None)
+    if st != NPCF_OK:
+        raise NPCFError(st, "npcf_multiplets: bad arguments")
+    width = {3: 2, 4: 3, 5: 5, 6: 7}[int(N)]
+    out = np.zeros(n.value * width, dtype=np.int32)
+    lib.npcf_multiplets(int(N), int(lmax), int(bool(allparity)), ctypes.byref(n), out.ctypes.data)
+    return out.reshape(n.value, width)
+
+
+def coupling(N: int, L, M) -> float:
+    """C^L_M of Eq. basis-coupling (npcf_coupling)."""
+    La = np.ascontiguousarray(L, dtype=np.int32)
+    Ma = np.ascontiguousarray(M, dtype=np.int32)
+    out = _d()
+    st = load().npcf_coupling(int(N), La.ctypes.data, Ma.ctypes.data, ctypes.byref(out))
+    if st != NPCF_OK:
+        raise NPCFError(st, "npcf_coupling: bad arguments")
     return out.value
 
 

@@ -1297,6 +1297,25 @@ npcf_status npcf_gaunt(int N, const int* L1, const int* L2, const int* L3, doubl
     return NPCF_OK;
 }
 
+npcf_status npcf_multiplets(int N, int lmax, int allparity, int* count, int* out) {
+    if (N < 3 || N > 6 || lmax < 0 || lmax > kMaxL || !count) return NPCF_EINVAL;
+    const OrderTable o = make_order(N, lmax, N - 1, allparity != 0);
+    *count = o.n_lambda();
+    if (out) std::memcpy(out, o.lam.data(), o.lam.size() * sizeof(int));
+    return NPCF_OK;
+}
+
+npcf_status npcf_coupling(int N, const int* L, const int* M, double* out) {
+    if (N < 3 || N > 6 || !L || !M || !out) return NPCF_EINVAL;
+    const int width = N == 3 ? 2 : (N == 4 ? 3 : (N == 5 ? 5 : 7));
+    for (int i = 0; i < width; ++i)
+        if (L[i] < 0 || L[i] > 4 * kMaxL) return NPCF_EINVAL;
+    for (int i = 0; i < N - 1; ++i)
+        if (M[i] < -4 * kMaxL || M[i] > 4 * kMaxL) return NPCF_EINVAL;
+    *out = coupling(N, L, M);
+    return NPCF_OK;
+}
+
 npcf_status npcf_edge_correct(npcf_ctx* nctx, npcf_ctx* rctx, double* out) {
     if (check_ctx(nctx) != NPCF_OK || check_ctx(rctx) != NPCF_OK) return NPCF_EINVAL;
     npcf_ctx* ctx = nctx;   // CUDA failures are reported on the data context

@@ -121,14 +121,42 @@ double generalized_gaunt(int N, const int* L1, const int* L2, const int* L3) {
 
 bool OrderTable::odd(int a) const {
     const int* L = &lam[(size_t)a * width];
-    int s = (N == 5) ? L[0] + L[1] + L[3] + L[4] : (N == 4 ? L[0] + L[1] + L[2] : 2 * L[0]);
+    int s = (N == 6)   ? L[0] + L[1] + L[3] + L[5] + L[6]
+            : (N == 5) ? L[0] + L[1] + L[3] + L[4]
+                       : (N == 4 ? L[0] + L[1] + L[2] : 2 * L[0]);
     return (s & 1) != 0;
+}
+
+double coupling(int N, const int* L, const int* M) {
+    if (N == 3) {
+        // Eq. (N=3-coeff): (-1)^{l - m} / sqrt(2 l + 1) for l1 = l2 = l, m2 = -m1
+        if (L[0] != L[1] || M[0] + M[1] != 0 || std::abs(M[0]) > L[0]) return 0.0;
+        return neg1pow(L[0] - M[0]) / std::sqrt(2.0 * L[0] + 1.0);
+    }
+    if (N == 4) return neg1pow(L[0] + L[1] + L[2]) * wigner3j(L[0], L[1], L[2], M[0], M[1], M[2]);
+    if (N == 5) {
+        // Eq. (basis-coupling) with one intermediate: m12 = m1 + m2 by the first 3-j symbol
+        const int m12 = M[0] + M[1];
+        if (std::abs(m12) > L[2]) return 0.0;
+        return neg1pow(L[0] + L[1] + L[3] + L[4]) * std::sqrt(2.0 * L[2] + 1.0) * neg1pow(L[2] - m12) *
+               wigner3j(L[0], L[1], L[2], M[0], M[1], -m12) * wigner3j(L[2], L[3], L[4], m12, M[2], M[3]);
+    }
+    if (N == 6) {
+        // two intermediates: L = (l1, l2, (l12), l3, (l123), l4, l5), m12 = m1 + m2 and
+        // m123 = m12 + m3 by the 3-j symbols
+        const int m12 = M[0] + M[1], m123 = m12 + M[2];
+        if (std::abs(m12) > L[2] || std::abs(m123) > L[4]) return 0.0;
+        return neg1pow(L[0] + L[1] + L[3] + L[5] + L[6]) * std::sqrt((2.0 * L[2] + 1.0) * (2.0 * L[4] + 1.0)) *
+               neg1pow(L[2] - m12 + L[4] - m123) * wigner3j(L[0], L[1], L[2], M[0], M[1], -m12) *
+               wigner3j(L[2], L[3], L[4], m12, M[2], -m123) * wigner3j(L[4], L[5], L[6], m123, M[3], M[4]);
+    }
+    return 0.0;
 }
 
 OrderTable make_order(int N, int lmax, int nr, bool allparity) {
     OrderTable o;
     o.N = N;
-    o.width = (N == 3) ? 2 : (N == 4 ? 3 : 5);
+    o.width = (N == 3) ? 2 : (N == 4 ? 3 : (N == 5 ? 5 : 7));
     if (N == 3) {
         for (int l = 0; l <= lmax; ++l) { o.lam.push_back(l); o.lam.push_back(l); }
     } else if (N == 4) {
@@ -151,6 +179,20 @@ OrderTable make_order(int N, int lmax, int nr, bool allparity) {
                             o.lam.insert(o.lam.end(), {l1, l2, l12, l3, l4});
                         }
                     }
+    } else if (N == 6) {
+        // intermediates l12 and l123 over their triangle ranges (at most 2 lmax)
+        for (int l1 = 0; l1 <= lmax; ++l1)
+            for (int l2 = 0; l2 <= lmax; ++l2)
+                for (int l12 = std::abs(l1 - l2); l12 <= l1 + l2; ++l12)
+                    for (int l3 = 0; l3 <= lmax; ++l3)
+                        for (int l123 = std::abs(l12 - l3); l123 <= std::min(l12 + l3, 2 * lmax); ++l123)
+                            for (int l4 = 0; l4 <= lmax; ++l4) {
+                                const int top = std::min(l123 + l4, lmax);
+                                for (int l5 = std::abs(l123 - l4); l5 <= top; ++l5) {
+                                    if (!allparity && ((l1 + l2 + l3 + l4 + l5) & 1)) continue;
+                                    o.lam.insert(o.lam.end(), {l1, l2, l12, l3, l123, l4, l5});
+                                }
+                            }
     }
     // strictly increasing bin tuples, lexicographic, last index fastest
     int k = N - 1;

@@ -24,6 +24,11 @@ double wigner9j(int j1, int j2, int j3, int j4, int j5, int j6, int j7, int j8, 
 // OrderTable: (l, l), (l1, l2, l3), (l1, l2, l12, l3, l4)); 0 for other N.
 double generalized_gaunt(int N, const int* L1, const int* L2, const int* L3);
 
+// Coupling coefficient C^L_M of Eq. (basis-coupling) (Eq. (N=3-coeff) and Eq. (N=4-coeff)
+// for N = 3, 4; one intermediate for N = 5, two for N = 6), multiplets laid out as in
+// OrderTable, M = (m_1, ..., m_{N-1}); 0 where the 3-j symbols vanish.
+double coupling(int N, const int* L, const int* M);
+
 // Number of complex slots per shell in the a_lm layout: l <= lmax, 0 <= m <= l.
 inline int nlm(int lmax) { return (lmax + 1) * (lmax + 2) / 2; }
 inline int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
@@ -31,7 +36,7 @@ inline int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
 // One order N of the statistic: its multiplets L and bin tuples B.
 struct OrderTable {
     int N = 0;
-    int width = 0;                  // ints per multiplet: 2 (N=3), 3 (N=4), 5 (N=5)
+    int width = 0;                  // ints per multiplet: 2 (N=3), 3 (N=4), 5 (N=5), 7 (N=6)
     std::vector<int> lam;           // n_lambda x width
     std::vector<int> bins;          // n_bins x (N-1)
     int n_lambda() const { return width ? (int)lam.size() / width : 0; }

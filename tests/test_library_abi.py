@@ -96,3 +96,37 @@ def test_gaunt_rejects_bad_order(lib):
     from paper_2105_08722_gb300 import _lib
     with pytest.raises(_lib.NPCFError):
         _lib.gaunt(6, [0] * 5, [0] * 5, [0] * 5)
+
+
+@pytest.mark.parametrize("N,lmax", [(3, 4), (4, 3), (5, 2), (6, 1), (6, 2)])
+def test_library_multiplets_and_couplings_match_the_oracle(lib, N, lmax):
+    # the library's host tables (npcf_multiplets, npcf_coupling) against the oracle's own
+    # enumeration and Eq. (basis-coupling), written separately; the 6PCF tables are the
+    # first piece of its GPU path
+    import itertools
+    import oracle
+    from paper_2105_08722_gb300 import _lib
+    oracle.build()
+    for ap in (False, True):
+        got = _lib.multiplets(N, lmax, ap)
+        assert np.array_equal(got, oracle.multiplets(N, lmax, ap)), (N, lmax, ap)
+    principal = {3: [0, 1], 4: [0, 1, 2], 5: [0, 1, 3, 4], 6: [0, 1, 3, 5, 6]}[N]
+    for L in _lib.multiplets(N, lmax, True):
+        ell = [int(L[i]) for i in principal]
+        for M in itertools.product(*[range(-l, l + 1) for l in ell[:-1]]):
+            M = list(M) + [-sum(M)]
+            if abs(M[-1]) > ell[-1]:
+                continue
+            assert _lib.coupling(N, L, M) == pytest.approx(oracle.coupling(N, L, M), abs=1e-14), (L, M)
+
+
+def test_multiplets_and_coupling_reject_bad_arguments(lib):
+    from paper_2105_08722_gb300 import _lib
+    with pytest.raises(_lib.NPCFError):
+        _lib.multiplets(7, 2)
+    with pytest.raises(_lib.NPCFError):
+        _lib.multiplets(4, 11)
+    with pytest.raises(_lib.NPCFError):
+        _lib.coupling(2, [0, 0], [0, 0])
+    with pytest.raises(_lib.NPCFError):
+        _lib.coupling(4, [1, -1, 0], [0, 0, 0])
