@@ -24,9 +24,11 @@
  *      d < -L/2 -> d + L; r2 = (dx*dx + dy*dy) + dz*dz; e2[k] = float(edge_k^2);
  *      pair accepted iff r2 > 0 and e2[0] <= r2 < e2[nr]; shell b with
  *      e2[b] <= r2 < e2[b+1]. Bins are distinct and ordered, b1 < b2 < ... (Sec. 3.2.1).
- *  - Multiplets L: l1 outer, then l2, [l12], l3, [l4], last index fastest;
+ *  - Multiplets L: l1 outer, then l2, [l12], l3, [l123], l4, [l5], last index fastest;
  *    N=3: (l, l), l = 0..lmax; N=4: |l1-l2| <= l3 <= min(l1+l2, lmax);
- *    N=5: |l1-l2| <= l12 <= l1+l2, |l12-l3| <= l4 <= min(l12+l3, lmax).
+ *    N=5: |l1-l2| <= l12 <= l1+l2, |l12-l3| <= l4 <= min(l12+l3, lmax);
+ *    N=6 (host tables only, npcf_multiplets): |l1-l2| <= l12 <= l1+l2,
+ *    |l12-l3| <= l123 <= l12+l3, |l123-l4| <= l5 <= min(l123+l4, lmax).
  *    Parity-even only (sum of principal l even) unless allparity != 0 (Table 1).
  *  - Output of npcf_finalize: orders ascending; for each order an array
  *    [n_multiplets][n_bin_tuples], bin tuples lexicographic with the last index
