@@ -32,7 +32,7 @@ METRIC = "primaries/sec for 4PCF (lmax=5, 10 shells); split-BF16 vs FP32 at stat
 WORKLOAD = "lognormal_200k_L1000_4pcf3pcf_lmax5_nr10_20-160"
 FOURPCF_ALG_FLOP_PER_PRIMARY = 405_360 + 126_240   # P-build + final contraction (lmax 5, N_r 10)
 PAIR_ALG_FLOP = 180                                  # per accepted pair at lmax 5
-N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES = 128                                     # FP32 lanes per SM (used only if the probe fails)
 KERNELS_PER_STEP = 10  # k_sumw, 4 cell-list kernels, pair, contract3, contract4, one reduce per order
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu pass) on the
@@ -128,18 +128,50 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(wl, sample_n: int, seed: int = 77):
+def cpu_oracle_rate(wl, sample_n: int, seed: int = 77, nthreads: int = 0, want_zeta: bool = False):
     """The oracle as it stands (OpenMP over primaries), timed on a sample of primaries
-    against the full catalog. Returns (primaries/s, cores, sample description)."""
+    against the full catalog. Returns (primaries/s, threads, sample description) and, with
+    want_zeta, also (sample indices, the oracle's raw zeta of that sample)."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
     sample = np.sort(rng.choice(wl.n, sample_n, replace=False))
-    cores = os.cpu_count() or 1
+    cores = nthreads or (os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample, nthreads=cores)
+    zeta, _ = oracle.npcf(wl.pos, wl.w, wl.orders, wl.lmax, wl.edges, wl.box, prim=sample, nthreads=cores)
     dt = time.perf_counter() - t0
-    return sample_n / dt, cores, "%d seeded primaries of the 200k catalog against all 200k secondaries" % sample_n
+    desc = "%d seeded primaries of the %dk catalog against all %dk secondaries" % (sample_n, wl.n // 1000,
+                                                                                  wl.n // 1000)
+    if want_zeta:
+        return sample_n / dt, cores, desc, sample, zeta
+    return sample_n / dt, cores, desc
+
+
+def fp32_peak_tflops(dev):
+    """Measured FP32 FMA throughput of this GPU (the library's probe), with the SM count
+    read from the device; falls back to SMs x 128 lanes x 2 x max clock if the probe fails."""
+    import torch
+    from paper_2105_08722_gb300._lib import probe_fp32_peak
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        t, _ = probe_fp32_peak()
+        return t, "measured: FMA-chain probe (npcf_probe_fp32_peak), %d SMs" % nsm, nsm
+    except Exception as e:   # noqa: BLE001
+        mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+        return (nsm * FP32_LANES * 2 * mhz * 1e6 / 1e12,
+                "derived: %d SMs x %d lanes x 2 x %.0f MHz (probe failed: %s)" % (nsm, FP32_LANES, mhz, e), nsm)
+
+
+def order_errors(got, want, orders, lmax, nr):
+    """max |got - want| / RMS(want) per order (the oracle's layout)."""
+    import oracle
+    g = oracle.split_orders(got, orders, lmax, nr)
+    o = oracle.split_orders(want, orders, lmax, nr)
+    out = {}
+    for N in orders:
+        rms = math.sqrt(float(np.mean(o[N] ** 2)))
+        out[str(N)] = float(np.max(np.abs(g[N] - o[N]))) / rms if rms > 0 else None
+    return out
 
 
 def max_over_ranks(values, world, device=None):
@@ -252,21 +284,28 @@ def run_gpu(args):
     # end to end: host buffers through the C ABI, copies and result read-back inside
     pos_h = np.ascontiguousarray(wl.pos)
     w_h = np.ascontiguousarray(wl.w)
-    e2e_est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, prec)
-    e2e_est.accumulate_host(pos_h, w_h)
-    e2e_est.finalize()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_est.reset()
-        e2e_est.accumulate_host(pos_h, w_h)
-        e2e_est.finalize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+
+    def e2e_ms_of(p):
+        e = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, p)
+        e.accumulate_host(pos_h, w_h)
+        e.finalize()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e.reset()
+            e.accumulate_host(pos_h, w_h)
+            e.finalize()
+        dt = (time.perf_counter() - t0) / args.steps
+        size = e.size
+        e.close()
+        return dt * 1e3, size
+
+    e2e_ms_local, out_size = e2e_ms_of(prec)
     barrier()
     clk = clocks.stop()
 
-    ms, e2e_ms = max_over_ranks([float(np.mean(step_ms)), e2e_s * 1e3], world, dev)
+    ms, e2e_ms = max_over_ranks([float(np.mean(step_ms)), e2e_ms_local], world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -276,14 +315,14 @@ def run_gpu(args):
     npairs_per_step = float(counts.sum()) / (args.warmup + args.steps)
     pair_tflops = npairs_per_step * PAIR_ALG_FLOP / (st[1] * 1e-3) / 1e12
     con_tflops = wl.n * FOURPCF_ALG_FLOP_PER_PRIMARY / (st[2] * 1e-3) / 1e12
-    fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak, peak_source, nsm = fp32_peak_tflops(dev)
     dominant = "pair" if st[1] >= st[2] else "contraction"
     achieved = pair_tflops if dominant == "pair" else con_tflops
     achieved = float(achieved)
     other = None
+    oprec = FP32 if prec == SPLIT_BF16 else SPLIT_BF16
     if not args.no_other_precision:
         # the other contraction arithmetic on the same workload (same timing protocol)
-        oprec = FP32 if prec == SPLIT_BF16 else SPLIT_BF16
         oest = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, oprec)
         for _ in range(args.warmup):
             oest.accumulate(pos, w)
@@ -299,9 +338,14 @@ def run_gpu(args):
             torch.cuda.synchronize()
             oms.append(s_ev.elapsed_time(e_ev))
         ost = np.mean(np.array(ost, dtype=np.float64), axis=0)
+        o_e2e_ms, _ = e2e_ms_of(oprec)
         other = {"precision": "bf16" if oprec == SPLIT_BF16 else "fp32",
                  "value": wl.n / (float(np.mean(oms)) * 1e-3), "ms_per_step": float(np.mean(oms)),
-                 "stages_ms": {"pair": float(ost[1]), "contraction": float(ost[2])}}
+                 "e2e": {"value": wl.n / (o_e2e_ms * 1e-3), "unit": "primaries/s",
+                         "h2d_bytes_per_step": int(wl.pos.nbytes + wl.w.nbytes),
+                         "d2h_bytes_per_step": int(8 * out_size)},
+                 "stages_ms": {"pair": float(ost[1]), "contraction": float(ost[2])},
+                 "contraction_tflops": float(wl.n * FOURPCF_ALG_FLOP_PER_PRIMARY / (ost[2] * 1e-3) / 1e12)}
         oest.close()
     line = {
         "metric": METRIC,
@@ -312,12 +356,13 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32" if prec == FP32 else "bf16x3",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_points": wl.n, "lmax": wl.lmax, "nr": 10, "orders": [3, 4],
+        "config": {"workload": WORKLOAD if wl.n == 200_000 else wl.name, "n_points": wl.n, "lmax": wl.lmax,
+                   "nr": 10, "orders": [3, 4],
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "e2e": {"value": aggregate_rate(wl.n, world, e2e_ms), "unit": "primaries/s",
                 "h2d_bytes_per_step": int(wl.pos.nbytes + wl.w.nbytes),
-                "d2h_bytes_per_step": int(8 * e2e_est.size)},
+                "d2h_bytes_per_step": int(8 * out_size)},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
                       "reduction": float(st[3])},
@@ -326,17 +371,32 @@ def run_gpu(args):
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": (_traffic(dominant if dominant == "pair" else "contraction/" + args.precision)
                                  if wl.n == 200_000 else None),
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+                     "peak_source": peak_source,
+                     "contraction_tflops": float(con_tflops),
+                     "contraction_frac": float(con_tflops / fp32_peak)},
         "clocks": clk,
         "other_precision": other,
-        "stated_error": {"fp32": "<= 1e-5 of each order's RMS vs the FP64 oracle (GPU tests)",
-                         "bf16": "<= 3e-5 of each order's RMS vs the FP64 oracle (GPU tests); "
-                                 "~3e-7 measured with tensor memory drained every 2 steps"},
     }
     if not args.no_cpu_baseline:
-        rate, cores, desc = cpu_oracle_rate(wl, args.cpu_sample)
+        rate, cores, desc, sample, zwant = cpu_oracle_rate(wl, args.cpu_sample, want_zeta=True)
+        rate1, _, desc1 = cpu_oracle_rate(wl, args.cpu_sample_1core, seed=78, nthreads=1)
         line["cpu_baseline"] = {"value": rate, "unit": "primaries/s", "cores": cores, "kind": "oracle",
-                                "sample": desc}
+                                "sample": desc, "value_1core": rate1, "sample_1core": desc1}
+        # measured error of both contraction arithmetics against the oracle on that sample:
+        # the sampled primaries (weight w, every other primary 0) against all secondaries
+        wprim = np.zeros(wl.n, np.float32)
+        wprim[sample] = wl.w[sample]
+        twp = torch.from_numpy(wprim).to(dev)
+        errs = {}
+        for p_, name in ((FP32, "fp32"), (SPLIT_BF16, "bf16")):
+            e = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, p_)
+            e.accumulate(pos, w, wprim=twp)
+            errs[name] = order_errors(e.finalize(), zwant, wl.orders, wl.lmax, len(wl.edges) - 1)
+            e.close()
+        line["stated_error"] = {
+            "measure": "max |gpu - oracle| / RMS(oracle) per zeta order, raw sums of %d seeded primaries "
+                       "against the full catalog" % len(sample),
+            "fp32": errs["fp32"], "bf16": errs["bf16"], "bar": {"fp32": 1e-5, "bf16": 3e-5}}
     print(json.dumps(line))
     sys.stdout.flush()
     if world > 1:
@@ -430,7 +490,7 @@ def run_gpu_batch(args):
     ms = float(np.mean(step_ms))
     counts = est.pair_counts_batch().sum() / (args.warmup + args.steps)
     alg = counts * PAIR_ALG_FLOP + n * FOURPCF_ALG_FLOP_PER_PRIMARY
-    fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak, peak_source, _ = fp32_peak_tflops(dev)
     achieved = alg / (ms * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": n / (ms * 1e-3), "unit": "primaries/s", "n_gpus": 1,
@@ -446,7 +506,7 @@ def run_gpu_batch(args):
         "gpu_launches": args.steps,   # one CUDA-graph launch per step (KERNELS_PER_STEP kernels inside)
         "roofline": {"bound": "alu", "kernel": "whole batch (pair + contraction)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+                     "peak_source": peak_source},
         "clocks": clk,
         "per_catalog_error_vs_fp32": {str(N): {"max": max(errs[N]), "median": statistics.median(errs[N])}
                                       for N in (3, 4)},
@@ -640,7 +700,7 @@ def run_gpu_5pcf(args):
     t = float(np.mean(ms))
     # algorithmic 5PCF flop per primary: the P12 and P34 builds and the final products
     alg = wl.n * (543_200 * 2 + 1_110_200)
-    fp32_peak = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak, peak_source, _ = fp32_peak_tflops(dev)
     achieved = alg / (st[2] * 1e-3) / 1e12
     line = {
         "metric": "primaries/sec for the 5PCF (lmax=4, 8 shells)", "value": wl.n / (t * 1e-3),
@@ -653,7 +713,7 @@ def run_gpu_5pcf(args):
                       "reduction": float(st[3])},
         "roofline": {"bound": "alu", "kernel": "contraction (5PCF)", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"},
+                     "peak_source": peak_source},
         "clocks": clk,
     }
     print(json.dumps(line))
@@ -679,6 +739,7 @@ def main():
                          "lognormal100k-5pcf: 100k points, 5PCF; batch64: 64 catalogs in one batch; "
                          "paper4 / paper5: the paper's timing catalog (5e4 uniform, L 1500), 4PCF / 5PCF")
     ap.add_argument("--cpu-sample", type=int, default=1500)
+    ap.add_argument("--cpu-sample-1core", type=int, default=120)
     ap.add_argument("--ref-sample", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-precision", action="store_true",

@@ -61,8 +61,10 @@ typedef enum {
 } npcf_status;
 
 /* Arithmetic of the contraction over primaries (step 3). FP32: CUDA-core FP32
- * products and sums. SPLIT_BF16: tensor-core (tcgen05) products of bf16 hi/lo
- * splits (hi*hi + hi*lo + lo*hi), FP32 accumulation. Cross-block sums are FP64. */
+ * products and sums. SPLIT_BF16: each FP32 operand v is split into three bf16 terms
+ * v ~ hi + mid + lo and the tensor cores (tcgen05) form the six products
+ * hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid with FP32 accumulation.
+ * Cross-block sums are FP64. */
 typedef enum {
     NPCF_FP32 = 0,
     NPCF_SPLIT_BF16 = 1
@@ -87,8 +89,12 @@ npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr,
  * so random-catalog splits co-add, Sec. 4.2).
  *   d_pos   device float32 [n][3] positions (x, y, z), caller-owned
  *   d_w     device float32 [n] weights w_j (secondaries, and primaries unless d_wprim)
- *   d_wprim nullable device float32 [n] primary weights u_i; primaries with u_i == 0
- *           are skipped (used to evaluate a sample of primaries)
+ *   d_wprim nullable device float32 [n] primary weights u_i. When given, a primary with
+ *           u_i == 0 is skipped entirely: its a_lm are not formed and its neighbours
+ *           are not counted (so a seeded sample of primaries can be evaluated against
+ *           the full catalog; npcf_pair_counts then counts the sample's pairs only).
+ *           Without d_wprim, u_i = w_i and every primary's neighbours are counted,
+ *           including those of primaries of weight 0 (which add nothing to zeta).
  *   n       number of particles, 0 <= n < 2^31
  *   stream  cudaStream_t to enqueue on (0 = legacy default stream)
  * Work is enqueued asynchronously; caller buffers must stay valid until the stream
@@ -200,21 +206,25 @@ npcf_status npcf_get_timings(npcf_ctx* ctx, float* ms4);
 
 /* Exact per-shell pair counts of one catalog, computed without allocating any device
  * memory. The paper has no counterpart; this exists for callers that cannot call
- * cudaMalloc: code running while a CUDA graph is captured, processes whose device memory
- * belongs to another allocator, plug-ins that must not grow their memory footprint.
+ * cudaMalloc: processes whose device memory belongs entirely to another allocator (a
+ * framework's caching pool, a pipeline that forbids allocation after start-up), and
+ * plug-ins that must not grow their memory footprint per call.
  *   d_pos    device float32 [n][3] positions, caller-owned; in [0, box) when periodic
  *   n        0 <= n <= 262144 (larger catalogs are rejected with NPCF_EINVAL)
  *   nr, edges, box   as in npcf_create (host edges[nr+1]; box > 3 edges[nr] or 0)
  *   d_counts device uint64 [nr], caller-owned; overwritten with the counts of this call
  *   stream   cudaStream_t the work is enqueued on
  * Counts are the same as npcf_accumulate + npcf_pair_counts give for the catalog (the
- * same FP32 neighbour rule). All scratch lives in one fixed device array of about 13 MiB
- * that every GPU loading the library keeps until the process exits. The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make it before
- * any stream capture. Calls share the array: each clears what must start at zero, and
- * calls that overlap on the GPU race. With box == 0 the call reads the bounding box back
- * to the host (one stream synchronisation); with box > 0 it is fully asynchronous.
- * Errors are reported through npcf_last_error(NULL). */
+ * same FP32 neighbour rule, every particle a primary). A position outside [0, box) when
+ * periodic, or a NaN position, is found on the device after the call has returned: then
+ * every entry of d_counts is set to UINT64_MAX (a value no count reaches) instead of a
+ * count. All scratch lives in one fixed device array of about 13 MiB that every GPU
+ * loading the library keeps until the process exits. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress). Calls share the array: each clears
+ * what must start at zero, and calls that overlap on the GPU race. With box == 0 the call
+ * reads the bounding box back to the host (one stream synchronisation); with box > 0 it
+ * only enqueues work. Errors found on the host are reported through
+ * npcf_last_error(NULL). */
 npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, int nr, const double* edges,
                                      double box, uint64_t* d_counts, void* stream);
 
@@ -256,7 +266,8 @@ npcf_status npcf_gaunt(int N, const int* L1, const int* L2, const int* L3, doubl
 /* Multiplets L of order N = 3..6 (Sec. 2.2: the triangle conditions of the 3-j symbols of
  * Eq. basis-coupling, principal l's <= lmax, intermediates over their natural range; the
  * parity-even ones, sum of principal l's even, unless allparity), in the output order of
- * npcf_finalize ("last element varied first", Sec. 5.1). Layout per multiplet: {l, l},
+ * npcf_finalize (lexicographic in the l's with the last entry fastest, the order of the
+ * edge-correction matrices of the mock-catalog figures, Sec. 5.4). Layout per multiplet: {l, l},
  * {l1, l2, l3}, {l1, l2, l12, l3, l4}, {l1, l2, l12, l3, l123, l4, l5}. *count receives
  * their number; out (nullable) receives count x (2, 3, 5, 7) ints. Host-only. The 6PCF
  * has no GPU contraction yet: npcf_create takes orders 3 to 5. lmax in [0, 10]. */
@@ -267,6 +278,16 @@ npcf_status npcf_multiplets(int N, int lmax, int allparity, int* count, int* out
  * M = {m_1, ..., m_{N-1}} (host ints). *out receives the value (0 where the 3-j symbols
  * vanish). Host-only; NPCF_EINVAL for N outside 3..6 or an l outside [0, 40]. */
 npcf_status npcf_coupling(int N, const int* L, const int* M, double* out);
+
+/* FP32 CUDA-core throughput of the current device, measured: the peak that the FP32
+ * roofline fractions of the pair kernel and the FP32 contractions are taken against (the
+ * paper has no counterpart). Launches fused multiply-add chains on every SM (four blocks
+ * of 256 threads per SM, eight independent chains per thread), times five launches after a
+ * warm-up with CUDA events on the legacy default stream and keeps the fastest.
+ * *tflops receives 2 x FMAs / time in TFLOP/s; ms (nullable) that launch's time.
+ * Synchronises the device; allocates a small output buffer; errors through
+ * npcf_last_error(NULL). */
+npcf_status npcf_probe_fp32_peak(double* tflops, double* ms);
 
 /* Message of the last failed call on ctx; with ctx == NULL, of the last failed
  * npcf_create or npcf_pair_counts_noalloc on this thread. */

@@ -13,8 +13,9 @@
  *                   associated-Legendre three-term recurrence in cos(theta) and
  *                   e^{i m phi} from atan2 -- the textbook route.
  *   orc_multiplets  the multiplets L of orders 3 to 6 (Sec. 2.2: triangle conditions
- *                   of the 3-j symbols, parity-even unless allparity), in the order
- *                   "last element varied first" (Sec. 5.1); orc_multiplets_cap bounds
+ *                   of the 3-j symbols, parity-even unless allparity), lexicographic
+ *                   with the last entry fastest (the order of the edge-correction
+ *                   matrices of the mock-catalog figures, Sec. 5.4); orc_multiplets_cap bounds
  *                   the intermediate l's.
  *   orc_coupling    C^L_M: Eq. (N=3-coeff), Eq. (N=4-coeff) and, for N=5 and N=6,
  *                   the general Eq. (basis-coupling) with its sqrt(2 l12 + 1) (and
@@ -110,7 +111,7 @@ void orc_ylm(int lmax, double x, double y, double z, double* re, double* im) {
 
 static int n_ell(int N) { return N == 3 ? 2 : (N == 4 ? 3 : (N == 5 ? 5 : 7)); }
 
-/* Multiplets in lexicographic order, last element varied first (Sec. 5.1). icap bounds
+/* Multiplets in lexicographic order, the last entry fastest (Sec. 5.4). icap bounds
  * the intermediate l's (l12, l123); their natural range (triangle conditions with every
  * principal l <= lmax) is 2 lmax, which orc_multiplets uses. */
 int orc_multiplets_cap(int N, int lmax, int icap, int allparity, int* out) {

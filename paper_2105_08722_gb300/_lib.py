@@ -46,6 +46,7 @@ SIGNATURES = {
     "npcf_truncate": (_i, [_vp, _vp, _sz, _i, _vp, ctypes.POINTER(_sz)]),
     "npcf_multiplets": (_i, [_i, _i, _i, ctypes.POINTER(_i), _vp]),
     "npcf_coupling": (_i, [_i, _vp, _vp, ctypes.POINTER(_d)]),
+    "npcf_probe_fp32_peak": (_i, [ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "npcf_last_error": (ctypes.c_char_p, [_vp]),
     "npcf_destroy": (None, [_vp]),
 }
@@ -78,6 +79,17 @@ def pair_counts_noalloc(pos, edges, box: float, out, stream=None):
                                       _ptr(out), _stream_handle(stream))
     if st != NPCF_OK:
         raise NPCFError(st, lib.npcf_last_error(None).decode())
+
+
+def probe_fp32_peak() -> Tuple[float, float]:
+    """Measured FP32 FMA throughput of the current device (npcf_probe_fp32_peak):
+    (TFLOP/s, ms of the fastest launch)."""
+    lib = load()
+    t, ms = _d(), _d()
+    st = lib.npcf_probe_fp32_peak(ctypes.byref(t), ctypes.byref(ms))
+    if st != NPCF_OK:
+        raise NPCFError(st, lib.npcf_last_error(None).decode())
+    return t.value, ms.value
 
 
 def gaunt(N: int, L1, L2, L3) -> float:

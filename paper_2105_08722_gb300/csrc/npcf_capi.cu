@@ -770,7 +770,9 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecord(ctx->ev[1], s));
 
-    launch_pair(P.pa, ctx->nsm, s);   // persistent: one block per SM, work units taken dynamically
+    PairArgs pa = P.pa;
+    pa.skip_zero = d_wprim != nullptr;
+    launch_pair(pa, ctx->nsm, s);   // persistent: one block per SM, work units taken dynamically
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecord(ctx->ev[2], s));
 

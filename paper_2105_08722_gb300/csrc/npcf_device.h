@@ -70,6 +70,8 @@ struct PairArgs {
     int n;
     int* work;                 // dynamic cell counter (zeroed by caller)
     int* err;                  // error bits (2: a bounded wait gave up)
+    int skip_zero;             // separate primary weights given: a primary of weight 0 is
+                               // not evaluated (no a_lm, no counts); else every primary is
     int cap;                   // 16-bit entries per warp neighbour list
     int cand_cap;              // points the staging buffer holds
     int run;                   // cells per work unit (x-adjacent)

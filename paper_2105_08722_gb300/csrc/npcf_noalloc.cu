@@ -1,12 +1,12 @@
 // Exact per-shell pair counts without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured, hosts whose device memory belongs entirely to another allocator (a
-// framework's caching pool, a real-time pipeline that forbids allocation after start-up),
-// or plug-ins that must not change the process's memory footprint per call. For them
-// npcf_pair_counts_noalloc computes the same neighbour counts as the context-based path
-// (npcf_accumulate + npcf_pair_counts) but keeps every scratch buffer -- the cell list,
-// the neighbour rows, the counters -- in one file-scope device array of fixed size.
+// Some callers cannot call cudaMalloc: hosts whose device memory belongs entirely to
+// another allocator (a framework's caching pool that must not be bypassed, a real-time
+// pipeline that forbids allocation after start-up), or plug-ins that must not change the
+// process's memory footprint per call. For them npcf_pair_counts_noalloc computes the same
+// neighbour counts as the context-based path (npcf_accumulate + npcf_pair_counts) but
+// keeps every scratch buffer -- the cell list and the counters -- in one file-scope device
+// array of fixed size; the few neighbour-row offsets travel in the kernel's arguments.
 //
 // That array (kScratchBytes, about 13 MiB) is held by every GPU that loads the library
 // until the process exits. It bounds the catalog to kMaxPoints points and the grid to
@@ -35,7 +35,7 @@ using namespace npcf;
 
 constexpr int64_t kMaxPoints = 1 << 18;    // 262,144 particles
 constexpr int kMaxCells = 1 << 18;         // neighbour-grid cells
-constexpr int kMaxRows = 2048;             // neighbour rows of the grid
+constexpr int kMaxRows = 128;              // neighbour rows of the grid (4 cells per r_max: 77)
 constexpr int kBBoxBlocks = 64;
 constexpr int kWarps = 8;
 
@@ -50,8 +50,7 @@ constexpr size_t kOffWp = align256(kOffCellOf + 4 * kMaxPoints);
 constexpr size_t kOffCount = align256(kOffWp + 4 * kMaxPoints);
 constexpr size_t kOffStart = align256(kOffCount + 4 * (size_t)kMaxCells);
 constexpr size_t kOffCursor = align256(kOffStart + 4 * ((size_t)kMaxCells + 1));
-constexpr size_t kOffRows = align256(kOffCursor + 4 * (size_t)kMaxCells);
-constexpr size_t kOffBBox = align256(kOffRows + 16 * (size_t)kMaxRows);
+constexpr size_t kOffBBox = align256(kOffCursor + 4 * (size_t)kMaxCells);
 constexpr size_t kOffMisc = align256(kOffBBox + 4 * 6 * (size_t)kBBoxBlocks);
 constexpr size_t kScratchBytes = align256(kOffMisc + 256);
 
@@ -92,13 +91,14 @@ struct CountArgs {
     const float4* pts;
     const uint32_t* cell_of;
     const uint32_t* cell_start;
-    const int4* rows;
+    int4 rows[kMaxRows];       // (dy, dz, dx_lo, dx_hi), by value: no host buffer to copy
     int nrows;
     GridInfo g;
     float e2[kMaxNr + 1];
     int nr;
     int n;
     int* work;
+    const int* err;            // error bits of the binning (1: position outside the box or NaN)
     unsigned long long* counts;
 };
 
@@ -113,8 +113,14 @@ __global__ void k_fill_ones(float* w, int n) {
 }
 
 // Count-only variant of the pair kernel: one warp per primary, neighbour cells read from
-// global memory, per-warp shared histograms flushed once per warp at the end.
+// global memory, per-warp shared histograms flushed once per warp at the end. If the
+// binning flagged a position outside the periodic box or a NaN position, no pair is
+// counted and every count is set to UINT64_MAX instead (a value no count reaches).
 __global__ void __launch_bounds__(kWarps * 32) k_count(const CountArgs a) {
+    if (*(volatile const int*)a.err & 1) {
+        if (blockIdx.x == 0 && threadIdx.x < a.nr) a.counts[threadIdx.x] = ~0ull;
+        return;
+    }
     __shared__ uint32_t hist[kWarps][kMaxNr];
     __shared__ float e2[kMaxNr + 1];
     if (threadIdx.x <= a.nr) e2[threadIdx.x] = a.e2[threadIdx.x];
@@ -249,8 +255,6 @@ extern "C" npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, i
     const int nrows = (int)rows.size() / 4;
     if (nrows > kMaxRows || g.ncell > kMaxCells) return bad(NPCF_EINVAL, "neighbour grid exceeds the fixed scratch");
 
-    int4* d_rows = reinterpret_cast<int4*>(base + kOffRows);
-    CUN(cudaMemcpyAsync(d_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     uint32_t* count = reinterpret_cast<uint32_t*>(base + kOffCount);
     int* misc = reinterpret_cast<int*>(base + kOffMisc);   // [0] error bits, [1] work counter
     CUN(cudaMemsetAsync(count, 0, (size_t)g.ncell * sizeof(uint32_t), s));
@@ -284,13 +288,15 @@ extern "C" npcf_status npcf_pair_counts_noalloc(const float* d_pos, int64_t n, i
     c.pts = b.pts;
     c.cell_of = b.cell_of;
     c.cell_start = b.start;
-    c.rows = d_rows;
+    for (int r = 0; r < nrows; ++r)
+        c.rows[r] = make_int4(rows[4 * r], rows[4 * r + 1], rows[4 * r + 2], rows[4 * r + 3]);
     c.nrows = nrows;
     c.g = g;
     for (int i = 0; i <= nr; ++i) c.e2[i] = (float)(edges[i] * edges[i]);
     c.nr = nr;
     c.n = (int)n;
     c.work = misc + 1;
+    c.err = misc;
     c.counts = reinterpret_cast<unsigned long long*>(d_counts);
     int dev = 0, nsm = 0;
     CUN(cudaGetDevice(&dev));

@@ -380,8 +380,10 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
     const int gt = warp * 32 + lane;   // thread index in the group
     const GridInfo& g = a.g;
     float2* out = a.alm + (size_t)p * nr * NLM;
-    const float u = a.wp[p];
-    if (u == 0.f) {  // primary not evaluated
+    // A primary of weight 0 adds nothing to zeta, but its neighbours are still counted
+    // (every primary's pairs enter the counts) unless separate primary weights select a
+    // sample of primaries: then a weight of 0 means "not in the sample".
+    if (a.skip_zero && a.wp[p] == 0.f) {  // primary not evaluated
         if (!add) {
             for (int i = gt; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
             if (gt < nr) a.cnt[(size_t)p * nr + gt] = 0u;

@@ -119,6 +119,26 @@ def test_pair_counts_on_exact_edges_and_duplicates(torch_dev):
         assert np.array_equal(counts, oracle.pair_counts(pos, edges, box)), box
 
 
+def test_zero_and_negative_weights_counts_and_zeta(torch_dev):
+    # Algorithm 1 visits every primary and every secondary within the shells: a primary of
+    # weight 0 adds nothing to zeta but its pairs are still counted. About 10 % of the
+    # weights are exactly 0 and the signs are mixed (as in data-minus-randoms catalogs).
+    rng = np.random.default_rng(4242)
+    n, box = 3000, 120.0
+    pos = rng.uniform(0, box, size=(n, 3)).astype(np.float32)
+    w = rng.uniform(-1.5, 1.5, size=n).astype(np.float32)
+    w[rng.random(n) < 0.1] = 0.0
+    assert (w == 0).sum() > 200 and (w < 0).sum() > 1000
+    edges = np.linspace(4.0, 30.0, 7)
+    for prec, tol in ((0, TOL_FP32), (1, TOL_BF16)):
+        est, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, box, prec=prec)
+        assert np.array_equal(counts, oracle.pair_counts(pos, edges, box)), prec
+        want, wc = oracle.npcf(pos, w, (3, 4), 3, edges, box)
+        assert np.array_equal(counts, wc)
+        assert_orders_close(got, want, (3, 4), 3, len(edges) - 1, tol=tol)
+        est.close()
+
+
 # ------------------------------------------------------------------ a_lm
 
 @pytest.mark.parametrize("lmax", [6, 8, 10])
