@@ -68,10 +68,11 @@ struct npcf_ctx {
     // cell-list tuning and geometry
     int cells_per_rmax = 0;    // 0: chosen per call from the catalog's density
     int cell_run = 3;          // x-adjacent cells per pair-kernel work unit
-    int pair_cap = 6144;       // per group of the pair kernel
+    int pair_cap = 8192;       // pair kernel: bucket entries per warp (all shells)
     int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int drain_steps = 2;       // tensor-core contraction: steps of 16 primaries per TMEM drain
     int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
+    int use_stab = 1;          // pair kernel: shell by table lookup when the table is valid
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -111,6 +112,10 @@ struct npcf_ctx {
     DevBuf<uint32_t> idx, cell_of, cid;
     DevBuf<float2> alm;
     DevBuf<uint32_t> cnt;
+    DevBuf<uint32_t> bucket;   // pair kernel: per-warp per-shell buckets of accepted pairs
+    DevBuf<int4> stab;         // pair kernel: shell of r2 by bins (when stab_ok)
+    int stab_ok = 0, stab_n = 0;
+    float stab_scale = 0.f;
     DevBuf<uint32_t> count, start, cursor;
     DevBuf<double> partial, zeta, sumw, zscale;
     DevBuf<unsigned long long> counts;
@@ -503,7 +508,7 @@ npcf_status check_ctx(npcf_ctx* ctx) {
 int auto_cells_per_rmax(double points, double volume, double rmax) {
     if (!(volume > 0) || !(points > 0)) return 5;
     const double nb = points / volume * (4.0 / 3.0) * M_PI * rmax * rmax * rmax;
-    return nb < 630.0 ? 2 : (nb < 2500.0 ? 3 : 5);
+    return nb < 630.0 ? 2 : (nb < 2500.0 ? 3 : 4);
 }
 
 npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, int ncat, cudaStream_t s) {
@@ -675,8 +680,23 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     pa.ncat = ncat;
     pa.n = n;
     pa.work = ctx->work.p;
-    pa.cap = ctx->pair_cap;
     pa.err = ctx->errflag.p;
+    {
+        // buckets: every shell at least 128 entries, the rest shared in proportion to the
+        // shell volumes (the expected share of pairs of an unclustered catalog)
+        const int nr = ctx->nr, C = ctx->pair_cap;
+        const double e0 = ctx->edges[0], en = ctx->edges[nr];
+        const double vtot = en * en * en - e0 * e0 * e0;
+        const int spare = C - 128 * nr;
+        pa.boff[0] = 0;
+        for (int t = 0; t < nr; ++t) {
+            const double lo = ctx->edges[t], hi = ctx->edges[t + 1];
+            const double f = (hi * hi * hi - lo * lo * lo) / vtot;
+            pa.boff[t + 1] = pa.boff[t] + 128 + (int)std::floor(f * spare);
+        }
+        CU(ctx->bucket.ensure((size_t)ctx->nsm * kPairWarps * pa.boff[nr]));
+        pa.bucket = ctx->bucket.p;
+    }
     {
         // a run of cells must not make the periodic neighbour span wrap onto itself
         int reach = 0;
@@ -694,6 +714,20 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         pa.linear = lin ? 1 : 0;
         pa.lin_r0 = (float)r0;
         pa.lin_inv_w = lin ? (float)(1.0 / w) : 0.f;
+        if (!ctx->stab.p && !ctx->stab_ok) {
+            std::vector<int4> tab;
+            float scale = 0.f;
+            if (build_shell_table(ctx->e2, ctx->nr, kPairShellTab, &tab, &scale)) {
+                CU(upload(ctx->stab, tab));
+                ctx->stab_ok = 1;
+                ctx->stab_n = (int)tab.size();
+                ctx->stab_scale = scale;
+            }
+        }
+        pa.tab_ok = ctx->stab_ok && ctx->use_stab;
+        pa.tab_n = ctx->stab_n;
+        pa.tab_scale = ctx->stab_scale;
+        pa.tab = ctx->stab.p;
         // x-window cut of the staged rows: row cells are packed in 13 bits per axis
         const double cell = 1.0 / (double)g.inv_cell;
         double M = 0.0;
@@ -712,8 +746,8 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         const long long room =
             (long long)optin - (long long)pair_static_smem(ctx->lmax) - (long long)pair_dynamic_smem(pa) - 256;
         if (room < 16 * 256)
-            return fail(ctx, NPCF_EINVAL, "pair kernel: neighbour-list capacity %d leaves no room for "
-                        "staging (shared memory limit %d B)", pa.cap, optin);
+            return fail(ctx, NPCF_EINVAL, "pair kernel: %d neighbour rows leave no room for staging "
+                        "(shared memory limit %d B)", pa.nrows, optin);
         pa.cand_cap = (int)std::min<long long>(room / 16, 65535);
         if (ctx->stage_limit > 0) pa.cand_cap = std::min(pa.cand_cap, ctx->stage_limit);
     }
@@ -936,8 +970,8 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
         (uintptr_t)ctx->partial.p, (uintptr_t)ctx->zeta.p, (uintptr_t)ctx->counts.p, (uintptr_t)ctx->sumw.p,
         (uintptr_t)ctx->d_off.p, (uintptr_t)ctx->chunks.p, (uintptr_t)ctx->cbeg.p, (uintptr_t)ctx->rows.p,
         (uintptr_t)ctx->chunks4.p, (uintptr_t)ctx->cbeg4.p, (uintptr_t)P.nchunk4,
-        (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.run, (uintptr_t)P.pa.cap,
-        (uintptr_t)P.pa.cand_cap, (uintptr_t)P.pa.trim, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
+        (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.run, (uintptr_t)P.pa.bucket, (uintptr_t)P.pa.boff[ctx->nr],
+        (uintptr_t)P.pa.cand_cap, (uintptr_t)P.pa.trim, (uintptr_t)P.pa.tab_ok, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
     for (long long v : off) sig.push_back((uintptr_t)v);
     if (ctx->gexec && sig == ctx->gsig) {
         CU(cudaGraphLaunch(ctx->gexec, s));
@@ -1221,8 +1255,8 @@ npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, i
     float best_ms = 1e30f;
     // pair kernel: grid cell size, cells per work unit, neighbour-list capacity
     for (int k : {2, 3, 4, 5, 6})
-        for (int run : {2, 3, 4})
-            for (int cap : {4096, 6144}) {
+        for (int run : {2, 3, 4, 6})
+            for (int cap : {4096, 8192}) {
                 ctx->cells_per_rmax = k;
                 ctx->cell_run = run;
                 ctx->pair_cap = cap;
@@ -1443,10 +1477,11 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             ctx->chunk_target = value;
             return NPCF_OK;
         case 3:
-            // the staged scan appends up to 128 entries per warp and step: a warp's list
-            // (capacity / 8) must hold one whole step, or the scan cannot advance
-            if (value < 1024 || value > 16384 || (value % 256))
-                return fail(ctx, NPCF_EINVAL, "pair list capacity must be a multiple of 256 in [1024, 16384]");
+            // every shell's bucket gets at least 128 entries (a scan step appends at most 32
+            // per shell), so 16 shells need 2048
+            if (value < 2048 || value > 65536 || (value % 256))
+                return fail(ctx, NPCF_EINVAL, "pair bucket entries per warp must be a multiple of 256 in "
+                            "[2048, 65536]");
             ctx->pair_cap = value;
             return NPCF_OK;
         case 4:
@@ -1454,7 +1489,7 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             ctx->stage_limit = value;
             return NPCF_OK;
         case 5:
-            if (value < 1 || value > 4) return fail(ctx, NPCF_EINVAL, "cells per work unit in [1, 4]");
+            if (value < 1 || value > 8) return fail(ctx, NPCF_EINVAL, "cells per work unit in [1, 8]");
             ctx->cell_run = value;
             return NPCF_OK;
         case 6:
@@ -1464,6 +1499,10 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
         case 7:
             if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "x-window cut is 0 or 1");
             ctx->trim = value;
+            return NPCF_OK;
+        case 8:
+            if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "shell table is 0 or 1");
+            ctx->use_stab = value;
             return NPCF_OK;
         default:
             return fail(ctx, NPCF_EINVAL, "unknown tuning key %d", key);

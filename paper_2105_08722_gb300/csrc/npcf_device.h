@@ -25,6 +25,10 @@ bool plan_periodic_grid(double L, double rmax, int cells_per_rmax, int max_cells
                         std::vector<int>* rows);
 void plan_open_grid(const float mn[3], const float mx[3], double rmax, int cells_per_rmax,
                     int max_cells, GridInfo* g, std::vector<int>* rows);
+// Table of the neighbour rule's shell over bins of r2 of width 2^-k (at most max_bins
+// bins up to e2[nr]): entry i = (shell below, shell above, bits of the float r2 where it
+// changes, 0), valid when no bin holds two changes; *scale = 2^k. False if none fits.
+bool build_shell_table(const float* e2, int nr, int max_bins, std::vector<int4>* tab, float* scale);
 
 // ---------------------------------------------------------------- cell list (a1)
 struct BinArgs {
@@ -51,6 +55,8 @@ void launch_bbox(const float* pos, int n, float* part, int nblocks, cudaStream_t
 void launch_bin(const BinArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- pair kernel (a2 + a3)
+constexpr int kPairWarps = 16;     // independent warps per pair-kernel block (one block per SM)
+constexpr int kPairShellTab = 512; // bins of r2 of the pair kernel's shell table
 struct PairArgs {
     const float4* pts;
     const float* wp;
@@ -72,11 +78,16 @@ struct PairArgs {
     int* err;                  // error bits (2: a bounded wait gave up)
     int skip_zero;             // separate primary weights given: a primary of weight 0 is
                                // not evaluated (no a_lm, no counts); else every primary is
-    int cap;                   // 16-bit entries per warp neighbour list
+    uint32_t* bucket;          // [blocks][kPairWarps][boff[nr]] per-shell buckets of accepted pairs
+    int boff[kMaxNr + 1];      // shell t's bucket: entries [boff[t], boff[t+1]) of a warp's region
     int cand_cap;              // points the staging buffer holds
     int run;                   // cells per work unit (x-adjacent)
     int linear;                // edges are linear in r: shell estimated from sqrt(r2)
     float lin_r0, lin_inv_w;   // first edge and 1 / shell width of linear edges
+    int tab_ok;                // the shell table below is valid (else the estimate above)
+    int tab_n;                 // bins of the table
+    float tab_scale;           // bin of r2: floor(r2 tab_scale), a power of two
+    const int4* tab;           // [tab_n] (shell below, shell above, bits of float r2 where it changes, 0)
     int trim;                  // cut staged rows to each primary's x-window (cells sorted by x)
     float cell;                // cell side of the grid
     float trim_margin;         // slack of the cut (covers FP32 rounding of the cell bounds)

@@ -1,6 +1,9 @@
 // Host-side planning of the neighbour-search grid, shared by every entry point.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
+#include <cstring>
+#include <limits>
 #include <vector>
 
 #include "npcf_device.h"
@@ -88,6 +91,57 @@ void plan_open_grid(const float mn[3], const float mx[3], double rmax, int cells
     g->ncell = g->gx * g->gy * g->gz;
     int reach = 0;
     *rows = neighbour_rows(cell, rmax, &reach);
+}
+
+// Shell of the FP32 neighbour rule as a function of r2 alone: -1 for r2 == 0 (coincident
+// points), below e2[0] or at/above e2[nr]; b for e2[b] <= r2 < e2[b+1]. Same comparisons as
+// the device rule (float operands).
+static int rule_shell(float r2, const float* e2, int nr) {
+    if (!(r2 > 0.f) || !(r2 >= e2[0]) || !(r2 < e2[nr])) return -1;
+    int b = 0;
+    while (b + 1 < nr && r2 >= e2[b + 1]) ++b;
+    return b;
+}
+
+bool build_shell_table(const float* e2, int nr, int max_bins, std::vector<int4>* tab, float* scale) {
+    // bins of width 2^-k over [0, e2[nr]], as many as fit: k the largest integer with
+    // floor(e2[nr] 2^k) + 1 <= max_bins; then r2 * 2^k is exact in FP32 and so is its floor
+    const double top = e2[nr];
+    if (!(top > 0.0) || !std::isfinite(top)) return false;
+    int k = (int)std::floor(std::log2((max_bins - 1) / top));
+    while (std::floor(top * std::ldexp(1.0, k)) + 1 > max_bins) --k;
+    while (std::floor(top * std::ldexp(1.0, k + 1)) + 1 <= max_bins) ++k;
+    if (k < -120 || k > 120) return false;
+    const int nb = (int)std::floor(top * std::ldexp(1.0, k)) + 1;
+    // the points where the rule's shell changes: just above 0, and every edge
+    std::vector<float> brk;
+    brk.push_back(std::numeric_limits<float>::denorm_min());
+    for (int b = 0; b <= nr; ++b)
+        if (e2[b] > 0.f) brk.push_back(e2[b]);
+    std::sort(brk.begin(), brk.end());
+    brk.erase(std::unique(brk.begin(), brk.end()), brk.end());
+    tab->assign(nb, make_int4(0, 0, 0, 0));
+    size_t q = 0;
+    for (int i = 0; i < nb; ++i) {
+        const double lo = std::ldexp((double)i, -k), hi = std::ldexp((double)(i + 1), -k);
+        while (q < brk.size() && (double)brk[q] <= lo) ++q;   // already in force at the bin start
+        const float flo = (float)lo;                            // exact: lo has few significant bits
+        const int below = rule_shell(flo, e2, nr);
+        int above = below;
+        float edge = std::numeric_limits<float>::infinity();
+        size_t inside = 0;
+        while (q + inside < brk.size() && (double)brk[q + inside] < hi) ++inside;
+        if (inside > 1) return false;   // two changes in one bin: no table
+        if (inside == 1) {
+            edge = brk[q];
+            above = rule_shell(edge, e2, nr);
+        }
+        int bits;
+        std::memcpy(&bits, &edge, 4);
+        (*tab)[i] = make_int4(below, above, bits, 0);
+    }
+    *scale = (float)std::ldexp(1.0, k);
+    return true;
 }
 
 }  // namespace npcf

@@ -12,21 +12,23 @@
 // The Chebyshev basis keeps the conversion coefficients O(1), so FP32 sums do not lose
 // accuracy to cancellation at high l as plain powers z^k would.
 //
-// A persistent block (2 groups of 8 warps) takes work units, runs of x-adjacent cells of
-// one catalog's grid, from a device counter. For a unit, warp 0 lists the neighbour rows
-// (rows of cells within r_max of the run) and one thread stages their points into shared
-// memory with bulk asynchronous copies, in passes of rows that fit the buffer. A group
-// then takes the unit's primaries one at a time:
+// A persistent block of kPairWarps independent warps takes work units, runs of
+// x-adjacent cells of one catalog's grid, from a device counter. For a unit, warp 0 lists
+// the neighbour rows (rows of cells within r_max of the run) and one thread stages their
+// points into shared memory with bulk asynchronous copies, in passes of rows that fit the
+// buffer. Each warp then takes the unit's primaries one at a time from a shared counter
+// and runs the whole primary alone, so no warp waits for another between the phases of a
+// primary (the scan of one warp overlaps the accumulation of another):
 //   cut: every staged row is cut to the primary's x-window and the kept rows form one
-//        flat index space, split evenly over the group's warps;
-//   scan: each lane tests candidates with the exact FP32 neighbour/shell rule; accepted
-//        pairs go to the warp's sub-list (16-bit staged index, shell), shells counted;
-//   sort: a counting sort orders the group's slice by shell (a full sub-list ends the
-//        slice early; the scan then resumes where it stopped);
-//   accumulate: each warp takes an equal run of 32-entry packets of the sorted slice,
-//        accumulates the S_{m,k} of each shell in registers and reduces them across
-//        lanes with a shuffle transpose-reduction; the per-shell sums, folded in warp
-//        order, are converted to a_lm (added to the earlier passes' a_lm, if any).
+//        flat index space;
+//   scan: each lane tests four candidates a step with the exact FP32 neighbour/shell
+//        rule; accepted pairs go straight to per-shell buckets (a private region of
+//        global scratch per warp, sized by shell volume and resident in L2) as
+//        (staged index, periodic shift code);
+//   accumulate: a full bucket, and at the end every non-empty one, is summed into the
+//        S_{m,k} of its shell in registers and reduced across lanes with a shuffle
+//        transpose-reduction; the per-shell sums are converted to a_lm (added to the
+//        earlier passes' a_lm, if any).
 #include "npcf_device.h"
 #include "npcf_rules.cuh"
 #include "npcf_warp.cuh"
@@ -204,67 +206,44 @@ __device__ void build_segments(const PairArgs& a, const int4* rows, int cbase, i
     if (lane == 0) { *out_nseg = nseg; *out_total = total; *out_maxseg = maxseg; }
 }
 
-constexpr int kW = 8;             // warps per group; a group works on one primary
-constexpr int kG = 2;             // groups per block
 constexpr int kShiftCodes = 64;   // 2 bits per axis
+constexpr int kKC = 4;            // candidates per lane per scan step (independent chains)
+constexpr int kShellTab = kPairShellTab;
 
 // Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
-// cap is the neighbour-list capacity of one group in 16-bit entries.
 struct PairLayout {
-    size_t cand, segs, rows, tpref, tdc, tstart, tcode, ulist, ushell, slist, part, total;
+    size_t cand, segs, rows, tpref, tdc, psum, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Floats of one group's partial area: nr + kW - 1 slots for the slice's per-warp sums
-// (warp w's share of shell t goes to slot t + w: the warps' equal runs of packets of the
-// shell-sorted slice are ordered, so these never collide) and nr per-shell sums.
-__host__ __device__ constexpr int part_floats(int nr, int nc) { return (2 * nr + kW - 1) * nc; }
-
-__host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int cap, int nr, int nc) {
+__host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int nr, int nc) {
     PairLayout l;
     l.cand = 0;
     l.segs = align16(l.cand + (size_t)cand_cap * 16);
     l.rows = align16(l.segs + (size_t)2 * nrows * 16);
-    // per group: flat-index prefix and (staging offset minus prefix, shift code) of each
-    // kept row; per-row scratch of the cut (staging start, code and count)
+    // per warp: flat-index prefix and (staging offset minus prefix, shift code) of each
+    // kept row of the current primary, then the primary's per-shell sums
     l.tpref = align16(l.rows + (size_t)nrows * 16);
-    l.tdc = align16(l.tpref + (size_t)kG * (2 * nrows + 1) * 4);
-    l.tstart = align16(l.tdc + (size_t)kG * 2 * nrows * 4);
-    l.tcode = align16(l.tstart + (size_t)kG * 2 * nrows * 4);
-    l.ulist = align16(l.tcode + (size_t)kG * 2 * nrows * 4);
-    l.ushell = align16(l.ulist + (size_t)kG * cap * 2);
-    l.slist = align16(l.ushell + (size_t)kG * cap);
-    // per group: the slice's (warp, shell) partials in slots shell + warp, then the
-    // primary's per-shell sums
-    l.part = align16(l.slist + (size_t)kG * cap * 2);
-    l.total = align16(l.part + (size_t)kG * part_floats(nr, nc) * 4);
+    l.tdc = align16(l.tpref + (size_t)kPairWarps * (2 * nrows + 1) * 4);
+    l.psum = align16(l.tdc + (size_t)kPairWarps * 2 * nrows * 4);
+    l.total = align16(l.psum + (size_t)kPairWarps * nr * nc * 4);
     return l;
 }
 
-// Shared state of one group.
-struct GroupShared {
-    uint32_t hist[kW][kMaxNr];     // per-warp shell counts of the current slice
-    uint32_t base[kW][kMaxNr];     // where each warp scatters each shell
-    uint32_t off[kMaxNr + 1];      // shell offsets of the sorted slice
-    uint32_t pk[kMaxNr + 1];       // first 32-entry packet of each shell (packets never straddle shells)
-    uint32_t tot[kMaxNr];          // shell totals of the current primary
-    int done[kW];
-    int wtot[kW];                  // per-warp sums of the row-trimming prefix
-};
-
 template <int L>
 struct PairShared {
-    float4 shift[kShiftCodes];     // (sx, sy, sz) of each periodic shift code
+    float4 shift[kShiftCodes];       // (sx, sy, sz) of each periodic shift code
+    int4 stab[kShellTab];            // shell of r2 by bins of r2 (valid when the table is on)
     float kmat[nlmc(L) * (L + 1)];
     float e2[kMaxNr + 1];
-    GroupShared grp[kG];
+    int boff[kMaxNr + 1];            // bucket of shell t: entries [boff[t], boff[t+1]) of a warp's region
+    int2 ne[kPairWarps][kMaxNr + 1]; // per warp and shell: next free entry, end of the bucket;
+                                     // slot kMaxNr takes rejected candidates and never fills
+    uint32_t tot[kPairWarps][kMaxNr];// accepted pairs of the warp's current primary, per shell
     int unit[4];
+    int next;                        // next primary of the current pass (dynamic over warps)
 };
-
-__device__ __forceinline__ void group_sync(int grp) {
-    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kW * 32) : "memory");
-}
 
 // Both ends of the staged row at 'base' (n points, sorted by x) that fall in [vlo, vhi]:
 // the first index with x >= vlo and the first with x > vhi. The two searches run in
@@ -283,356 +262,290 @@ __device__ __forceinline__ int2 x_bounds(const float4* cand, int base, int n, fl
     return make_int2(a, b);
 }
 
-// The part of every staged row this primary can reach, as one flat index space over
-// the rows left non-empty: row s covers flat [tpref[s], tpref[s+1]), its staged index is
-// flat + (tdc[s] >> 6) and its periodic shift code tdc[s] & 63. With trim, a row keeps
-// only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus a margin) of the
-// primary, d_yz the distance from the primary to the row's (y, z) cell square; the exact
-// FP32 rule is applied to what remains. Rows are sorted by x (cells in x order, members
-// sorted by x). tstart and tcode are scratch. Returns the flat total; *nrow = rows kept.
-template <int L>
-__device__ __forceinline__ int trim_rows(const PairArgs& a, const PairShared<L>& sh, const float4* cand,
-                                         const int4* segs, int nseg, int zbase, const float4 pi, int* tpref,
-                                         int* tdc, int* tstart, int* tcode, int* wtot, bool trim, int grp,
-                                         int warp, int lane, int* nrow) {
-    const int gt = warp * 32 + lane;
-    const int per = (nseg + kW * 32 - 1) / (kW * 32);   // rows per thread
-    const int s0 = min(nseg, gt * per), s1 = min(nseg, s0 + per);
-    const float R2 = sh.e2[a.nr], m = a.trim_margin, c = a.cell;
-    int cnt_local = 0, rows_local = 0;
-    for (int s = s0; s < s1; ++s) {
-        const int4 sg = segs[s];
-        int lo = 0, hi = sg.y;
-        if (trim) {
-            const float4 sf = sh.shift[sg.w & 63];
-            const int yy = (sg.w >> 6) & 8191, zz = (int)((unsigned)sg.w >> 19);
-            const float ylo = a.g.oy + (float)yy * c - sf.y - m, yhi = ylo + c + 2.f * m;
-            const float zlo = a.g.oz + (float)zz * c - sf.z - m, zhi = zlo + c + 2.f * m;
-            const float dy = fmaxf(0.f, fmaxf(ylo - pi.y, pi.y - yhi));
-            const float dz = fmaxf(0.f, fmaxf(zlo - pi.z, pi.z - zhi));
-            const float d2 = dy * dy + dz * dz;
-            if (d2 >= R2 * (1.f + 1e-5f)) {
-                hi = 0;
-            } else {
-                const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
-                const float xc = pi.x + sf.x;
-                const int2 ab = x_bounds(cand, sg.z - zbase, sg.y, xc - h, xc + h);
-                lo = ab.x;
-                hi = ab.y;
-            }
-        }
-        tstart[s] = sg.z - zbase + lo;
-        tcode[s] = (sg.w & 63) | ((hi - lo) << 8);
-        cnt_local += hi - lo;
-        rows_local += hi > lo ? 1 : 0;
-    }
-    // exclusive prefix over the group's threads of (rows kept << 16 | points); both fit
-    // in 16 bits: points <= staging capacity, rows <= 2 nrows
-    const int v = (rows_local << 16) | cnt_local;
-    int incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wtot[warp] = incl;
-    group_sync(grp);
-    int base = incl - v;
-    for (int w = 0; w < warp; ++w) base += wtot[w];
-    int total = 0;
-    for (int w = 0; w < kW; ++w) total += wtot[w];
-    int pb = base & 0xffff, rb = base >> 16;
-    for (int s = s0; s < s1; ++s) {
-        const int cs = tcode[s] >> 8;
-        if (cs > 0) {
-            tpref[rb] = pb;
-            tdc[rb] = ((tstart[s] - pb) << 6) | (tcode[s] & 63);   // staged start >= flat start
-            ++rb;
-            pb += cs;
-        }
-    }
-    *nrow = total >> 16;
-    total &= 0xffff;
-    if (gt == 0) tpref[*nrow] = total;
-    group_sync(grp);
-    return total;
+// The exact FP32 neighbour rule (same operations as shell_of in npcf_rules.cuh), its
+// shell read from a table over bins of r2: bin i = [i, i + 1) / scale with scale a power
+// of two, so i = floor(r2 scale) is exact; the host has checked that no bin holds more
+// than one point where the rule's shell changes (r2 > 0, the edges e2[b]), and entry i
+// gives the shell below and above that point. -1 for a rejected pair.
+__device__ __forceinline__ int pair_shell_tab(const float4 pj, const float4 pi, float sx, float sy, float sz,
+                                              const int4* tab, float scale, int nbin) {
+    const float dx = __fsub_rn(__fsub_rn(pj.x, pi.x), sx);
+    const float dy = __fsub_rn(__fsub_rn(pj.y, pi.y), sy);
+    const float dz = __fsub_rn(__fsub_rn(pj.z, pi.z), sz);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    const int i = min(__float2int_rz(__fmul_rn(r2, scale)), nbin - 1);   // NaN gives 0
+    const int4 e = tab[i];
+    return r2 >= __int_as_float(e.z) ? e.y : e.x;
 }
 
-// One primary, processed by one group of kW warps. Neighbours are split evenly over the
-// warps (flat index space of the cut staged rows, or segments round-robin for the
-// global-memory path); each warp appends accepted neighbours (index, shell) to its own
-// sub-list; a counting sort orders the slice by shell (ranks from __match_any_sync); each
-// warp takes an equal run of 32-entry packets of the sorted slice and its per-shell sums
-// go to per-warp partials, which give a_lm at the end (added to the a_lm of earlier
-// staging passes when add is set). Sub-lists that fill up end the slice early, and the
-// scan resumes where it stopped.
+// The part of every staged row this primary can reach, as one flat index space over the
+// rows left non-empty (one warp): row s covers flat [tpref[s], tpref[s+1]), its staged
+// index is flat + (tdc[s] >> 6) and its periodic shift code tdc[s] & 63. With trim, a row
+// keeps only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus a margin) of the
+// primary, d_yz the distance from the primary to the row's (y, z) cell square; the exact
+// FP32 rule is applied to what remains. Rows are sorted by x (cells in x order, members
+// sorted by x). Returns the flat total; *nrow = rows kept.
+template <int L>
+__device__ __forceinline__ int cut_rows(const PairArgs& a, const PairShared<L>& sh, const float4* cand,
+                                        const int4* segs, int nseg, int zbase, const float4 pi, int* tpref,
+                                        int* tdc, bool trim, int lane, int* nrow) {
+    const float R2 = sh.e2[a.nr], m = a.trim_margin, c = a.cell;
+    int rows_acc = 0, pts_acc = 0;
+    for (int k0 = 0; k0 < nseg; k0 += 32) {
+        const int s = k0 + lane;
+        int lo = 0, hi = 0, start = 0, code = 0;
+        if (s < nseg) {
+            const int4 sg = segs[s];
+            hi = sg.y;
+            code = sg.w & 63;
+            if (trim) {
+                const float4 sf = sh.shift[code];
+                const int yy = (sg.w >> 6) & 8191, zz = (int)((unsigned)sg.w >> 19);
+                const float ylo = a.g.oy + (float)yy * c - sf.y - m, yhi = ylo + c + 2.f * m;
+                const float zlo = a.g.oz + (float)zz * c - sf.z - m, zhi = zlo + c + 2.f * m;
+                const float dy = fmaxf(0.f, fmaxf(ylo - pi.y, pi.y - yhi));
+                const float dz = fmaxf(0.f, fmaxf(zlo - pi.z, pi.z - zhi));
+                const float d2 = dy * dy + dz * dz;
+                if (d2 >= R2 * (1.f + 1e-5f)) {
+                    hi = 0;
+                } else {
+                    const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
+                    const float xc = pi.x + sf.x;
+                    const int2 ab = x_bounds(cand, sg.z - zbase, sg.y, xc - h, xc + h);
+                    lo = ab.x;
+                    hi = ab.y;
+                }
+            }
+            start = sg.z - zbase + lo;
+        }
+        const int cnt = hi - lo;
+        // inclusive prefix of (kept rows << 16 | points): points <= staging capacity < 2^16
+        const int v = ((cnt > 0 ? 1 : 0) << 16) | cnt;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int ex = incl - v;
+        if (cnt > 0) {
+            const int rb = rows_acc + (ex >> 16), pb = pts_acc + (ex & 0xffff);
+            tpref[rb] = pb;
+            tdc[rb] = ((start - pb) << 6) | code;   // staged start >= flat start
+        }
+        const int tot = __shfl_sync(kFull, incl, 31);
+        rows_acc += tot >> 16;
+        pts_acc += tot & 0xffff;
+    }
+    if (lane == 0) tpref[rows_acc] = pts_acc;
+    __syncwarp();
+    *nrow = rows_acc;
+    return pts_acc;
+}
+
+// n accepted pairs of one shell into that shell's sums pw[0 .. ncomp(L)) (one warp; all
+// lanes call it together): the lanes take consecutive entries and accumulate
+// S_{m,k} = sum w (x + i y)^m T_k(z) in registers (T_k Chebyshev, m + k <= lmax); a
+// shuffle transpose-reduction adds the lanes' sums to pw. Staged entries hold (staged
+// index | shift code << 16): the separation is the one the neighbour rule accepted,
+// (p_j - p_i) - shift. Global entries hold the point index; the periodic image is then the
+// minimum image (accepted pairs are closer than L/3). Not inlined: a scan calls it only
+// when a bucket fills, and once per non-empty shell at the end of a primary.
 template <int L, bool STAGED>
-__device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand,
-                                            const int4* segs, int nseg, int zbase, int total,
-                                            int* tpref, int* tdc, int* tstart, int* tcode, bool trim,
-                                            uint16_t* ulist, uint8_t* ushell, uint16_t* slist, float* part,
-                                            int p, int cat, bool add, int grp, int warp, int lane,
-                                            const int* slot_org) {
+__device__ __noinline__ void sum_bucket(const float4* cand, const float4* pts, const float4* shift,
+                                        const uint32_t* e, int n, float4 pi, float boxL, float* pw, int lane) {
+    constexpr int NC = ncomp(L);
+    using R = TR<NC>;
+    float acc[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) acc[i] = 0.f;
+    const float invL = boxL > 0.f ? 1.f / boxL : 0.f;
+    uint32_t cur = lane < n ? __ldcg(e + lane) : 0u;
+    for (int i = lane; i - lane < n; i += 32) {
+        const uint32_t nxt = i + 32 < n ? __ldcg(e + i + 32) : 0u;
+        if (i < n) {
+            float dx, dy, dz, wj;
+            if (STAGED) {
+                const float4 pj = cand[cur & 0xffffu];
+                const float4 sf = shift[cur >> 16];
+                dx = (pj.x - pi.x) - sf.x;
+                dy = (pj.y - pi.y) - sf.y;
+                dz = (pj.z - pi.z) - sf.z;
+                wj = pj.w;
+            } else {
+                const float4 pj = pts[cur];
+                dx = pj.x - pi.x;
+                dy = pj.y - pi.y;
+                dz = pj.z - pi.z;
+                wj = pj.w;
+                dx = fmaf(-boxL, rintf(dx * invL), dx);
+                dy = fmaf(-boxL, rintf(dy * invL), dy);
+                dz = fmaf(-boxL, rintf(dz * invL), dz);
+            }
+            const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, wj);
+        }
+        cur = nxt;
+    }
+    R::run(acc, lane);
+#pragma unroll
+    for (int i = 0; i < R::F; ++i) {
+        const int o = R::origin(i, lane);
+        if (o >= 0) pw[o] += acc[i];
+    }
+    __syncwarp();
+}
+
+// Shell t's bucket of the warp into the shell's sums; the bucket is then empty.
+template <int L, bool STAGED>
+__device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh, const float4* cand,
+                                            const uint32_t* bucket, float* psum, int t, float4 pi, int warp,
+                                            int lane) {
+    __syncwarp();   // the entries written by every lane are visible
+    const int b0 = sh.boff[t];
+    const int n = sh.ne[warp][t].x - b0;
+    sum_bucket<L, STAGED>(cand, a.pts, sh.shift, bucket + b0, n, pi, a.g.periodic ? a.g.L : 0.f,
+                          psum + t * ncomp(L), lane);
+    if (lane == 0) {
+        sh.tot[warp][t] += (uint32_t)n;
+        sh.ne[warp][t].x = b0;
+    }
+    __syncwarp();
+}
+
+// Append one accepted pair per lane (shell b, -1 for none) to the warp's per-shell
+// buckets; a bucket that cannot take its lanes' entries is summed and emptied first.
+template <int L, bool STAGED>
+__device__ __forceinline__ void bucket_insert(const PairArgs& a, PairShared<L>& sh, const float4* cand,
+                                              uint32_t* bucket, float* psum, int b, uint32_t entry, float4 pi,
+                                              int warp, int lane, unsigned lt) {
+    const unsigned gm = __match_any_sync(kFull, b);
+    const int rank = __popc(gm & lt);
+    const int bi = b < 0 ? kMaxNr : b;
+    int2 ne = sh.ne[warp][bi];
+    if (__any_sync(kFull, ne.x + rank >= ne.y)) {   // rare: some lane's bucket is full
+        const unsigned fullm = __reduce_or_sync(kFull, ne.x + rank >= ne.y ? 1u << bi : 0u);
+        for (unsigned mm = fullm; mm; mm &= mm - 1)
+            flush_shell<L, STAGED>(a, sh, cand, bucket, psum, __ffs(mm) - 1, pi, warp, lane);
+        ne = sh.ne[warp][bi];
+    }
+    if (b >= 0) bucket[ne.x + rank] = entry;
+    __syncwarp();
+    if (b >= 0 && rank == 0) sh.ne[warp][bi].x = ne.x + __popc(gm);
+    __syncwarp();
+}
+
+// One primary, processed by one warp (no other warp waits for it). Staged: the rows of
+// the staging pass are cut to the primary's x-window and form one flat index space that
+// the lanes scan kKC candidates at a time with the exact FP32 neighbour rule; global: the
+// rows are read from global memory, 32 candidates a step. Accepted pairs go straight to
+// per-shell buckets (a private region of global scratch, L2-resident); a full bucket and,
+// at the end, every non-empty one are summed into the per-shell sums, which give a_lm
+// (added to the a_lm of earlier staging passes when add is set).
+template <int L, bool STAGED>
+__device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand, const int4* segs,
+                            int nseg, int zbase, int* tpref, int* tdc, float* psum, uint32_t* bucket, bool trim,
+                            int p, int cat, bool add, int warp, int lane) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
-    using R = TR<NC>;
-    GroupShared& G = sh.grp[grp];
     const int nr = a.nr;
-    const int gt = warp * 32 + lane;   // thread index in the group
-    const GridInfo& g = a.g;
     float2* out = a.alm + (size_t)p * nr * NLM;
     // A primary of weight 0 adds nothing to zeta, but its neighbours are still counted
     // (every primary's pairs enter the counts) unless separate primary weights select a
     // sample of primaries: then a weight of 0 means "not in the sample".
-    if (a.skip_zero && a.wp[p] == 0.f) {  // primary not evaluated
+    if (a.skip_zero && a.wp[p] == 0.f) {
         if (!add) {
-            for (int i = gt; i < nr * NLM; i += kW * 32) out[i] = make_float2(0.f, 0.f);
-            if (gt < nr) a.cnt[(size_t)p * nr + gt] = 0u;
+            for (int i = lane; i < nr * NLM; i += 32) out[i] = make_float2(0.f, 0.f);
+            if (lane < nr) a.cnt[(size_t)p * nr + lane] = 0u;
         }
         return;
     }
     const float4 pi = a.pts[p];
-    float* slot = part;                          // [nr + kW - 1][NC], rewritten every slice
-    float* psum = part + (nr + kW - 1) * NC;     // [nr][NC] sums of the primary
-    for (int i = gt; i < nr * NC; i += kW * 32) psum[i] = 0.f;
-    if (gt < kMaxNr) G.tot[gt] = 0u;
-
-    // this warp's share of the neighbours and its sub-list
-    const int capw = STAGED ? a.cap / kW : a.cap / (2 * kW);
-    // sub-list entries: 16-bit staged index (staged) or 32-bit point index (global), shell
-    uint16_t* ul16 = ulist + (size_t)warp * (a.cap / kW);
-    uint32_t* ul32 = reinterpret_cast<uint32_t*>(ul16);
-    uint8_t* us = ushell + (size_t)warp * (a.cap / kW);
-    const float e2lo = sh.e2[0], e2hi = sh.e2[nr];
-    uint32_t* sl32 = reinterpret_cast<uint32_t*>(slist);
-    // staged: the rows cut to this primary's x-window, one flat index space split evenly
-    int nrow = 0;
-    const int T = STAGED ? trim_rows<L>(a, sh, cand, segs, nseg, zbase, pi, tpref, tdc, tstart, tcode, G.wtot,
-                                        trim, grp, warp, lane, &nrow)
-                         : total;
-    const int per = (T + kW - 1) / kW;
-    int cursor = STAGED ? min(T, warp * per) : 0;
-    const int kend = STAGED ? min(T, cursor + per) : 0;
-    int seg = warp, segpos = 0;   // global-memory path: segments warp, warp + kW, ...
-    const unsigned lt = (1u << lane) - 1u;
-    // staged: the row of flat index cursor (first s with tpref[s + 1] > cursor), the same
-    // in every lane
-    int srow = 0;
-    if (STAGED && cursor < kend) {
-        const int k0 = cursor;
-        int lo = 0, n = nrow;
-        while (n > 0) {
-            const int half = n >> 1;
-            if (tpref[lo + half + 1] <= k0) {
-                lo += half + 1;
-                n -= half + 1;
-            } else {
-                n = half;
-            }
-        }
-        srow = lo;
+    for (int i = lane; i < nr * NC; i += 32) psum[i] = 0.f;
+    if (lane < nr) {
+        sh.ne[warp][lane] = make_int2(sh.boff[lane], sh.boff[lane + 1]);
+        sh.tot[warp][lane] = 0u;
     }
-    group_sync(grp);   // partials zeroed before any warp adds to them
-
-    for (;;) {
-        // ---- scan: append accepted neighbours while the sub-list has room, counting shells
-        int cw = 0;
-        if (lane < kMaxNr) G.hist[warp][lane] = 0u;
-        __syncwarp();
-        if (STAGED) {
-            // candidates per lane per step (independent chains). A step appends up to
-            // 32 KC entries, so capw >= 32 KC is required for progress: the host admits
-            // list capacities of at least 1024 (capw >= 128).
-            constexpr int KC = 4;
-            while (cw + 32 * KC <= capw && cursor < kend) {
-                // Rows of the step's flat indices cursor + o, o < 32 KC, without per-lane
-                // searches: lane i loads the end of row srow + i (rows are non-empty, so the
-                // ends increase strictly); a bitmap of the ends' offsets in the step gives
-                // each offset's row as srow + the ends at or below it. The step stops at the
-                // last loaded end, so no row beyond the loaded ones is met.
-                const int d = tpref[min(srow + 1 + lane, nrow)] - cursor;   // >= 1
-                const int lim = min(min(32 * KC, kend - cursor), __shfl_sync(kFull, d, 31));
-                unsigned W[KC];
+    __syncwarp();
+    const float e2lo = sh.e2[0], e2hi = sh.e2[nr];
+    const bool tab = a.tab_ok != 0;
+    const unsigned lt = (1u << lane) - 1u;
+    if (STAGED) {
+        int nrow = 0;
+        const int T = cut_rows<L>(a, sh, cand, segs, nseg, zbase, pi, tpref, tdc, trim, lane, &nrow);
+        int cursor = 0, srow = 0;
+        while (cursor < T) {
+            // Rows of the step's flat indices cursor + o, o < 32 kKC, without per-lane
+            // searches: lane i loads the end of row srow + i (rows are non-empty, so the
+            // ends increase strictly); a bitmap of the ends' offsets in the step gives each
+            // offset's row as srow + the ends at or below it. The step stops at the last
+            // loaded end, so no row beyond the loaded ones is met.
+            const int d = tpref[min(srow + 1 + lane, nrow)] - cursor;   // >= 1
+            const int lim = min(min(32 * kKC, T - cursor), __shfl_sync(kFull, d, 31));
+            unsigned W[kKC];
 #pragma unroll
-                for (int j = 0; j < KC; ++j) {
-                    const unsigned o = (unsigned)(d - 32 * j);
-                    W[j] = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
+            for (int j = 0; j < kKC; ++j) {
+                const unsigned o = (unsigned)(d - 32 * j);
+                W[j] = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
+            }
+            const unsigned le = 0xffffffffu >> (31 - lane);   // offsets 32 j .. 32 j + lane
+            int q[kKC], b[kKC], code[kKC];
+            float4 sf[kKC];
+            int below = 0;
+#pragma unroll
+            for (int j = 0; j < kKC; ++j) {
+                const int row = min(srow + below + __popc(W[j] & le), nrow - 1);
+                below += __popc(W[j]);
+                const int dc = tdc[row];
+                q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + (dc >> 6) : 0;
+                code[j] = dc & 63;
+                sf[j] = sh.shift[code[j]];
+            }
+            float4 c[kKC];
+#pragma unroll
+            for (int j = 0; j < kKC; ++j) c[j] = cand[q[j]];
+            if (tab) {
+#pragma unroll
+                for (int j = 0; j < kKC; ++j) {
+                    const int r = pair_shell_tab(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.stab, a.tab_scale,
+                                                 a.tab_n);
+                    b[j] = (32 * j + lane < lim) ? r : -1;
                 }
-                const unsigned le = 0xffffffffu >> (31 - lane);   // offsets 32 j .. 32 j + lane
-                int q[KC], b[KC];
-                float4 sf[KC];
-                int below = 0;
+            } else {
 #pragma unroll
-                for (int j = 0; j < KC; ++j) {
-                    const int row = min(srow + below + __popc(W[j] & le), nrow - 1);
-                    below += __popc(W[j]);
-                    const int dc = tdc[row];
-                    q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + (dc >> 6) : 0;
-                    sf[j] = sh.shift[dc & 63];
-                }
-                float4 c[KC];
-#pragma unroll
-                for (int j = 0; j < KC; ++j) c[j] = cand[q[j]];
-#pragma unroll
-                for (int j = 0; j < KC; ++j) {
+                for (int j = 0; j < kKC; ++j) {
                     const int r = pair_shell_fast(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.e2, nr, e2lo, e2hi,
                                                   a.linear, a.lin_r0, a.lin_inv_w);
                     b[j] = (32 * j + lane < lim) ? r : -1;
                 }
-#pragma unroll
-                for (int j = 0; j < KC; ++j) {
-                    const unsigned m = __ballot_sync(kFull, b[j] >= 0);
-                    if (b[j] >= 0) {
-                        const int pos = cw + __popc(m & lt);
-                        ul16[pos] = (uint16_t)q[j];
-                        us[pos] = (uint8_t)b[j];
-                    }
-                    cw += __popc(m);
-                    const unsigned gm = __match_any_sync(kFull, b[j]);
-                    if (b[j] >= 0 && lane == __ffs(gm) - 1) atomicAdd(&G.hist[warp][b[j]], (uint32_t)__popc(gm));
-                }
-                srow += __popc(__ballot_sync(kFull, d <= lim));   // the row of cursor + lim
-                cursor += lim;
             }
-        } else {
-            while (seg < nseg && cw + 32 <= capw) {
-                const int4 sg = segs[seg];
-                const float4 sf = sh.shift[sg.w & 63];
-                const int k = segpos + lane;
+            srow += __popc(__ballot_sync(kFull, d <= lim));   // the row of cursor + lim
+            cursor += lim;
+#pragma unroll
+            for (int j = 0; j < kKC; ++j)
+                bucket_insert<L, true>(a, sh, cand, bucket, psum, b[j], (uint32_t)q[j] | ((uint32_t)code[j] << 16),
+                                       pi, warp, lane, lt);
+        }
+    } else {
+        for (int s = 0; s < nseg; ++s) {
+            const int4 sg = segs[s];
+            const float4 sf = sh.shift[sg.w & 63];
+            for (int k0 = 0; k0 < sg.y; k0 += 32) {
+                const int k = k0 + lane;
                 int b = -1;
                 if (k < sg.y)
-                    b = pair_shell_fast(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.e2, nr, e2lo, e2hi, a.linear,
-                                        a.lin_r0, a.lin_inv_w);
-                const unsigned m = __ballot_sync(kFull, b >= 0);
-                if (b >= 0) {
-                    const int pos = cw + __popc(m & lt);
-                    ul32[pos] = (uint32_t)(sg.x + k);
-                    us[pos] = (uint8_t)b;
-                }
-                cw += __popc(m);
-                const unsigned gm = __match_any_sync(kFull, b);
-                if (b >= 0 && lane == __ffs(gm) - 1) atomicAdd(&G.hist[warp][b], (uint32_t)__popc(gm));
-                segpos += 32;
-                if (segpos >= sg.y) { seg += kW; segpos = 0; }
+                    b = tab ? pair_shell_tab(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.stab, a.tab_scale, a.tab_n)
+                            : pair_shell_fast(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.e2, nr, e2lo, e2hi,
+                                              a.linear, a.lin_r0, a.lin_inv_w);
+                bucket_insert<L, false>(a, sh, cand, bucket, psum, b, (uint32_t)(sg.x + k), pi, warp, lane, lt);
             }
         }
-        const bool done = STAGED ? (cursor >= kend) : (seg >= nseg);
-        if (lane == 0) G.done[warp] = done ? 1 : 0;
-        group_sync(grp);
-        int all_done = 1;
-        for (int w = 0; w < kW; ++w) all_done &= G.done[w];
-
-        // ---- shell offsets of the slice and each warp's scatter bases
-        if (warp == 0) {
-            uint32_t tsum = 0u;
-            if (lane < nr)
-                for (int w = 0; w < kW; ++w) tsum += G.hist[w][lane];
-            uint32_t incl = tsum;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
-            }
-            // packets of 32 entries per shell, and their prefix
-            const uint32_t npk = (tsum + 31u) / 32u;
-            uint32_t pincl = npk;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, pincl, o);
-                if (lane >= o) pincl += y;
-            }
-            if (lane < nr) {
-                uint32_t bw = incl - tsum;
-                G.off[lane] = bw;
-                G.pk[lane] = pincl - npk;
-                for (int w = 0; w < kW; ++w) { G.base[w][lane] = bw; bw += G.hist[w][lane]; }
-                G.tot[lane] += tsum;
-            }
-            if (lane == nr - 1) {
-                G.off[nr] = incl;
-                G.pk[nr] = pincl;
-            }
-        }
-        group_sync(grp);
-
-        // ---- scatter the sub-list into shell order (stable within a warp)
-        for (int k0 = 0; k0 < cw; k0 += 32) {
-            const bool ok = k0 + lane < cw;
-            const int shk = ok ? (int)us[k0 + lane] : -1;
-            const uint32_t idx = ok ? (STAGED ? (uint32_t)ul16[k0 + lane] : ul32[k0 + lane]) : 0u;
-            const unsigned m = __match_any_sync(kFull, shk);
-            const uint32_t b0 = ok ? G.base[warp][shk] : 0u;
-            __syncwarp();
-            if (ok) {
-                const uint32_t pos = b0 + (uint32_t)__popc(m & lt);
-                if (STAGED) slist[pos] = (uint16_t)idx;
-                else sl32[pos] = idx;
-                if (lane == __ffs(m) - 1) G.base[warp][shk] = b0 + (uint32_t)__popc(m);
-            }
-            __syncwarp();
-        }
-        group_sync(grp);
-
-        // ---- accumulate an equal run of 32-entry packets of the sorted slice, per shell
-        // (a packet holds one shell's entries, so only a shell's last packet has idle lanes)
-        {
-            const int npk = (int)G.pk[nr];
-            const int per = (npk + kW - 1) / kW;
-            const int q0 = min(npk, warp * per), q1 = min(npk, q0 + per);
-            for (int t = 0; t < nr; ++t) {
-                const int pa = max(q0, (int)G.pk[t]), pb = min(q1, (int)G.pk[t + 1]);
-                if (pa >= pb) continue;
-                const int base = (int)G.off[t] - 32 * (int)G.pk[t], hi = (int)G.off[t + 1];
-                float acc[NC];
-                const float invL = 1.f / g.L;
-#pragma unroll
-                for (int i = 0; i < NC; ++i) acc[i] = 0.f;
-                for (int q = pa; q < pb; ++q) {
-                    const int k = base + 32 * q + lane;
-                    if (k >= hi) continue;
-                    float dx, dy, dz, wj;
-                    // accepted pairs are closer than r_max < L/3: the minimum image is the
-                    // image the neighbour rule accepted (taken without branches)
-                    const float4 pj = STAGED ? cand[slist[k]] : a.pts[sl32[k]];
-                    dx = pj.x - pi.x;
-                    dy = pj.y - pi.y;
-                    dz = pj.z - pi.z;
-                    wj = pj.w;
-                    if (g.periodic) {
-                        dx = fmaf(-g.L, rintf(dx * invL), dx);
-                        dy = fmaf(-g.L, rintf(dy * invL), dy);
-                        dz = fmaf(-g.L, rintf(dz * invL), dz);
-                    }
-                    const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, wj);
-                }
-                R::run(acc, lane);
-                float* pw = slot + (size_t)(t + warp) * NC;
-#pragma unroll
-                for (int i = 0; i < R::F; ++i)
-                    if (slot_org[i] >= 0) pw[slot_org[i]] = acc[i];
-            }
-        }
-        group_sync(grp);   // lists are rewritten by the next slice
-        // fold the slice's slots into the primary's sums, warps in order (deterministic);
-        // the next slice writes slots only after its next group barrier
-        {
-            const int npk = (int)G.pk[nr];
-            const int per = (npk + kW - 1) / kW;
-            for (int i = gt; i < nr * NC; i += kW * 32) {
-                const int t = i / NC, c = i - t * NC;
-                const int o0 = (int)G.pk[t], o1 = (int)G.pk[t + 1];
-                float v = 0.f;
-                for (int w = 0; w < kW; ++w) {
-                    const int q0 = min(npk, w * per), q1 = min(npk, q0 + per);
-                    if (max(q0, o0) < min(q1, o1)) v += slot[(t + w) * NC + c];
-                }
-                psum[i] += v;
-            }
-        }
-        if (all_done) break;
     }
-    group_sync(grp);   // every fold is done before the sums are read
+    for (int t = 0; t < nr; ++t)
+        if (sh.ne[warp][t].x > sh.boff[t]) flush_shell<L, STAGED>(a, sh, cand, bucket, psum, t, pi, warp, lane);
+    __syncwarp();
 
-    // ---- combine the per-warp partials and convert to a_lm
-    for (int i = gt; i < nr * NLM; i += kW * 32) {
+    // ---- per-shell sums to a_lm
+    for (int i = lane; i < nr * NLM; i += 32) {
         const int t = i / NLM, q = i % NLM;
         int l = 0, m = q;
         while (m > l) { m -= l + 1; ++l; }
@@ -652,19 +565,18 @@ __device__ __forceinline__ void one_primary(const PairArgs& a, PairShared<L>& sh
         }
         out[i] = make_float2(re, im);
     }
-    if (gt < nr) {
-        const uint32_t c = G.tot[gt];
-        a.cnt[(size_t)p * nr + gt] = add ? a.cnt[(size_t)p * nr + gt] + c : c;
-        if (c) atomicAdd(&a.counts[(size_t)cat * nr + gt], (unsigned long long)c);
+    if (lane < nr) {
+        const uint32_t c = sh.tot[warp][lane];
+        a.cnt[(size_t)p * nr + lane] = add ? a.cnt[(size_t)p * nr + lane] + c : c;
+        if (c) atomicAdd(&a.counts[(size_t)cat * nr + lane], (unsigned long long)c);
     }
-    group_sync(grp);   // partials and totals are reset by the next primary
+    __syncwarp();   // psum, ne and tot are reset by the next primary
 }
 
 template <int L>
-__global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
-    using R = TR<ncomp(L)>;
+__global__ void __launch_bounds__(kPairWarps * 32, 1) k_pair(const PairArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    const PairLayout lay = pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(L));
+    const PairLayout lay = pair_layout(a.cand_cap, a.nrows, a.nr, ncomp(L));
     float4* cand = reinterpret_cast<float4*>(dsm + lay.cand);
     int4* segs = reinterpret_cast<int4*>(dsm + lay.segs);
     int4* rows = reinterpret_cast<int4*>(dsm + lay.rows);
@@ -674,7 +586,13 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     const GridInfo& g = a.g;
     for (int i = threadIdx.x; i < a.nrows; i += blockDim.x) rows[i] = a.rows[i];
     for (int i = threadIdx.x; i < nlmc(L) * (L + 1); i += blockDim.x) sh.kmat[i] = a.kmat[i];
-    if (threadIdx.x <= a.nr) sh.e2[threadIdx.x] = a.e2[threadIdx.x];
+    if (threadIdx.x <= a.nr) {
+        sh.e2[threadIdx.x] = a.e2[threadIdx.x];
+        sh.boff[threadIdx.x] = a.boff[threadIdx.x];
+    }
+    if (a.tab_ok)
+        for (int i = threadIdx.x; i < a.tab_n; i += blockDim.x) sh.stab[i] = a.tab[i];
+    if (threadIdx.x < kPairWarps) sh.ne[threadIdx.x][kMaxNr] = make_int2(0, 0x7fffffff);
     if (threadIdx.x < kShiftCodes) {
         const int c = threadIdx.x;
         sh.shift[c] = make_float4(shift_of(c & 3, g.L), shift_of((c >> 2) & 3, g.L),
@@ -686,28 +604,23 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
     }
     __syncthreads();
 
-    const int wblk = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = wblk / kW, warp = wblk % kW;
-    uint16_t* ulist = reinterpret_cast<uint16_t*>(dsm + lay.ulist) + (size_t)grp * a.cap;
-    uint8_t* ushell = dsm + lay.ushell + (size_t)grp * a.cap;
-    uint16_t* slist = reinterpret_cast<uint16_t*>(dsm + lay.slist) + (size_t)grp * a.cap;
-    float* part = reinterpret_cast<float*>(dsm + lay.part) + (size_t)grp * part_floats(a.nr, ncomp(L));
-    int* tpref = reinterpret_cast<int*>(dsm + lay.tpref) + (size_t)grp * (2 * a.nrows + 1);
-    int* tdc = reinterpret_cast<int*>(dsm + lay.tdc) + (size_t)grp * 2 * a.nrows;
-    int* tstart = reinterpret_cast<int*>(dsm + lay.tstart) + (size_t)grp * 2 * a.nrows;
-    int* tcode = reinterpret_cast<int*>(dsm + lay.tcode) + (size_t)grp * 2 * a.nrows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* tpref = reinterpret_cast<int*>(dsm + lay.tpref) + (size_t)warp * (2 * a.nrows + 1);
+    int* tdc = reinterpret_cast<int*>(dsm + lay.tdc) + (size_t)warp * 2 * a.nrows;
+    float* psum = reinterpret_cast<float*>(dsm + lay.psum) + (size_t)warp * a.nr * ncomp(L);
+    uint32_t* bucket = a.bucket + ((size_t)blockIdx.x * kPairWarps + warp) * a.boff[a.nr];
     // the x-window cut needs every cell sorted by x (binning flags bit 8 otherwise)
     const bool trim = a.trim != 0 && (*(volatile int*)a.err & 8) == 0;
-    int slot_org[R::F];
-#pragma unroll
-    for (int i = 0; i < R::F; ++i) slot_org[i] = R::origin(i, lane);
     uint32_t parity = 0;
     const int upr = (g.gx + a.run - 1) / a.run;   // units per row of cells
     const int ucat = upr * g.gy * g.gz;           // units per catalog
     const int nunits = ucat * a.ncat;
 
     for (;;) {
-        if (threadIdx.x == 0) sh.unit[0] = atomicAdd(a.work, 1);
+        if (threadIdx.x == 0) {
+            sh.unit[0] = atomicAdd(a.work, 1);
+            sh.next = 0;
+        }
         __syncthreads();
         const int u = sh.unit[0];
         if (u >= nunits) break;
@@ -723,15 +636,20 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
             __syncthreads();
             continue;
         }
-        if (wblk == 0)
+        if (warp == 0)
             build_segments(a, rows, cbase, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], &sh.unit[3], lane);
         __syncthreads();
-        const int nseg = sh.unit[1], total = sh.unit[2];
+        const int nseg = sh.unit[1];
         if (sh.unit[3] > a.cand_cap) {
             // a row longer than the staging buffer: neighbours straight from global memory
-            for (int p = pbeg + grp; p < pend; p += kG)
-                one_primary<L, false>(a, sh, cand, segs, nseg, 0, total, tpref, tdc, tstart, tcode, trim, ulist,
-                                      ushell, slist, part, p, cat, false, grp, warp, lane, slot_org);
+            for (;;) {
+                int p = 0;
+                if (lane == 0) p = pbeg + atomicAdd(&sh.next, 1);
+                p = __shfl_sync(kFull, p, 0);
+                if (p >= pend) break;
+                one_primary<L, false>(a, sh, cand, segs, nseg, 0, tpref, tdc, psum, bucket, trim, p, cat, false,
+                                      warp, lane);
+            }
             __syncthreads();
             continue;
         }
@@ -786,11 +704,17 @@ __global__ void __launch_bounds__(kG * kW * 32, 1) k_pair(const PairArgs a) {
                 }
                 parity ^= 1u;
             }
-            for (int p = pbeg + grp; p < pend; p += kG)
-                one_primary<L, true>(a, sh, cand, segs + s0, s1 - s0, zbase, ptotal, tpref, tdc, tstart, tcode,
-                                     trim, ulist, ushell, slist, part, p, cat, pass > 0, grp, warp, lane,
-                                     slot_org);
-            __syncthreads();   // both groups are done with this pass's staged points
+            for (;;) {
+                int p = 0;
+                if (lane == 0) p = pbeg + atomicAdd(&sh.next, 1);
+                p = __shfl_sync(kFull, p, 0);
+                if (p >= pend) break;
+                one_primary<L, true>(a, sh, cand, segs + s0, s1 - s0, zbase, tpref, tdc, psum, bucket, trim, p,
+                                     cat, pass > 0, warp, lane);
+            }
+            __syncthreads();   // every warp is done with this pass's staged points
+            if (threadIdx.x == 0) sh.next = 0;
+            __syncthreads();
             s0 = s1;
         }
         if (failed) break;
@@ -801,7 +725,7 @@ template <int L>
 void launch_L(const PairArgs& a, int nblocks, cudaStream_t s) {
     const size_t smem = pair_dynamic_smem(a);
     cudaFuncSetAttribute(k_pair<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pair<L><<<nblocks, kG * kW * 32, smem, s>>>(a);
+    k_pair<L><<<nblocks, kPairWarps * 32, smem, s>>>(a);
 }
 
 }  // namespace
@@ -831,7 +755,7 @@ size_t pair_static_smem(int lmax) {
 }
 
 size_t pair_dynamic_smem(const PairArgs& a) {
-    return pair_layout(a.cand_cap, a.nrows, a.cap, a.nr, ncomp(a.lmax)).total;
+    return pair_layout(a.cand_cap, a.nrows, a.nr, ncomp(a.lmax)).total;
 }
 
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s) {

@@ -240,22 +240,65 @@ def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
 
 
 @pytest.mark.parametrize("tuning", [
-    {},                 # staged neighbour cells, one list slice per primary
-    {3: 1024},          # staged, several list slices per primary
+    {},                 # staged neighbour cells, every bucket summed once per primary
+    {3: 2048},          # staged, buckets that fill and are summed during the scan
     {4: 256},           # neighbourhood larger than the staging buffer: staged in passes
-    {3: 1024, 4: 256},  # several staging passes, each with several list slices
+    {3: 2048, 4: 256},  # several staging passes, buckets summed during the scan
     {4: 16},            # rows longer than the staging buffer: global-memory path
-    {3: 1024, 4: 16},   # global-memory path with several list slices
+    {3: 2048, 4: 16},   # global-memory path, buckets summed during the scan
+    {5: 8},             # long work units (8 cells)
 ])
 def test_dense_primaries_staged_and_global_paths(torch_dev, tuning):
-    # ~1000 neighbours per primary: with a list capacity of 1024 every primary takes
-    # several slices; rows of ~30 points and neighbourhoods of ~3000 points per unit
+    # ~1000 neighbours per primary: with 2048 bucket entries per warp the buckets of the
+    # outer shells (a few hundred entries each) fill several times per primary; rows of
+    # ~30 points and neighbourhoods of ~3000 points per unit
     pos, w = _catalog(9000, 60.0, 61)
     edges = np.linspace(2.0, 18.0, 5)
     _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0, tuning=tuning)
     want, wcounts = oracle.npcf(pos, w, (3, 4), 3, edges, 60.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (3, 4), 3, 4)
+
+
+@pytest.mark.parametrize("edges", [
+    list(np.linspace(20.0, 160.0, 11)),           # the bench's shells: table on
+    [0.0, 2.0, 4.0, 8.0],                        # r_min = 0: the r2 > 0 change and edge 0 share bin 0
+    list(np.geomspace(0.02, 40.0, 17)),          # tiny inner shells: no table fits, computed shell
+])
+def test_shell_table_and_computed_shell_agree(torch_dev, edges):
+    # the pair kernel reads a candidate's shell from a table over bins of r2 when every
+    # bin holds at most one shell change (tuning key 8 = 1), else computes it; both apply
+    # the same exact FP32 rule, so the counts are the oracle's in both settings
+    box = 3.2 * edges[-1] + 1.0
+    pos = catalogs.lognormal_box(6000, box, 32, seed=81)
+    # points at exactly representable distances of 2, 4, 8 from a base point
+    base = np.array([box / 2, box / 2, box / 2], np.float32)
+    extra = [base]
+    for e in (2.0, 4.0, 8.0):
+        for ax in range(3):
+            p_ = base.copy(); p_[ax] += np.float32(e); extra.append(p_)
+    pos = np.concatenate([pos, np.array(extra, np.float32)])
+    w = np.ones(len(pos), np.float32)
+    want = oracle.pair_counts(pos, edges, box)
+    ref = None
+    for key8 in (1, 0):
+        _, z, counts = gpu_run(torch_dev, pos, w, (3,), 3, edges, box, tuning={8: key8})
+        assert np.array_equal(counts, want), key8
+        if ref is None:
+            ref = z
+        assert np.max(np.abs(z - ref)) <= 1e-5 * np.sqrt(np.mean(ref ** 2)), key8
+
+
+def test_sixteen_shells_minimum_buckets(torch_dev):
+    # 16 shells and 2048 bucket entries per warp: every shell's bucket holds the minimum
+    # of 128 entries, so nearly every bucket is summed many times per primary
+    pos, w = _catalog(6000, 70.0, 63)
+    edges = np.linspace(1.0, 20.0, 17)
+    want, wcounts = oracle.npcf(pos, w, (3,), 4, edges, 70.0)
+    for tuning in ({}, {3: 2048}):
+        _, got, counts = gpu_run(torch_dev, pos, w, (3,), 4, edges, 70.0, tuning=tuning)
+        assert np.array_equal(counts, wcounts), tuning
+        assert_orders_close(got, want, (3,), 4, 16)
 
 
 def test_non_periodic_signed_weights_staged_in_passes(torch_dev):
@@ -741,8 +784,8 @@ def test_autotune_picks_candidates_and_leaves_sums_empty(torch_dev):
     tp, tw = torch.from_numpy(pos).to(dev), torch.from_numpy(w).to(dev)
     est = NPCF(4, (3, 4), edges, 500.0)
     chosen = est.autotune(tp, tw)
-    assert chosen["cells_per_rmax"] in (2, 3, 4, 5, 6) and chosen["cell_run"] in (2, 3, 4)
-    assert chosen["pair_cap"] in (4096, 6144) and chosen["chunk"] >= 64
+    assert chosen["cells_per_rmax"] in (2, 3, 4, 5, 6) and chosen["cell_run"] in (2, 3, 4, 6)
+    assert chosen["pair_cap"] in (4096, 8192) and chosen["chunk"] >= 64
     assert est.batch_info()[0] == 0 and np.all(est.finalize() == 0)
     est.accumulate(tp, tw)
     got = est.finalize()
