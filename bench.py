@@ -431,7 +431,7 @@ def run_gpu_batch(args):
     chosen = tuner.autotune(pos[off[big]:off[big + 1]], w[off[big]:off[big + 1]])
     tuner.close()
     est = NPCF(lmax, orders, edges, box, prec)
-    for key, name in ((0, "cells_per_rmax"), (5, "cell_run"), (3, "pair_cap"), (2, "chunk")):
+    for key, name in ((0, "cells_per_rmax"), (5, "pair_chunk"), (3, "pair_cap"), (2, "chunk")):
         est.set_tuning(key, chosen[name])
 
     stream = torch.cuda.Stream(dev)
@@ -457,7 +457,7 @@ def run_gpu_batch(args):
     pos_p = torch.from_numpy(pos_h).pin_memory()
     w_p = torch.from_numpy(w_h).pin_memory()
     e2e = NPCF(lmax, orders, edges, box, prec)
-    for key, name in ((0, "cells_per_rmax"), (5, "cell_run"), (3, "pair_cap"), (2, "chunk")):
+    for key, name in ((0, "cells_per_rmax"), (5, "pair_chunk"), (3, "pair_cap"), (2, "chunk")):
         e2e.set_tuning(key, chosen[name])
     dpos = torch.empty_like(pos)
     dw = torch.empty_like(w)

@@ -95,7 +95,7 @@ npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr,
  *           the full catalog; npcf_pair_counts then counts the sample's pairs only).
  *           Without d_wprim, u_i = w_i and every primary's neighbours are counted,
  *           including those of primaries of weight 0 (which add nothing to zeta).
- *   n       number of particles, 0 <= n < 2^31
+ *   n       number of particles, 0 <= n < 2^26 (NPCF_EUNSUPPORTED above)
  *   stream  cudaStream_t to enqueue on (0 = legacy default stream)
  * Work is enqueued asynchronously; caller buffers must stay valid until the stream
  * reaches it. For box == 0 the call reads the bounding box back to the host (one
@@ -159,7 +159,7 @@ npcf_status npcf_pair_counts_batch(npcf_ctx* ctx, uint64_t* out, size_t out_len)
 
 /* Autotuner: runs the pipeline on the catalog (d_pos, d_w, n as in npcf_accumulate) for
  * candidate settings and keeps the fastest: pair kernel (median of three timed runs after a
- * warm-up) over cells per r_max {2, ..., 6} x cells per work unit {2, 3, 4, 6} x bucket
+ * warm-up) over cells per r_max {2, ..., 6} x primaries per chunk {8, 16, 32, 64} x bucket
  * entries per warp {4096, 8192}, then the contractions over primaries per chunk (1, 2, 4 or 8 waves of
  * chunks over the SMs). The accumulators must be empty (fresh context or npcf_reset) and
  * are reset afterwards. chosen (nullable, host int[4]) receives the settings: tuning keys
@@ -185,22 +185,21 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
                            uint32_t* counts);
 
 /* Tuning knobs (the autotuner sets these): key 0 = cells per r_max (1..8; the cell
- * side of the neighbour grid is about r_max / key0; 0, the default, picks 2, 3 or 5 from
- * the mean number of neighbours within r_max: below ~630, ~2,500, or more), key 2 = contraction primaries
+ * side of the neighbour grid is about r_max / key0; 0, the default, picks 2 below ~630
+ * mean neighbours within r_max and 3 above), key 2 = contraction primaries
  * per chunk, rounded up to a multiple of 64, for every contraction kernel (0 = automatic:
  * about n / (4 x SMs) for the 3PCF and 5PCF, n / SMs for the 4PCF), key 3 = pair kernel:
  * entries of each warp's per-shell buckets of accepted pairs (multiple of 256 in
  * 2048..65536, default 8192; every shell gets at least 128, the rest in proportion to
  * the shell volumes; a bucket that fills is summed early, so larger buckets mean fewer
- * reductions for dense primaries; device scratch of SMs x 16 x 4 bytes per entry), key 4 = cap on the
- * neighbour points staged in shared memory at a time (0 = as many as fit; a larger
- * neighbourhood is staged in several passes, and a work unit with a single row of cells
- * longer than the cap reads its neighbours from global memory), key 5 = x-adjacent cells
- * per pair-kernel work unit (1..8), key 6 = split-bf16 contraction: steps of 16 primaries
- * between drains of the tensor-memory accumulators into FP64 (>= 1; fewer steps bound the
- * accumulation error of the tensor cores more tightly), key 7 = pair kernel: cut each staged
- * row of neighbour cells to the primary's x-window (1, default) or scan whole rows (0),
- * key 8 = pair kernel: read the shell of each candidate from a table over bins of r2
+ * reductions for dense primaries; device scratch of SMs x 16 x 4 bytes per entry),
+ * key 5 = pair kernel: consecutive (cell-sorted) primaries per chunk that a block takes
+ * from the global counter (1..1024, default 16; small chunks keep a block's warps on
+ * nearby primaries, whose neighbourhoods then share L1), key 6 = split-bf16 contraction:
+ * steps of 16 primaries between drains of the tensor-memory accumulators into FP64 (>= 1;
+ * fewer steps bound the accumulation error of the tensor cores more tightly), key 7 = pair
+ * kernel: cut each neighbour row to the primary's x-window (1, default) or scan whole rows
+ * (0), key 8 = pair kernel: read the shell of each candidate from a table over bins of r2
  * (1, default, used when no bin holds two shell edges) or compute it from sqrt(r2) and the
  * edges (0); both apply the same exact FP32 rule. */
 npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);

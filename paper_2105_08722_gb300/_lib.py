@@ -229,7 +229,7 @@ class NPCF:
         chosen = np.zeros(4, dtype=np.int32)
         self._check(self._lib.npcf_autotune(self._h, _ptr(pos), _ptr(w), int(pos.shape[0]),
                                             _stream_handle(stream), chosen.ctypes.data))
-        return {"cells_per_rmax": int(chosen[0]), "cell_run": int(chosen[1]), "pair_cap": int(chosen[2]),
+        return {"cells_per_rmax": int(chosen[0]), "pair_chunk": int(chosen[1]), "pair_cap": int(chosen[2]),
                 "chunk": int(chosen[3])}
 
     def batch_info(self) -> Tuple[int, int]:

@@ -67,9 +67,8 @@ struct npcf_ctx {
 
     // cell-list tuning and geometry
     int cells_per_rmax = 0;    // 0: chosen per call from the catalog's density
-    int cell_run = 3;          // x-adjacent cells per pair-kernel work unit
+    int pair_chunk = 16;       // pair kernel: consecutive primaries per chunk a block takes
     int pair_cap = 8192;       // pair kernel: bucket entries per warp (all shells)
-    int stage_limit = 0;       // cap on staged neighbour points per cell (0 = as many as fit)
     int drain_steps = 2;       // tensor-core contraction: steps of 16 primaries per TMEM drain
     int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
     int use_stab = 1;          // pair kernel: shell by table lookup when the table is valid
@@ -500,15 +499,13 @@ npcf_status check_ctx(npcf_ctx* ctx) {
 // Grid and neighbour rows for the current geometry.
 // Cells per r_max when tuning key 0 is 0, from the mean number of neighbours within r_max
 // of a primary, nbar 4/3 pi r_max^3 (nbar: points per catalog / volume). Coarse cells mean
-// fewer neighbour rows per primary and per work unit, which is what a sparse catalog pays
-// for; in a dense one they make a unit's neighbourhood outgrow the staging buffer (staged
-// in several passes) and cut the rows to the x-window less tightly. Measured on the pair
-// kernel (log-normal and uniform catalogs from 137 to 3,400 neighbours per primary, lmax 4
-// and 5): 2 was best below ~600 neighbours, 3 from ~850 to ~1,700, 5 at ~3,400.
+// fewer neighbour rows per primary, which is what a sparse catalog pays for; finer ones cut
+// the rows to the x-window more tightly. Measured on the pair kernel: 2 was best below ~600
+// neighbours, 3 at ~3,400 (2 to 5 within 5 % there).
 int auto_cells_per_rmax(double points, double volume, double rmax) {
     if (!(volume > 0) || !(points > 0)) return 5;
     const double nb = points / volume * (4.0 / 3.0) * M_PI * rmax * rmax * rmax;
-    return nb < 630.0 ? 2 : (nb < 2500.0 ? 3 : 4);
+    return nb < 630.0 ? 2 : 3;
 }
 
 npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, int ncat, cudaStream_t s) {
@@ -576,8 +573,8 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     const long long n64 = off.back();
     const int ncat = (int)off.size() - 1;
     if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", n64);
-    if (n64 >= (int64_t(1) << 28))
-        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^28 points per call", n64);
+    if (n64 >= (int64_t(1) << 26))
+        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^26 points per call", n64);
     if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
     if (ctx->ncat != 0 && ctx->ncat != ncat)
         return fail(ctx, NPCF_EINVAL, "the accumulators hold %d catalogs, this call has %d (npcf_reset first)",
@@ -698,13 +695,7 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         pa.bucket = ctx->bucket.p;
     }
     {
-        // a run of cells must not make the periodic neighbour span wrap onto itself
-        int reach = 0;
-        for (size_t i = 0; i < ctx->rows_host.size(); i += 4)
-            reach = std::max({reach, std::abs(ctx->rows_host[i]), std::abs(ctx->rows_host[i + 1]),
-                              std::abs(ctx->rows_host[i + 2]), std::abs(ctx->rows_host[i + 3])});
-        pa.run = std::max(1, ctx->cell_run);
-        if (g.periodic) pa.run = std::max(1, std::min(pa.run, g.gx - 2 * reach));
+        pa.chunk = ctx->pair_chunk;
         // linear shell edges allow a direct shell estimate (corrected exactly on the device)
         // (shells narrower than 1e-3 r_max take the binary search)
         const double r0 = ctx->edges[0], w = (ctx->edges[ctx->nr] - r0) / ctx->nr;
@@ -742,14 +733,10 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         int dev = 0, optin = 0;
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        // each staged point takes 16 B
-        const long long room =
-            (long long)optin - (long long)pair_static_smem(ctx->lmax) - (long long)pair_dynamic_smem(pa) - 256;
-        if (room < 16 * 256)
-            return fail(ctx, NPCF_EINVAL, "pair kernel: %d neighbour rows leave no room for staging "
-                        "(shared memory limit %d B)", pa.nrows, optin);
-        pa.cand_cap = (int)std::min<long long>(room / 16, 65535);
-        if (ctx->stage_limit > 0) pa.cand_cap = std::min(pa.cand_cap, ctx->stage_limit);
+        const size_t need = pair_static_smem(ctx->lmax) + pair_dynamic_smem(pa);
+        if (need > (size_t)optin)
+            return fail(ctx, NPCF_EUNSUPPORTED, "pair kernel: %d neighbour rows need %zu B of shared memory "
+                        "(limit %d B)", pa.nrows, need, optin);
     }
     if (ctx->prec == NPCF_SPLIT_BF16) {
         int dev = 0, optin = 0;
@@ -970,8 +957,8 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
         (uintptr_t)ctx->partial.p, (uintptr_t)ctx->zeta.p, (uintptr_t)ctx->counts.p, (uintptr_t)ctx->sumw.p,
         (uintptr_t)ctx->d_off.p, (uintptr_t)ctx->chunks.p, (uintptr_t)ctx->cbeg.p, (uintptr_t)ctx->rows.p,
         (uintptr_t)ctx->chunks4.p, (uintptr_t)ctx->cbeg4.p, (uintptr_t)P.nchunk4,
-        (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.run, (uintptr_t)P.pa.bucket, (uintptr_t)P.pa.boff[ctx->nr],
-        (uintptr_t)P.pa.cand_cap, (uintptr_t)P.pa.trim, (uintptr_t)P.pa.tab_ok, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
+        (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.chunk, (uintptr_t)P.pa.bucket, (uintptr_t)P.pa.boff[ctx->nr],
+        (uintptr_t)P.pa.trim, (uintptr_t)P.pa.tab_ok, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
     for (long long v : off) sig.push_back((uintptr_t)v);
     if (ctx->gexec && sig == ctx->gsig) {
         CU(cudaGraphLaunch(ctx->gexec, s));
@@ -1250,15 +1237,15 @@ npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, i
         *ms = t[1];
         return NPCF_OK;
     };
-    const int keep[4] = {ctx->cells_per_rmax, ctx->cell_run, ctx->pair_cap, ctx->chunk_target};
+    const int keep[4] = {ctx->cells_per_rmax, ctx->pair_chunk, ctx->pair_cap, ctx->chunk_target};
     int best[4] = {keep[0], keep[1], keep[2], keep[3]};
     float best_ms = 1e30f;
-    // pair kernel: grid cell size, cells per work unit, neighbour-list capacity
+    // pair kernel: grid cell size, primaries per chunk, bucket entries per warp
     for (int k : {2, 3, 4, 5, 6})
-        for (int run : {2, 3, 4, 6})
+        for (int run : {8, 16, 32, 64})
             for (int cap : {4096, 8192}) {
                 ctx->cells_per_rmax = k;
-                ctx->cell_run = run;
+                ctx->pair_chunk = run;
                 ctx->pair_cap = cap;
                 float ms = 0.f;
                 if (stage_ms(1, &ms) != NPCF_OK) continue;   // e.g. no room to stage: skip
@@ -1270,7 +1257,7 @@ npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, i
                 }
             }
     ctx->cells_per_rmax = best[0];
-    ctx->cell_run = best[1];
+    ctx->pair_chunk = best[1];
     ctx->pair_cap = best[2];
     // contractions: primaries per chunk (waves of chunks over the SMs)
     best_ms = 1e30f;
@@ -1289,7 +1276,7 @@ npcf_status npcf_autotune(npcf_ctx* ctx, const float* d_pos, const float* d_w, i
     if (st != NPCF_OK) return st;
     if (best_ms >= 1e30f) {
         ctx->cells_per_rmax = keep[0];
-        ctx->cell_run = keep[1];
+        ctx->pair_chunk = keep[1];
         ctx->pair_cap = keep[2];
         ctx->chunk_target = keep[3];
         return fail(ctx, NPCF_EINVAL, "autotune: no candidate setting ran");
@@ -1484,13 +1471,9 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
                             "[2048, 65536]");
             ctx->pair_cap = value;
             return NPCF_OK;
-        case 4:
-            if (value < 0) return fail(ctx, NPCF_EINVAL, "staging limit must be >= 0");
-            ctx->stage_limit = value;
-            return NPCF_OK;
         case 5:
-            if (value < 1 || value > 8) return fail(ctx, NPCF_EINVAL, "cells per work unit in [1, 8]");
-            ctx->cell_run = value;
+            if (value < 1 || value > 1024) return fail(ctx, NPCF_EINVAL, "primaries per chunk in [1, 1024]");
+            ctx->pair_chunk = value;
             return NPCF_OK;
         case 6:
             if (value < 1) return fail(ctx, NPCF_EINVAL, "drain interval must be >= 1");

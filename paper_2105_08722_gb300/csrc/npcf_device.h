@@ -74,14 +74,13 @@ struct PairArgs {
     unsigned long long* counts;// [ncat][nr]
     int ncat;                  // catalogs; work units run over catalogs x cell runs
     int n;
-    int* work;                 // dynamic cell counter (zeroed by caller)
+    int* work;                 // global counter of primaries handed out in chunks (zeroed by caller)
     int* err;                  // error bits (2: a bounded wait gave up)
     int skip_zero;             // separate primary weights given: a primary of weight 0 is
                                // not evaluated (no a_lm, no counts); else every primary is
     uint32_t* bucket;          // [blocks][kPairWarps][boff[nr]] per-shell buckets of accepted pairs
     int boff[kMaxNr + 1];      // shell t's bucket: entries [boff[t], boff[t+1]) of a warp's region
-    int cand_cap;              // points the staging buffer holds
-    int run;                   // cells per work unit (x-adjacent)
+    int chunk;                 // primaries per chunk a block takes from the global counter
     int linear;                // edges are linear in r: shell estimated from sqrt(r2)
     float lin_r0, lin_inv_w;   // first edge and 1 / shell width of linear edges
     int tab_ok;                // the shell table below is valid (else the estimate above)

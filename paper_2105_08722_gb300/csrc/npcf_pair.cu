@@ -12,23 +12,21 @@
 // The Chebyshev basis keeps the conversion coefficients O(1), so FP32 sums do not lose
 // accuracy to cancellation at high l as plain powers z^k would.
 //
-// A persistent block of kPairWarps independent warps takes work units, runs of
-// x-adjacent cells of one catalog's grid, from a device counter. For a unit, warp 0 lists
-// the neighbour rows (rows of cells within r_max of the run) and one thread stages their
-// points into shared memory with bulk asynchronous copies, in passes of rows that fit the
-// buffer. Each warp then takes the unit's primaries one at a time from a shared counter
-// and runs the whole primary alone, so no warp waits for another between the phases of a
-// primary (the scan of one warp overlaps the accumulation of another):
-//   cut: every staged row is cut to the primary's x-window and the kept rows form one
-//        flat index space;
+// A persistent block of kPairWarps independent warps per SM takes chunks of consecutive
+// primaries (cell-sorted, so spatially close) from a global counter; each warp takes one
+// primary at a time from its block's chunks and runs it alone, so no warp waits for
+// another (the scan of one warp overlaps the accumulation of another, and there is no
+// barrier at which a block idles):
+//   cut: the primary's neighbour rows (cells within r_max, read as runs of the cell-sorted
+//        points) are cut to its x-window and form one flat index space;
 //   scan: each lane tests four candidates a step with the exact FP32 neighbour/shell
-//        rule; accepted pairs go straight to per-shell buckets (a private region of
-//        global scratch per warp, sized by shell volume and resident in L2) as
-//        (staged index, periodic shift code);
+//        rule, reading them through L1 (the neighbourhoods of a block's primaries
+//        overlap); accepted pairs go straight to per-shell buckets (a private region of
+//        global scratch per warp, sized by shell volume and resident in L2) as (point
+//        index, periodic shift code);
 //   accumulate: a full bucket, and at the end every non-empty one, is summed into the
 //        S_{m,k} of its shell in registers and reduced across lanes with a shuffle
-//        transpose-reduction; the per-shell sums are converted to a_lm (added to the
-//        earlier passes' a_lm, if any).
+//        transpose-reduction; the per-shell sums are converted to a_lm.
 #include "npcf_device.h"
 #include "npcf_rules.cuh"
 #include "npcf_warp.cuh"
@@ -76,26 +74,43 @@ __device__ __forceinline__ void harm_accumulate(float (&acc)[ncomp(L)], float x,
     }
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 21); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+// Two pairs at once (same sums): the two recurrences are independent chains, so their
+// instructions interleave and hide each other's latency.
+template <int L>
+__device__ __forceinline__ void harm_accumulate2(float (&acc)[ncomp(L)], float xa, float ya, float za, float wa,
+                                                 float xb, float yb, float zb, float wb) {
+    float ca[L + 1], sa[L + 1], ta[L + 1], cb[L + 1], sb[L + 1], tb[L + 1];
+    ca[0] = cb[0] = 1.f;
+    sa[0] = sb[0] = 0.f;
+#pragma unroll
+    for (int m = 1; m <= L; ++m) {
+        ca[m] = fmaf(ca[m - 1], xa, -sa[m - 1] * ya);
+        sa[m] = fmaf(sa[m - 1], xa, ca[m - 1] * ya);
+        cb[m] = fmaf(cb[m - 1], xb, -sb[m - 1] * yb);
+        sb[m] = fmaf(sb[m - 1], xb, cb[m - 1] * yb);
+    }
+    ta[0] = wa;
+    tb[0] = wb;
+    if (L >= 1) {
+        ta[1] = wa * za;
+        tb[1] = wb * zb;
+    }
+    const float za2 = za + za, zb2 = zb + zb;
+#pragma unroll
+    for (int k = 2; k <= L; ++k) {
+        ta[k] = fmaf(za2, ta[k - 1], -ta[k - 2]);
+        tb[k] = fmaf(zb2, tb[k - 1], -tb[k - 2]);
+    }
+#pragma unroll
+    for (int k = 0; k <= L; ++k) acc[k] += ta[k] + tb[k];
+#pragma unroll
+    for (int m = 1; m <= L; ++m) {
+#pragma unroll
+        for (int k = 0; k + m <= L; ++k) {
+            acc[s_index(L, m, k)] = fmaf(cb[m], tb[k], fmaf(ca[m], ta[k], acc[s_index(L, m, k)]));
+            acc[s_index(L, m, k) + 1] = fmaf(sb[m], tb[k], fmaf(sa[m], ta[k], acc[s_index(L, m, k) + 1]));
+        }
+    }
 }
 
 // The exact FP32 neighbour rule (same operations as shell_of in npcf_rules.cuh) followed
@@ -129,104 +144,32 @@ __device__ __forceinline__ int pair_shell_fast(const float4 pj, const float4 pi,
     return ok ? b : -1;
 }
 
-// The neighbour rows of a run of cells (x-adjacent, same y and z) as segments of the
-// cell-sorted point array: (global start, count, offset in the staging buffer, code).
-// code bits 0-5: periodic shift, 2 bits per axis; bits 6-18: the row's y cell; bits 19-31:
-// its z cell. Computed by one warp; the totals go to shared memory.
-__device__ void build_segments(const PairArgs& a, const int4* rows, int cbase, int cx, int cy, int cz, int run,
-                               int4* segs, int* out_nseg, int* out_total, int* out_maxseg, int lane) {
-    const GridInfo& g = a.g;
-    int nseg = 0, total = 0, maxseg = 0;
-    for (int r0 = 0; r0 < a.nrows; r0 += 32) {
-        const int r = r0 + lane;
-        int cnt[2] = {0, 0}, beg[2] = {0, 0}, code[2] = {0, 0}, ns = 0;
-        if (r < a.nrows) {
-            const int4 rw = rows[r];
-            int yy = cy + rw.x, zz = cz + rw.y, cyz = 0;
-            bool ok = true;
-            if (g.periodic) {
-                if (yy < 0) { yy += g.gy; cyz |= 1 << 2; } else if (yy >= g.gy) { yy -= g.gy; cyz |= 2 << 2; }
-                if (zz < 0) { zz += g.gz; cyz |= 1 << 4; } else if (zz >= g.gz) { zz -= g.gz; cyz |= 2 << 4; }
-            } else {
-                ok = yy >= 0 && yy < g.gy && zz >= 0 && zz < g.gz;
-            }
-            if (ok) {
-                const int base = cbase + (zz * g.gy + yy) * g.gx;
-                cyz |= (yy << 6) | (zz << 19);   // the row's cell (y, z) rides along for the x-window cut
-                int x0 = cx + rw.z, x1 = cx + run - 1 + rw.w;
-                if (g.periodic) {
-                    if (x0 < 0) {
-                        beg[ns] = (int)a.cell_start[base + x0 + g.gx];
-                        cnt[ns] = (int)a.cell_start[base + g.gx] - beg[ns];
-                        code[ns++] = cyz | 1;
-                        x0 = 0;
-                    }
-                    if (x1 >= g.gx) {
-                        beg[ns] = (int)a.cell_start[base];
-                        cnt[ns] = (int)a.cell_start[base + x1 - g.gx + 1] - beg[ns];
-                        code[ns++] = cyz | 2;
-                        x1 = g.gx - 1;
-                    }
-                } else {
-                    x0 = x0 < 0 ? 0 : x0;
-                    x1 = x1 >= g.gx ? g.gx - 1 : x1;
-                }
-                if (x0 <= x1 && ns < 2) {
-                    beg[ns] = (int)a.cell_start[base + x0];
-                    cnt[ns] = (int)a.cell_start[base + x1 + 1] - beg[ns];
-                    code[ns++] = cyz;
-                }
-            }
-        }
-        // drop empty segments, then a warp scan of segment and point counts
-        int k = 0, pts = 0;
-        for (int q = 0; q < ns; ++q)
-            if (cnt[q] > 0) {
-                beg[k] = beg[q];
-                cnt[k] = cnt[q];
-                code[k] = code[q];
-                pts += cnt[q];
-                maxseg = max(maxseg, cnt[q]);
-                ++k;
-            }
-        int ks = k, ps = pts;
-        for (int o = 1; o < 32; o <<= 1) {
-            int a1 = __shfl_up_sync(kFull, ks, o), a2 = __shfl_up_sync(kFull, ps, o);
-            if (lane >= o) { ks += a1; ps += a2; }
-        }
-        int sidx = nseg + ks - k, soff = total + ps - pts;
-        for (int q = 0; q < k; ++q) {
-            segs[sidx + q] = make_int4(beg[q], cnt[q], soff, code[q]);
-            soff += cnt[q];
-        }
-        nseg += __shfl_sync(kFull, ks, 31);
-        total += __shfl_sync(kFull, ps, 31);
-    }
-    for (int o = 16; o > 0; o >>= 1) maxseg = max(maxseg, __shfl_xor_sync(kFull, maxseg, o));
-    if (lane == 0) { *out_nseg = nseg; *out_total = total; *out_maxseg = maxseg; }
-}
 
 constexpr int kShiftCodes = 64;   // 2 bits per axis
 constexpr int kKC = 4;            // candidates per lane per scan step (independent chains)
 constexpr int kShellTab = kPairShellTab;
+// Chunk ring of a block (tagged entries). Each warp holds at most one position whose
+// chunk it has not read yet, and a position fetches at most one chunk (two ahead), so at
+// most kPairWarps + 2 chunks are live at a time, whatever the chunk size: 64 slots are
+// never overwritten before they are read.
+constexpr int kRing = 64;
+constexpr int kIdxBits = 26;      // bucket entry: point index (26 bits) | shift code << 26
 
-// Byte offsets of the pair kernel's dynamic shared memory (host and device agree).
+// Byte offsets of the pair kernel's dynamic shared memory (host and device agree): per
+// warp, the flat-index prefix of the kept rows of its current primary, each kept row's
+// (first point minus flat start, shift code), and the primary's per-shell sums.
 struct PairLayout {
-    size_t cand, segs, rows, tpref, tdc, psum, total;
+    size_t rows, tpref, tdc, psum, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline PairLayout pair_layout(int cand_cap, int nrows, int nr, int nc) {
+__host__ __device__ inline PairLayout pair_layout(int nrows, int nr, int nc) {
     PairLayout l;
-    l.cand = 0;
-    l.segs = align16(l.cand + (size_t)cand_cap * 16);
-    l.rows = align16(l.segs + (size_t)2 * nrows * 16);
-    // per warp: flat-index prefix and (staging offset minus prefix, shift code) of each
-    // kept row of the current primary, then the primary's per-shell sums
+    l.rows = 0;
     l.tpref = align16(l.rows + (size_t)nrows * 16);
     l.tdc = align16(l.tpref + (size_t)kPairWarps * (2 * nrows + 1) * 4);
-    l.psum = align16(l.tdc + (size_t)kPairWarps * 2 * nrows * 4);
+    l.psum = align16(l.tdc + (size_t)kPairWarps * 2 * nrows * 8);
     l.total = align16(l.psum + (size_t)kPairWarps * nr * nc * 4);
     return l;
 }
@@ -241,20 +184,20 @@ struct PairShared {
     int2 ne[kPairWarps][kMaxNr + 1]; // per warp and shell: next free entry, end of the bucket;
                                      // slot kMaxNr takes rejected candidates and never fills
     uint32_t tot[kPairWarps][kMaxNr];// accepted pairs of the warp's current primary, per shell
-    int unit[4];
-    int next;                        // next primary of the current pass (dynamic over warps)
+    unsigned long long ring[kRing];  // chunks of this block: chunk id << 32 | first primary
+    int take;                        // next position in this block's stream of primaries
 };
 
-// Both ends of the staged row at 'base' (n points, sorted by x) that fall in [vlo, vhi]:
-// the first index with x >= vlo and the first with x > vhi. The two searches run in
-// lockstep without branches: the answer is built bit by bit from the highest power of
-// two <= n, each bit kept if the predicate holds at the probed index.
-__device__ __forceinline__ int2 x_bounds(const float4* cand, int base, int n, float vlo, float vhi) {
+// Both ends of the cell-sorted row pts[base, base + n) (sorted by x) that fall in
+// [vlo, vhi]: the first index with x >= vlo and the first with x > vhi. The two searches
+// run in lockstep without branches: the answer is built bit by bit from the highest power
+// of two <= n, each bit kept if the predicate holds at the probed index.
+__device__ __forceinline__ int2 x_bounds(const float4* __restrict__ pts, int base, int n, float vlo, float vhi) {
     int a = 0, b = 0;
     if (n > 0) {
         for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
-            const float xa = cand[base + min(a + step, n) - 1].x;
-            const float xb = cand[base + min(b + step, n) - 1].x;
+            const float xa = __ldg(&pts[base + min(a + step, n) - 1].x);
+            const float xb = __ldg(&pts[base + min(b + step, n) - 1].x);
             a += (a + step <= n && xa < vlo) ? step : 0;
             b += (b + step <= n && !(xb > vhi)) ? step : 0;
         }
@@ -278,63 +221,107 @@ __device__ __forceinline__ int pair_shell_tab(const float4 pj, const float4 pi, 
     return r2 >= __int_as_float(e.z) ? e.y : e.x;
 }
 
-// The part of every staged row this primary can reach, as one flat index space over the
-// rows left non-empty (one warp): row s covers flat [tpref[s], tpref[s+1]), its staged
-// index is flat + (tdc[s] >> 6) and its periodic shift code tdc[s] & 63. With trim, a row
-// keeps only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus a margin) of the
-// primary, d_yz the distance from the primary to the row's (y, z) cell square; the exact
-// FP32 rule is applied to what remains. Rows are sorted by x (cells in x order, members
-// sorted by x). Returns the flat total; *nrow = rows kept.
+// The neighbourhood of primary pi in cell (cx, cy, cz) of catalog grid cbase, as one flat
+// index space over the non-empty parts of its neighbour rows (one warp; lane r takes rows
+// r, r + 32, ...). A neighbour row (cells within r_max of the primary's cell, same y and z)
+// is one or two runs of the cell-sorted points (two where the periodic grid wraps in x);
+// with trim, a run keeps only the points whose x lies within sqrt(r_max^2 - d_yz^2) (plus
+// a margin) of the primary, d_yz the distance from the primary to the row's (y, z) cell
+// square (runs are sorted by x: cells in x order, members sorted by x); the exact FP32
+// rule is applied to what remains. Kept run s covers flat [tpref[s], tpref[s+1]); its
+// points are pts[flat + tdc[s].x] and its periodic shift code is tdc[s].y. Returns the flat
+// total; *nrow = runs kept.
 template <int L>
-__device__ __forceinline__ int cut_rows(const PairArgs& a, const PairShared<L>& sh, const float4* cand,
-                                        const int4* segs, int nseg, int zbase, const float4 pi, int* tpref,
-                                        int* tdc, bool trim, int lane, int* nrow) {
+__device__ __forceinline__ int cut_rows(const PairArgs& a, const PairShared<L>& sh, const int4* rows, int cbase,
+                                        int cx, int cy, int cz, const float4 pi, int* tpref, int2* tdc, bool trim,
+                                        int lane, int* nrow) {
+    const GridInfo& g = a.g;
     const float R2 = sh.e2[a.nr], m = a.trim_margin, c = a.cell;
     int rows_acc = 0, pts_acc = 0;
-    for (int k0 = 0; k0 < nseg; k0 += 32) {
-        const int s = k0 + lane;
-        int lo = 0, hi = 0, start = 0, code = 0;
-        if (s < nseg) {
-            const int4 sg = segs[s];
-            hi = sg.y;
-            code = sg.w & 63;
-            if (trim) {
-                const float4 sf = sh.shift[code];
-                const int yy = (sg.w >> 6) & 8191, zz = (int)((unsigned)sg.w >> 19);
-                const float ylo = a.g.oy + (float)yy * c - sf.y - m, yhi = ylo + c + 2.f * m;
-                const float zlo = a.g.oz + (float)zz * c - sf.z - m, zhi = zlo + c + 2.f * m;
-                const float dy = fmaxf(0.f, fmaxf(ylo - pi.y, pi.y - yhi));
-                const float dz = fmaxf(0.f, fmaxf(zlo - pi.z, pi.z - zhi));
-                const float d2 = dy * dy + dz * dz;
-                if (d2 >= R2 * (1.f + 1e-5f)) {
-                    hi = 0;
+    for (int k0 = 0; k0 < a.nrows; k0 += 32) {
+        const int r = k0 + lane;
+        int beg[2] = {0, 0}, cnt[2] = {0, 0}, code[2] = {0, 0};
+        if (r < a.nrows) {
+            const int4 rw = rows[r];
+            int yy = cy + rw.x, zz = cz + rw.y, cyz = 0;
+            bool ok = true;
+            if (g.periodic) {
+                if (yy < 0) { yy += g.gy; cyz |= 1 << 2; } else if (yy >= g.gy) { yy -= g.gy; cyz |= 2 << 2; }
+                if (zz < 0) { zz += g.gz; cyz |= 1 << 4; } else if (zz >= g.gz) { zz -= g.gz; cyz |= 2 << 4; }
+            } else {
+                ok = yy >= 0 && yy < g.gy && zz >= 0 && zz < g.gz;
+            }
+            if (ok) {
+                const int base = cbase + (zz * g.gy + yy) * g.gx;
+                int x0 = cx + rw.z, x1 = cx + rw.w, ns = 0;
+                if (g.periodic) {
+                    if (x0 < 0) {
+                        beg[ns] = (int)__ldg(&a.cell_start[base + x0 + g.gx]);
+                        cnt[ns] = (int)__ldg(&a.cell_start[base + g.gx]) - beg[ns];
+                        code[ns++] = cyz | 1;
+                        x0 = 0;
+                    }
+                    if (x1 >= g.gx) {
+                        beg[ns] = (int)__ldg(&a.cell_start[base]);
+                        cnt[ns] = (int)__ldg(&a.cell_start[base + x1 - g.gx + 1]) - beg[ns];
+                        code[ns++] = cyz | 2;
+                        x1 = g.gx - 1;
+                    }
                 } else {
-                    const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
-                    const float xc = pi.x + sf.x;
-                    const int2 ab = x_bounds(cand, sg.z - zbase, sg.y, xc - h, xc + h);
-                    lo = ab.x;
-                    hi = ab.y;
+                    x0 = x0 < 0 ? 0 : x0;
+                    x1 = x1 >= g.gx ? g.gx - 1 : x1;
+                }
+                if (x0 <= x1 && ns < 2) {
+                    beg[ns] = (int)__ldg(&a.cell_start[base + x0]);
+                    cnt[ns] = (int)__ldg(&a.cell_start[base + x1 + 1]) - beg[ns];
+                    code[ns++] = cyz;
+                }
+                if (trim) {
+                    // the row's (y, z) cell square, and the primary's distance to it
+                    const float4 sf = sh.shift[cyz];
+                    const float ylo = g.oy + (float)yy * c - sf.y - m, yhi = ylo + c + 2.f * m;
+                    const float zlo = g.oz + (float)zz * c - sf.z - m, zhi = zlo + c + 2.f * m;
+                    const float dy = fmaxf(0.f, fmaxf(ylo - pi.y, pi.y - yhi));
+                    const float dz = fmaxf(0.f, fmaxf(zlo - pi.z, pi.z - zhi));
+                    const float d2 = dy * dy + dz * dz;
+                    if (d2 >= R2 * (1.f + 1e-5f)) {
+                        cnt[0] = cnt[1] = 0;
+                    } else {
+                        const float h = sqrtf(fmaxf(R2 * (1.f + 1e-5f) - d2, 0.f)) + m;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            if (cnt[q] > 0) {
+                                const float xc = pi.x + sh.shift[code[q]].x;
+                                const int2 ab = x_bounds(a.pts, beg[q], cnt[q], xc - h, xc + h);
+                                beg[q] += ab.x;
+                                cnt[q] = ab.y - ab.x;
+                            }
+                        }
+                    }
                 }
             }
-            start = sg.z - zbase + lo;
         }
-        const int cnt = hi - lo;
-        // inclusive prefix of (kept rows << 16 | points): points <= staging capacity < 2^16
-        const int v = ((cnt > 0 ? 1 : 0) << 16) | cnt;
-        int incl = v;
+        // inclusive prefixes of kept runs and of their points over the lanes
+        int kr = (cnt[0] > 0) + (cnt[1] > 0), kp = cnt[0] + cnt[1];
+        int ir = kr, ip = kp;
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
+            const int yr = __shfl_up_sync(kFull, ir, o), yp = __shfl_up_sync(kFull, ip, o);
+            if (lane >= o) {
+                ir += yr;
+                ip += yp;
+            }
         }
-        const int ex = incl - v;
-        if (cnt > 0) {
-            const int rb = rows_acc + (ex >> 16), pb = pts_acc + (ex & 0xffff);
-            tpref[rb] = pb;
-            tdc[rb] = ((start - pb) << 6) | code;   // staged start >= flat start
-        }
-        const int tot = __shfl_sync(kFull, incl, 31);
-        rows_acc += tot >> 16;
-        pts_acc += tot & 0xffff;
+        int rb = rows_acc + ir - kr, pb = pts_acc + ip - kp;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (cnt[q] > 0) {
+                tpref[rb] = pb;
+                tdc[rb] = make_int2(beg[q] - pb, code[q]);
+                ++rb;
+                pb += cnt[q];
+            }
+        rows_acc += __shfl_sync(kFull, ir, 31);
+        pts_acc += __shfl_sync(kFull, ip, 31);
     }
     if (lane == 0) tpref[rows_acc] = pts_acc;
     __syncwarp();
@@ -345,46 +332,50 @@ __device__ __forceinline__ int cut_rows(const PairArgs& a, const PairShared<L>& 
 // n accepted pairs of one shell into that shell's sums pw[0 .. ncomp(L)) (one warp; all
 // lanes call it together): the lanes take consecutive entries and accumulate
 // S_{m,k} = sum w (x + i y)^m T_k(z) in registers (T_k Chebyshev, m + k <= lmax); a
-// shuffle transpose-reduction adds the lanes' sums to pw. Staged entries hold (staged
-// index | shift code << 16): the separation is the one the neighbour rule accepted,
-// (p_j - p_i) - shift. Global entries hold the point index; the periodic image is then the
-// minimum image (accepted pairs are closer than L/3). Not inlined: a scan calls it only
-// when a bucket fills, and once per non-empty shell at the end of a primary.
-template <int L, bool STAGED>
-__device__ __noinline__ void sum_bucket(const float4* cand, const float4* pts, const float4* shift,
-                                        const uint32_t* e, int n, float4 pi, float boxL, float* pw, int lane) {
+// shuffle transpose-reduction adds the lanes' sums to pw. An entry holds (point index |
+// shift code << 26): the separation is the one the neighbour rule accepted,
+// (p_j - p_i) - shift. Not inlined: called once per non-empty shell at the end of a
+// primary, and during a scan only when a bucket fills.
+template <int L>
+__device__ __noinline__ void sum_bucket(const float4* __restrict__ pts, const float4* shift, const uint32_t* e,
+                                        int n, float4 pi, float* pw, int lane) {
     constexpr int NC = ncomp(L);
     using R = TR<NC>;
     float acc[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) acc[i] = 0.f;
-    const float invL = boxL > 0.f ? 1.f / boxL : 0.f;
-    uint32_t cur = lane < n ? __ldcg(e + lane) : 0u;
-    for (int i = lane; i - lane < n; i += 32) {
-        const uint32_t nxt = i + 32 < n ? __ldcg(e + i + 32) : 0u;
-        if (i < n) {
-            float dx, dy, dz, wj;
-            if (STAGED) {
-                const float4 pj = cand[cur & 0xffffu];
-                const float4 sf = shift[cur >> 16];
-                dx = (pj.x - pi.x) - sf.x;
-                dy = (pj.y - pi.y) - sf.y;
-                dz = (pj.z - pi.z) - sf.z;
-                wj = pj.w;
-            } else {
-                const float4 pj = pts[cur];
-                dx = pj.x - pi.x;
-                dy = pj.y - pi.y;
-                dz = pj.z - pi.z;
-                wj = pj.w;
-                dx = fmaf(-boxL, rintf(dx * invL), dx);
-                dy = fmaf(-boxL, rintf(dy * invL), dy);
-                dz = fmaf(-boxL, rintf(dz * invL), dz);
-            }
-            const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            harm_accumulate<L>(acc, dx * inv, dy * inv, dz * inv, wj);
+    auto sep = [&](uint32_t c, float& x, float& y, float& z, float& w) {
+        const float4 pj = __ldg(&pts[c & ((1u << kIdxBits) - 1u)]);
+        const float4 sf = shift[c >> kIdxBits];
+        const float dx = (pj.x - pi.x) - sf.x;
+        const float dy = (pj.y - pi.y) - sf.y;
+        const float dz = (pj.z - pi.z) - sf.z;
+        w = pj.w;
+        const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        x = dx * inv;
+        y = dy * inv;
+        z = dz * inv;
+    };
+    // Lane takes entries i and i + 32 of each block of 64, two pairs at once; the entries
+    // of the next block are in flight meanwhile (L2 latency).
+    uint32_t a0 = lane < n ? __ldcg(e + lane) : 0u, b0 = lane + 32 < n ? __ldcg(e + lane + 32) : 0u;
+    uint32_t a1 = lane + 64 < n ? __ldcg(e + lane + 64) : 0u, b1 = lane + 96 < n ? __ldcg(e + lane + 96) : 0u;
+    for (int i = lane; i - lane < n; i += 64) {
+        const uint32_t ca = a0, cb = b0;
+        a0 = a1;
+        b0 = b1;
+        a1 = i + 128 < n ? __ldcg(e + i + 128) : 0u;
+        b1 = i + 160 < n ? __ldcg(e + i + 160) : 0u;
+        if (i + 32 < n) {
+            float xa, ya, za, wa, xb, yb, zb, wb;
+            sep(ca, xa, ya, za, wa);
+            sep(cb, xb, yb, zb, wb);
+            harm_accumulate2<L>(acc, xa, ya, za, wa, xb, yb, zb, wb);
+        } else if (i < n) {
+            float xa, ya, za, wa;
+            sep(ca, xa, ya, za, wa);
+            harm_accumulate<L>(acc, xa, ya, za, wa);
         }
-        cur = nxt;
     }
     R::run(acc, lane);
 #pragma unroll
@@ -396,15 +387,13 @@ __device__ __noinline__ void sum_bucket(const float4* cand, const float4* pts, c
 }
 
 // Shell t's bucket of the warp into the shell's sums; the bucket is then empty.
-template <int L, bool STAGED>
-__device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh, const float4* cand,
-                                            const uint32_t* bucket, float* psum, int t, float4 pi, int warp,
-                                            int lane) {
+template <int L>
+__device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh, const uint32_t* bucket,
+                                            float* psum, int t, float4 pi, int warp, int lane) {
     __syncwarp();   // the entries written by every lane are visible
     const int b0 = sh.boff[t];
     const int n = sh.ne[warp][t].x - b0;
-    sum_bucket<L, STAGED>(cand, a.pts, sh.shift, bucket + b0, n, pi, a.g.periodic ? a.g.L : 0.f,
-                          psum + t * ncomp(L), lane);
+    sum_bucket<L>(a.pts, sh.shift, bucket + b0, n, pi, psum + t * ncomp(L), lane);
     if (lane == 0) {
         sh.tot[warp][t] += (uint32_t)n;
         sh.ne[warp][t].x = b0;
@@ -414,37 +403,33 @@ __device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh
 
 // Append one accepted pair per lane (shell b, -1 for none) to the warp's per-shell
 // buckets; a bucket that cannot take its lanes' entries is summed and emptied first.
-template <int L, bool STAGED>
-__device__ __forceinline__ void bucket_insert(const PairArgs& a, PairShared<L>& sh, const float4* cand,
-                                              uint32_t* bucket, float* psum, int b, uint32_t entry, float4 pi,
-                                              int warp, int lane, unsigned lt) {
+template <int L>
+__device__ __forceinline__ void bucket_insert(const PairArgs& a, PairShared<L>& sh, uint32_t* bucket, float* psum,
+                                              int b, uint32_t entry, float4 pi, int warp, int lane, unsigned lt) {
     const unsigned gm = __match_any_sync(kFull, b);
     const int rank = __popc(gm & lt);
     const int bi = b < 0 ? kMaxNr : b;
     int2 ne = sh.ne[warp][bi];
     if (__any_sync(kFull, ne.x + rank >= ne.y)) {   // rare: some lane's bucket is full
         const unsigned fullm = __reduce_or_sync(kFull, ne.x + rank >= ne.y ? 1u << bi : 0u);
-        for (unsigned mm = fullm; mm; mm &= mm - 1)
-            flush_shell<L, STAGED>(a, sh, cand, bucket, psum, __ffs(mm) - 1, pi, warp, lane);
+        for (unsigned mm = fullm; mm; mm &= mm - 1) flush_shell<L>(a, sh, bucket, psum, __ffs(mm) - 1, pi, warp, lane);
         ne = sh.ne[warp][bi];
     }
-    if (b >= 0) bucket[ne.x + rank] = entry;
+    if (b >= 0) __stcg(bucket + ne.x + rank, entry);
     __syncwarp();
     if (b >= 0 && rank == 0) sh.ne[warp][bi].x = ne.x + __popc(gm);
     __syncwarp();
 }
 
-// One primary, processed by one warp (no other warp waits for it). Staged: the rows of
-// the staging pass are cut to the primary's x-window and form one flat index space that
-// the lanes scan kKC candidates at a time with the exact FP32 neighbour rule; global: the
-// rows are read from global memory, 32 candidates a step. Accepted pairs go straight to
+// One primary, processed by one warp (no other warp waits for it): its neighbour rows cut
+// to its x-window form one flat index space that the lanes scan kKC candidates at a time
+// with the exact FP32 neighbour rule (candidates read through L1: the block's warps work
+// on nearby primaries, whose neighbourhoods overlap); accepted pairs go straight to
 // per-shell buckets (a private region of global scratch, L2-resident); a full bucket and,
-// at the end, every non-empty one are summed into the per-shell sums, which give a_lm
-// (added to the a_lm of earlier staging passes when add is set).
-template <int L, bool STAGED>
-__device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* cand, const int4* segs,
-                            int nseg, int zbase, int* tpref, int* tdc, float* psum, uint32_t* bucket, bool trim,
-                            int p, int cat, bool add, int warp, int lane) {
+// at the end, every non-empty one are summed into the per-shell sums, which give a_lm.
+template <int L>
+__device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const int4* rows, int* tpref, int2* tdc,
+                            float* psum, uint32_t* bucket, bool trim, int p, int warp, int lane) {
     constexpr int NC = ncomp(L);
     constexpr int NLM = nlmc(L);
     const int nr = a.nr;
@@ -453,13 +438,15 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* 
     // (every primary's pairs enter the counts) unless separate primary weights select a
     // sample of primaries: then a weight of 0 means "not in the sample".
     if (a.skip_zero && a.wp[p] == 0.f) {
-        if (!add) {
-            for (int i = lane; i < nr * NLM; i += 32) out[i] = make_float2(0.f, 0.f);
-            if (lane < nr) a.cnt[(size_t)p * nr + lane] = 0u;
-        }
+        for (int i = lane; i < nr * NLM; i += 32) out[i] = make_float2(0.f, 0.f);
+        if (lane < nr) a.cnt[(size_t)p * nr + lane] = 0u;
         return;
     }
-    const float4 pi = a.pts[p];
+    const GridInfo& g = a.g;
+    const float4 pi = __ldg(&a.pts[p]);
+    const int cell = (int)__ldg(&a.cell_of[p]);
+    const int cat = cell / g.ncell, lc = cell - cat * g.ncell;
+    const int cx = lc % g.gx, cy = (lc / g.gx) % g.gy, cz = lc / (g.gx * g.gy);
     for (int i = lane; i < nr * NC; i += 32) psum[i] = 0.f;
     if (lane < nr) {
         sh.ne[warp][lane] = make_int2(sh.boff[lane], sh.boff[lane + 1]);
@@ -469,79 +456,62 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* 
     const float e2lo = sh.e2[0], e2hi = sh.e2[nr];
     const bool tab = a.tab_ok != 0;
     const unsigned lt = (1u << lane) - 1u;
-    if (STAGED) {
-        int nrow = 0;
-        const int T = cut_rows<L>(a, sh, cand, segs, nseg, zbase, pi, tpref, tdc, trim, lane, &nrow);
-        int cursor = 0, srow = 0;
-        while (cursor < T) {
-            // Rows of the step's flat indices cursor + o, o < 32 kKC, without per-lane
-            // searches: lane i loads the end of row srow + i (rows are non-empty, so the
-            // ends increase strictly); a bitmap of the ends' offsets in the step gives each
-            // offset's row as srow + the ends at or below it. The step stops at the last
-            // loaded end, so no row beyond the loaded ones is met.
-            const int d = tpref[min(srow + 1 + lane, nrow)] - cursor;   // >= 1
-            const int lim = min(min(32 * kKC, T - cursor), __shfl_sync(kFull, d, 31));
-            unsigned W[kKC];
+    int nrow = 0;
+    const int T = cut_rows<L>(a, sh, rows, cat * g.ncell, cx, cy, cz, pi, tpref, tdc, trim, lane, &nrow);
+    int cursor = 0, srow = 0;
+    while (cursor < T) {
+        // Rows of the step's flat indices cursor + o, o < 32 kKC, without per-lane
+        // searches: lane i loads the end of run srow + i (runs are non-empty, so the ends
+        // increase strictly); a bitmap of the ends' offsets in the step gives each offset's
+        // run as srow + the ends at or below it. The step stops at the last loaded end, so
+        // no run beyond the loaded ones is met.
+        const int d = tpref[min(srow + 1 + lane, nrow)] - cursor;   // >= 1
+        const int lim = min(min(32 * kKC, T - cursor), __shfl_sync(kFull, d, 31));
+        unsigned W[kKC];
+#pragma unroll
+        for (int j = 0; j < kKC; ++j) {
+            const unsigned o = (unsigned)(d - 32 * j);
+            W[j] = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
+        }
+        const unsigned le = 0xffffffffu >> (31 - lane);   // offsets 32 j .. 32 j + lane
+        int q[kKC], b[kKC], code[kKC];
+        float4 sf[kKC];
+        int below = 0;
+#pragma unroll
+        for (int j = 0; j < kKC; ++j) {
+            const int row = min(srow + below + __popc(W[j] & le), nrow - 1);
+            below += __popc(W[j]);
+            const int2 dc = tdc[row];
+            q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + dc.x : p;
+            code[j] = dc.y;
+            sf[j] = sh.shift[code[j]];
+        }
+        float4 c[kKC];
+#pragma unroll
+        for (int j = 0; j < kKC; ++j) c[j] = __ldg(&a.pts[q[j]]);
+        if (tab) {
 #pragma unroll
             for (int j = 0; j < kKC; ++j) {
-                const unsigned o = (unsigned)(d - 32 * j);
-                W[j] = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
+                const int r = pair_shell_tab(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.stab, a.tab_scale, a.tab_n);
+                b[j] = (32 * j + lane < lim) ? r : -1;
             }
-            const unsigned le = 0xffffffffu >> (31 - lane);   // offsets 32 j .. 32 j + lane
-            int q[kKC], b[kKC], code[kKC];
-            float4 sf[kKC];
-            int below = 0;
+        } else {
 #pragma unroll
             for (int j = 0; j < kKC; ++j) {
-                const int row = min(srow + below + __popc(W[j] & le), nrow - 1);
-                below += __popc(W[j]);
-                const int dc = tdc[row];
-                q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + (dc >> 6) : 0;
-                code[j] = dc & 63;
-                sf[j] = sh.shift[code[j]];
-            }
-            float4 c[kKC];
-#pragma unroll
-            for (int j = 0; j < kKC; ++j) c[j] = cand[q[j]];
-            if (tab) {
-#pragma unroll
-                for (int j = 0; j < kKC; ++j) {
-                    const int r = pair_shell_tab(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.stab, a.tab_scale,
-                                                 a.tab_n);
-                    b[j] = (32 * j + lane < lim) ? r : -1;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kKC; ++j) {
-                    const int r = pair_shell_fast(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.e2, nr, e2lo, e2hi,
-                                                  a.linear, a.lin_r0, a.lin_inv_w);
-                    b[j] = (32 * j + lane < lim) ? r : -1;
-                }
-            }
-            srow += __popc(__ballot_sync(kFull, d <= lim));   // the row of cursor + lim
-            cursor += lim;
-#pragma unroll
-            for (int j = 0; j < kKC; ++j)
-                bucket_insert<L, true>(a, sh, cand, bucket, psum, b[j], (uint32_t)q[j] | ((uint32_t)code[j] << 16),
-                                       pi, warp, lane, lt);
-        }
-    } else {
-        for (int s = 0; s < nseg; ++s) {
-            const int4 sg = segs[s];
-            const float4 sf = sh.shift[sg.w & 63];
-            for (int k0 = 0; k0 < sg.y; k0 += 32) {
-                const int k = k0 + lane;
-                int b = -1;
-                if (k < sg.y)
-                    b = tab ? pair_shell_tab(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.stab, a.tab_scale, a.tab_n)
-                            : pair_shell_fast(a.pts[sg.x + k], pi, sf.x, sf.y, sf.z, sh.e2, nr, e2lo, e2hi,
-                                              a.linear, a.lin_r0, a.lin_inv_w);
-                bucket_insert<L, false>(a, sh, cand, bucket, psum, b, (uint32_t)(sg.x + k), pi, warp, lane, lt);
+                const int r = pair_shell_fast(c[j], pi, sf[j].x, sf[j].y, sf[j].z, sh.e2, nr, e2lo, e2hi, a.linear,
+                                              a.lin_r0, a.lin_inv_w);
+                b[j] = (32 * j + lane < lim) ? r : -1;
             }
         }
+        srow += __popc(__ballot_sync(kFull, d <= lim));   // the run of cursor + lim
+        cursor += lim;
+#pragma unroll
+        for (int j = 0; j < kKC; ++j)
+            bucket_insert<L>(a, sh, bucket, psum, b[j], (uint32_t)q[j] | ((uint32_t)code[j] << kIdxBits), pi, warp,
+                             lane, lt);
     }
     for (int t = 0; t < nr; ++t)
-        if (sh.ne[warp][t].x > sh.boff[t]) flush_shell<L, STAGED>(a, sh, cand, bucket, psum, t, pi, warp, lane);
+        if (sh.ne[warp][t].x > sh.boff[t]) flush_shell<L>(a, sh, bucket, psum, t, pi, warp, lane);
     __syncwarp();
 
     // ---- per-shell sums to a_lm
@@ -558,30 +528,41 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const float4* 
             re = fmaf(kk, sr, re);
             im = fmaf(kk, sim, im);
         }
-        if (add) {   // a later staging pass of the unit: a_lm is linear in the sums
-            const float2 o = out[i];
-            re += o.x;
-            im += o.y;
-        }
-        out[i] = make_float2(re, im);
+        __stcs(&out[i], make_float2(re, im));
     }
     if (lane < nr) {
         const uint32_t c = sh.tot[warp][lane];
-        a.cnt[(size_t)p * nr + lane] = add ? a.cnt[(size_t)p * nr + lane] + c : c;
+        a.cnt[(size_t)p * nr + lane] = c;
         if (c) atomicAdd(&a.counts[(size_t)cat * nr + lane], (unsigned long long)c);
     }
     __syncwarp();   // psum, ne and tot are reset by the next primary
 }
 
+// Bounded wait for chunk k of the block's stream (its ring entry carries the chunk id);
+// returns the chunk's first primary, or -1 if the wait gave up.
+__device__ __forceinline__ int chunk_base(const unsigned long long* ring, int k) {
+    const volatile unsigned long long* r = ring + (k % kRing);
+    for (int it = 0; it < (1 << 22); ++it) {
+        const unsigned long long v = *r;
+        if ((int)(v >> 32) == k) return (int)(v & 0xffffffffu);
+        __nanosleep(64);
+    }
+    return -1;
+}
+
+// Chunk k of the block's stream: its first primary from the global counter, published
+// with the chunk id.
+__device__ __forceinline__ void fetch_chunk(const PairArgs& a, unsigned long long* ring, int k) {
+    const int base = atomicAdd(a.work, a.chunk);
+    atomicExch(ring + (k % kRing), ((unsigned long long)(unsigned)k << 32) | (unsigned)base);
+}
+
 template <int L>
 __global__ void __launch_bounds__(kPairWarps * 32, 1) k_pair(const PairArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    const PairLayout lay = pair_layout(a.cand_cap, a.nrows, a.nr, ncomp(L));
-    float4* cand = reinterpret_cast<float4*>(dsm + lay.cand);
-    int4* segs = reinterpret_cast<int4*>(dsm + lay.segs);
+    const PairLayout lay = pair_layout(a.nrows, a.nr, ncomp(L));
     int4* rows = reinterpret_cast<int4*>(dsm + lay.rows);
     __shared__ PairShared<L> sh;
-    __shared__ __align__(8) uint64_t bar;
 
     const GridInfo& g = a.g;
     for (int i = threadIdx.x; i < a.nrows; i += blockDim.x) rows[i] = a.rows[i];
@@ -598,126 +579,43 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) k_pair(const PairArgs a) {
         sh.shift[c] = make_float4(shift_of(c & 3, g.L), shift_of((c >> 2) & 3, g.L),
                                   shift_of((c >> 4) & 3, g.L), 0.f);
     }
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (threadIdx.x < kRing) sh.ring[threadIdx.x] = ~0ull;   // no chunk yet
+    if (threadIdx.x == 0) sh.take = 0;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        fetch_chunk(a, sh.ring, 0);
+        fetch_chunk(a, sh.ring, 1);
+    }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* tpref = reinterpret_cast<int*>(dsm + lay.tpref) + (size_t)warp * (2 * a.nrows + 1);
-    int* tdc = reinterpret_cast<int*>(dsm + lay.tdc) + (size_t)warp * 2 * a.nrows;
+    int2* tdc = reinterpret_cast<int2*>(dsm + lay.tdc) + (size_t)warp * 2 * a.nrows;
     float* psum = reinterpret_cast<float*>(dsm + lay.psum) + (size_t)warp * a.nr * ncomp(L);
     uint32_t* bucket = a.bucket + ((size_t)blockIdx.x * kPairWarps + warp) * a.boff[a.nr];
     // the x-window cut needs every cell sorted by x (binning flags bit 8 otherwise)
     const bool trim = a.trim != 0 && (*(volatile int*)a.err & 8) == 0;
-    uint32_t parity = 0;
-    const int upr = (g.gx + a.run - 1) / a.run;   // units per row of cells
-    const int ucat = upr * g.gy * g.gz;           // units per catalog
-    const int nunits = ucat * a.ncat;
 
+    // The block's warps take positions of the block's stream of primaries, chunks of
+    // a.chunk consecutive (cell-sorted, so nearby) primaries from the global counter. The
+    // warp that takes a chunk's first position fetches the chunk two ahead, so a chunk is
+    // normally published long before a warp needs it.
     for (;;) {
-        if (threadIdx.x == 0) {
-            sh.unit[0] = atomicAdd(a.work, 1);
-            sh.next = 0;
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&sh.take, 1);
+        t = __shfl_sync(kFull, t, 0);
+        const int k = t / a.chunk, r = t - k * a.chunk;
+        if (r == 0 && lane == 0) fetch_chunk(a, sh.ring, k + 2);
+        int base = 0;
+        if (lane == 0) base = chunk_base(sh.ring, k);
+        base = __shfl_sync(kFull, base, 0);
+        if (base < 0) {   // gave up waiting (never expected): report and stop
+            if (lane == 0) atomicOr(a.err, 2);
+            break;
         }
-        __syncthreads();
-        const int u = sh.unit[0];
-        if (u >= nunits) break;
-        // unit u: catalog u / ucat, then a run of x-adjacent cells of that catalog's grid
-        const int cat = u / ucat, uc = u - cat * ucat;
-        const int cbase = cat * g.ncell;
-        const int row = uc / upr, cx = (uc % upr) * a.run;
-        const int run = min(a.run, g.gx - cx);
-        const int cy = row % g.gy, cz = row / g.gy;
-        const int c0 = cbase + (cz * g.gy + cy) * g.gx + cx;
-        const int pbeg = (int)a.cell_start[c0], pend = (int)a.cell_start[c0 + run];
-        if (pbeg == pend) {
-            __syncthreads();
-            continue;
-        }
-        if (warp == 0)
-            build_segments(a, rows, cbase, cx, cy, cz, run, segs, &sh.unit[1], &sh.unit[2], &sh.unit[3], lane);
-        __syncthreads();
-        const int nseg = sh.unit[1];
-        if (sh.unit[3] > a.cand_cap) {
-            // a row longer than the staging buffer: neighbours straight from global memory
-            for (;;) {
-                int p = 0;
-                if (lane == 0) p = pbeg + atomicAdd(&sh.next, 1);
-                p = __shfl_sync(kFull, p, 0);
-                if (p >= pend) break;
-                one_primary<L, false>(a, sh, cand, segs, nseg, 0, tpref, tdc, psum, bucket, trim, p, cat, false,
-                                      warp, lane);
-            }
-            __syncthreads();
-            continue;
-        }
-        // Staged in passes of consecutive rows that fit the staging buffer (one pass unless
-        // the unit's neighbourhood is larger); each pass adds its sums to the primaries'
-        // a_lm and counts. A pass of the rows [s0, s1) is staged with bulk asynchronous
-        // copies (one mbarrier); row s sits at sg.z - segs[s0].z in the buffer.
-        bool failed = false;
-        for (int s0 = 0, pass = 0; pass == 0 || s0 < nseg; ++pass) {
-            // every thread plans the pass (the same search over the shared row list)
-            int s1 = s0, ptotal = 0;
-            const int zbase = s0 < nseg ? segs[s0].z : 0;
-            if (s0 < nseg) {
-                // the most rows from s0 whose points fit (staging offsets increase)
-                int lo = s0 + 1, n = nseg - s0 - 1;   // answer in [s0 + 1, nseg]
-                while (n > 0) {
-                    const int half = n >> 1;
-                    const int4 sg = segs[lo + half];
-                    if (sg.z + sg.y - zbase <= a.cand_cap) {
-                        lo += half + 1;
-                        n -= half + 1;
-                    } else {
-                        n = half;
-                    }
-                }
-                s1 = lo;
-                ptotal = segs[s1 - 1].z + segs[s1 - 1].y - zbase;
-            }
-            if (threadIdx.x == 0 && ptotal > 0) {
-                const uint32_t b = smem_u32(&bar);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                             "r"((uint32_t)ptotal * 16u)
-                             : "memory");
-                for (int q = s0; q < s1; ++q) {
-                    const int4 sg = segs[q];
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                        "[%3];" ::"r"(smem_u32(cand + (sg.z - zbase))),
-                        "l"(a.pts + sg.x), "r"((uint32_t)sg.y * 16u), "r"(b)
-                        : "memory");
-                }
-            }
-            if (ptotal > 0) {
-                const bool ok = mbar_wait_bounded(smem_u32(&bar), parity);
-                // the whole block leaves together if any thread's wait gave up
-                if (__syncthreads_or(ok ? 0 : 1)) {
-                    if (threadIdx.x == 0) atomicOr(a.err, 2);
-                    mbar_wait_bounded(smem_u32(&bar), parity);  // give in-flight copies a last chance to land
-                    failed = true;
-                    break;
-                }
-                parity ^= 1u;
-            }
-            for (;;) {
-                int p = 0;
-                if (lane == 0) p = pbeg + atomicAdd(&sh.next, 1);
-                p = __shfl_sync(kFull, p, 0);
-                if (p >= pend) break;
-                one_primary<L, true>(a, sh, cand, segs + s0, s1 - s0, zbase, tpref, tdc, psum, bucket, trim, p,
-                                     cat, pass > 0, warp, lane);
-            }
-            __syncthreads();   // every warp is done with this pass's staged points
-            if (threadIdx.x == 0) sh.next = 0;
-            __syncthreads();
-            s0 = s1;
-        }
-        if (failed) break;
+        if (base >= a.n) break;   // past the last primary: so is every later chunk
+        const int p = base + r;
+        if (p >= a.n) continue;
+        one_primary<L>(a, sh, rows, tpref, tdc, psum, bucket, trim, p, warp, lane);
     }
 }
 
@@ -755,7 +653,7 @@ size_t pair_static_smem(int lmax) {
 }
 
 size_t pair_dynamic_smem(const PairArgs& a) {
-    return pair_layout(a.cand_cap, a.nrows, a.nr, ncomp(a.lmax)).total;
+    return pair_layout(a.nrows, a.nr, ncomp(a.lmax)).total;
 }
 
 void launch_pair(const PairArgs& a, int nblocks, cudaStream_t s) {

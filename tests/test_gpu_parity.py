@@ -240,18 +240,16 @@ def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
 
 
 @pytest.mark.parametrize("tuning", [
-    {},                 # staged neighbour cells, every bucket summed once per primary
-    {3: 2048},          # staged, buckets that fill and are summed during the scan
-    {4: 256},           # neighbourhood larger than the staging buffer: staged in passes
-    {3: 2048, 4: 256},  # several staging passes, buckets summed during the scan
-    {4: 16},            # rows longer than the staging buffer: global-memory path
-    {3: 2048, 4: 16},   # global-memory path, buckets summed during the scan
-    {5: 8},             # long work units (8 cells)
+    {},                 # every bucket summed once per primary
+    {3: 2048},          # buckets that fill and are summed during the scan
+    {5: 1},             # one primary per chunk
+    {5: 1000, 3: 2048}, # chunks larger than a block's share, buckets summed during the scan
+    {7: 0},             # whole rows, no x-window cut
+    {0: 1},             # one cell per r_max: long rows
 ])
-def test_dense_primaries_staged_and_global_paths(torch_dev, tuning):
+def test_dense_primaries_tuning_variants(torch_dev, tuning):
     # ~1000 neighbours per primary: with 2048 bucket entries per warp the buckets of the
-    # outer shells (a few hundred entries each) fill several times per primary; rows of
-    # ~30 points and neighbourhoods of ~3000 points per unit
+    # outer shells (a few hundred entries each) fill several times per primary
     pos, w = _catalog(9000, 60.0, 61)
     edges = np.linspace(2.0, 18.0, 5)
     _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0, tuning=tuning)
@@ -301,14 +299,14 @@ def test_sixteen_shells_minimum_buckets(torch_dev):
         assert_orders_close(got, want, (3,), 4, 16)
 
 
-def test_non_periodic_signed_weights_staged_in_passes(torch_dev):
-    # data-minus-randoms style weights in an open box; a staging limit of 128 points splits
-    # every unit's neighbourhood into many passes, also at the box faces
+def test_non_periodic_signed_weights(torch_dev):
+    # data-minus-randoms style weights in an open box (rows cut at the box faces), with the
+    # default chunks and with chunks of 3 primaries
     pos, w = _catalog(4000, 60.0, 62)
     w = np.where(np.arange(len(w)) % 4 == 0, np.float32(-0.25), w).astype(np.float32)
     edges = np.linspace(3.0, 15.0, 5)
     want, wcounts = oracle.npcf(pos, w, (3, 4), 3, edges, 0.0)
-    for tuning in ({}, {4: 128}):
+    for tuning in ({}, {5: 3}):
         _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 0.0, tuning=tuning)
         assert np.array_equal(counts, wcounts), tuning
         assert_orders_close(got, want, (3, 4), 3, 4)
@@ -784,7 +782,7 @@ def test_autotune_picks_candidates_and_leaves_sums_empty(torch_dev):
     tp, tw = torch.from_numpy(pos).to(dev), torch.from_numpy(w).to(dev)
     est = NPCF(4, (3, 4), edges, 500.0)
     chosen = est.autotune(tp, tw)
-    assert chosen["cells_per_rmax"] in (2, 3, 4, 5, 6) and chosen["cell_run"] in (2, 3, 4, 6)
+    assert chosen["cells_per_rmax"] in (2, 3, 4, 5, 6) and chosen["pair_chunk"] in (8, 16, 32, 64)
     assert chosen["pair_cap"] in (4096, 8192) and chosen["chunk"] >= 64
     assert est.batch_info()[0] == 0 and np.all(est.finalize() == 0)
     est.accumulate(tp, tw)
