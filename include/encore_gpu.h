@@ -14,7 +14,8 @@
  *   3. the raw multiplets
  *         zeta^B_L += sum_i u_i sum_M E(L) C^L_M prod_k a^{b_k}_{l_k m_k}(s_i),
  *      Eq. (NPCF-mult-discrete-binned-estimator) without 1/V, summed with the
- *      m_{N-1} >= 0 halving of App. B (Eq. simple-NPCF-summation), for N = 3, 4, 5.
+ *      m_{N-1} >= 0 halving of App. B (Eq. simple-NPCF-summation), for N = 3, 4, 5, 6
+ *      (for N = 6 the halving runs over the second intermediate m123).
  *
  * Conventions shared with the documentation:
  *  - Y_lm orthonormal, Condon-Shortley phase (Sec. 2.1). Separation r_j - s_i.
@@ -27,7 +28,7 @@
  *  - Multiplets L: l1 outer, then l2, [l12], l3, [l123], l4, [l5], last index fastest;
  *    N=3: (l, l), l = 0..lmax; N=4: |l1-l2| <= l3 <= min(l1+l2, lmax);
  *    N=5: |l1-l2| <= l12 <= l1+l2, |l12-l3| <= l4 <= min(l12+l3, lmax);
- *    N=6 (host tables only, npcf_multiplets): |l1-l2| <= l12 <= l1+l2,
+ *    N=6: |l1-l2| <= l12 <= l1+l2,
  *    |l12-l3| <= l123 <= l12+l3, |l123-l4| <= l5 <= min(l123+l4, lmax).
  *    Parity-even only (sum of principal l even) unless allparity != 0 (Table 1).
  *  - Output of npcf_finalize: orders ascending; for each order an array
@@ -73,7 +74,10 @@ typedef enum {
 /* Create a context.
  *   lmax        maximum l of every principal angular momentum, 0 <= lmax <= 10
  *               (Sec. 3.1: the l_i <= lmax truncation).
- *   order_mask  bit N set to compute the N-point function; N in {3, 4, 5}.
+ *   order_mask  bit N set to compute the N-point function; N in {3, 4, 5, 6}. The 6PCF
+ *               takes at most 8 shells (NPCF_EUNSUPPORTED above; with fewer than 5 it has
+ *               no bin tuple and an empty output) and (lmax + 1)^2 x nr x 264 bytes of
+ *               shared memory (NPCF_EUNSUPPORTED beyond the device's limit).
  *   nr, edges   nr radial shells (1 <= nr <= 16) with host edges[nr+1] strictly
  *               increasing, edges[0] >= 0 (the binning functions Theta^b, Sec. 3.2).
  *   box         > 0: periodic cube of that side (Table 1 "periodic"); positions must
@@ -273,8 +277,8 @@ npcf_status npcf_gaunt(int N, const int* L1, const int* L2, const int* L3, doubl
  * npcf_finalize (lexicographic in the l's with the last entry fastest, the order of the
  * edge-correction matrices of the mock-catalog figures, Sec. 5.4). Layout per multiplet: {l, l},
  * {l1, l2, l3}, {l1, l2, l12, l3, l4}, {l1, l2, l12, l3, l123, l4, l5}. *count receives
- * their number; out (nullable) receives count x (2, 3, 5, 7) ints. Host-only. The 6PCF
- * has no GPU contraction yet: npcf_create takes orders 3 to 5. lmax in [0, 10]. */
+ * their number; out (nullable) receives count x (2, 3, 5, 7) ints. Host-only. lmax in
+ * [0, 10]. */
 npcf_status npcf_multiplets(int N, int lmax, int allparity, int* count, int* out);
 
 /* Coupling coefficient C^L_M of Eq. basis-coupling (Eq. N=3-coeff and N=4-coeff for N = 3,

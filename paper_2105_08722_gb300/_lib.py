@@ -278,7 +278,7 @@ class NPCF:
     def layout(self, order: int) -> Tuple[np.ndarray, np.ndarray]:
         nl, nb = _i(), _i()
         self._check(self._lib.npcf_layout(self._h, order, ctypes.byref(nl), ctypes.byref(nb), None, None))
-        width = {3: 2, 4: 3, 5: 5}[order]
+        width = {3: 2, 4: 3, 5: 5, 6: 7}[order]
         lam = np.zeros(nl.value * width, dtype=np.int32)
         bins = np.zeros(nb.value * (order - 1), dtype=np.int32)
         self._check(self._lib.npcf_layout(self._h, order, ctypes.byref(nl), ctypes.byref(nb),

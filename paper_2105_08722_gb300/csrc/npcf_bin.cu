@@ -121,33 +121,69 @@ __global__ void k_scatter(BinArgs a) {
     a.cell_of[k] = c;
 }
 
-// Order each cell's members by (x, input index) (insertion sort; cells hold tens of
-// points). Cells above the bound stay in scatter order and flag error bit 8, which turns
-// the pair kernel's x-window cut off.
-__global__ void k_cell_order(BinArgs a) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.g.ncell * a.ncat) return;
-    uint32_t s0 = a.start[c], s1 = a.start[c + 1];
-    if (s1 - s0 > 4096u) {  // keep the quadratic sort bounded
-        atomicOr(a.err, 8);
-        return;
-    }
-    for (uint32_t k = s0 + 1; k < s1; ++k) {
-        uint32_t key = a.idx[k];
-        float4 p = a.pts[k];
-        float u = a.wp[k];
-        uint32_t j = k;
-        while (j > s0) {
-            const float xj = a.pts[j - 1].x;
-            if (!(xj > p.x || (xj == p.x && a.idx[j - 1] > key))) break;
-            a.idx[j] = a.idx[j - 1];
-            a.pts[j] = a.pts[j - 1];
-            a.wp[j] = a.wp[j - 1];
-            --j;
+// Order each cell's members by (x, input index), one warp per cell: the members are
+// loaded into shared memory and each goes to its rank among the cell's keys (the keys are
+// distinct: the input index breaks ties), written back in order. Cells longer than
+// kSortCap are ordered by insertion sort in place by one lane; above 4096 members they stay
+// in scatter order and flag error bit 8, which turns the pair kernel's x-window cut off.
+constexpr int kSortWarps = 4;
+constexpr int kSortCap = 384;
+
+__device__ __forceinline__ bool key_less(float xa, uint32_t ia, float xb, uint32_t ib) {
+    return xa < xb || (xa == xb && ia < ib);
+}
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_cell_order(BinArgs a) {
+    __shared__ float4 sp[kSortWarps][kSortCap];
+    __shared__ uint32_t si[kSortWarps][kSortCap];
+    __shared__ float sw[kSortWarps][kSortCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncells = a.g.ncell * a.ncat;
+    for (int c = blockIdx.x * kSortWarps + warp; c < ncells; c += gridDim.x * kSortWarps) {
+        const uint32_t s0 = a.start[c], s1 = a.start[c + 1];
+        const int n = (int)(s1 - s0);
+        if (n <= 1) continue;
+        if (n <= kSortCap) {
+            for (int i = lane; i < n; i += 32) {
+                sp[warp][i] = a.pts[s0 + i];
+                si[warp][i] = a.idx[s0 + i];
+                sw[warp][i] = a.wp[s0 + i];
+            }
+            __syncwarp();
+            for (int i = lane; i < n; i += 32) {
+                const float xi = sp[warp][i].x;
+                const uint32_t ii = si[warp][i];
+                int rank = 0;
+                for (int j = 0; j < n; ++j) rank += key_less(sp[warp][j].x, si[warp][j], xi, ii) ? 1 : 0;
+                a.pts[s0 + rank] = sp[warp][i];
+                a.idx[s0 + rank] = ii;
+                a.wp[s0 + rank] = sw[warp][i];
+            }
+            __syncwarp();
+            continue;
         }
-        a.idx[j] = key;
-        a.pts[j] = p;
-        a.wp[j] = u;
+        if (lane != 0) continue;
+        if (n > 4096) {  // keep the quadratic sort bounded
+            atomicOr(a.err, 8);
+            continue;
+        }
+        for (uint32_t k = s0 + 1; k < s1; ++k) {
+            const uint32_t key = a.idx[k];
+            const float4 p = a.pts[k];
+            const float u = a.wp[k];
+            uint32_t j = k;
+            while (j > s0) {
+                const float xj = a.pts[j - 1].x;
+                if (!key_less(p.x, key, xj, a.idx[j - 1])) break;
+                a.idx[j] = a.idx[j - 1];
+                a.pts[j] = a.pts[j - 1];
+                a.wp[j] = a.wp[j - 1];
+                --j;
+            }
+            a.idx[j] = key;
+            a.pts[j] = p;
+            a.wp[j] = u;
+        }
     }
 }
 
@@ -158,12 +194,13 @@ void launch_bbox(const float* pos, int n, float* part, int nblocks, cudaStream_t
 }
 
 void launch_bin(const BinArgs& a, cudaStream_t s) {
-    int nb = (a.n + 255) / 256;
-    if (a.n > 0) k_assign<<<nb, 256, 0, s>>>(a);
+    const int nbp = (a.n + 255) / 256;
+    if (a.n > 0) k_assign<<<nbp, 256, 0, s>>>(a);
     const int cells = a.g.ncell * a.ncat;
     k_scan<<<1, 1024, 0, s>>>(a.count, a.start, a.cursor, cells);
-    if (a.n > 0) k_scatter<<<nb, 256, 0, s>>>(a);
-    k_cell_order<<<(cells + 127) / 128, 128, 0, s>>>(a);
+    if (a.n > 0) k_scatter<<<nbp, 256, 0, s>>>(a);
+    const int nb = (cells + kSortWarps - 1) / kSortWarps;
+    k_cell_order<<<nb < 4096 ? nb : 4096, kSortWarps * 32, 0, s>>>(a);
 }
 
 }  // namespace npcf

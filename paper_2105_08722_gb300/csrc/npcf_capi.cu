@@ -104,6 +104,11 @@ struct npcf_ctx {
     int c5npart = 0;
     DevBuf<int2> c5segs12, c5segs34;
     int c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
+    // 6PCF contraction tables
+    DevBuf<int4> c6lam, c6lam2, c6terms1, c6terms2, c6terms3;
+    DevBuf<int2> c6seg1, c6seg2, c6seg3, c6items;
+    DevBuf<int> c6binq;
+    int c6nitem = 0;
 
     // working buffers
     DevBuf<float4> pts;
@@ -376,6 +381,103 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
     return NPCF_OK;
 }
 
+// 6PCF tables (npcf_contract6.cu): per multiplet L = (l1, l2, l12, l3, l123, l4, l5) the
+// P12 terms of every m12, and for every m123 >= 0 the Q terms (m12, m3) and the P45 terms
+// (m4, m5), with the 3-j symbols of Eq. basis-coupling and the phases (-1)^{l12 - m12}
+// (in the P12 terms) and (-1)^{l123 - m123} (in the Q terms); harmonic rows lm = l^2 + l + m.
+npcf_status setup_c6_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
+    const int nr = ctx->nr, nb = o.n_bins();
+    if (nb == 0) return NPCF_OK;
+    if (nr > 8) return fail(ctx, NPCF_EUNSUPPORTED, "6PCF: %d shells (the contraction takes at most 8)", nr);
+    {
+        Contract6Args c{};
+        c.lmax = ctx->lmax;
+        c.nr = nr;
+        int dev = 0, optin = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (contract6_smem_bytes(c) + 1024 > (size_t)optin)
+            return fail(ctx, NPCF_EUNSUPPORTED, "6PCF: lmax %d with %d shells needs %zu B of shared memory",
+                        ctx->lmax, nr, contract6_smem_bytes(c));
+    }
+    auto lmf = [](int l, int m) { return l * l + l + m; };
+    auto bits = [](double v) {
+        const float f = (float)v;
+        int b;
+        std::memcpy(&b, &f, 4);
+        return b;
+    };
+    std::vector<int4> lam, lam2, t1, t2, t3;
+    std::vector<int2> seg1, seg2, seg3;
+    for (int a = 0; a < o.n_lambda(); ++a) {
+        const int* L = &o.lam[(size_t)a * 7];
+        const int l1 = L[0], l2 = L[1], l12 = L[2], l3 = L[3], l123 = L[4], l4 = L[5], l5 = L[6];
+        const int s1base = (int)seg1.size(), s23base = (int)seg2.size();
+        for (int m12 = -l12; m12 <= l12; ++m12) {
+            const int b = (int)t1.size();
+            for (int m1 = -l1; m1 <= l1; ++m1) {
+                const int m2 = m12 - m1;
+                if (std::abs(m2) > l2) continue;
+                const double c = (((l12 - m12) & 1) ? -1.0 : 1.0) * wigner3j(l1, l2, l12, m1, m2, -m12);
+                if (c != 0.0) t1.push_back(make_int4(lmf(l1, m1), lmf(l2, m2), bits(c), 0));
+            }
+            seg1.push_back(make_int2(b, (int)t1.size()));
+        }
+        for (int m123 = 0; m123 <= l123; ++m123) {
+            const int b2 = (int)t2.size();
+            for (int m12 = -l12; m12 <= l12; ++m12) {
+                const int m3 = m123 - m12;
+                if (std::abs(m3) > l3) continue;
+                const double c = (((l123 - m123) & 1) ? -1.0 : 1.0) * wigner3j(l12, l3, l123, m12, m3, -m123);
+                if (c != 0.0) t2.push_back(make_int4(s1base + m12 + l12, lmf(l3, m3), bits(c), 0));
+            }
+            seg2.push_back(make_int2(b2, (int)t2.size()));
+            const int b3 = (int)t3.size();
+            for (int m4 = -l4; m4 <= l4; ++m4) {
+                const int m5 = -m123 - m4;
+                if (std::abs(m5) > l5) continue;
+                const double c = wigner3j(l123, l4, l5, m123, m4, m5);
+                if (c != 0.0) t3.push_back(make_int4(lmf(l4, m4), lmf(l5, m5), bits(c), 0));
+            }
+            seg3.push_back(make_int2(b3, (int)t3.size()));
+        }
+        lam.push_back(make_int4(l12, l123, o.odd(a) ? 1 : 0, off + a * nb));
+        lam2.push_back(make_int4(s1base, s23base, bits(std::sqrt((2.0 * l12 + 1.0) * (2.0 * l123 + 1.0))), 0));
+    }
+    // bin index of (b1, b2, b3, b3 + 1, b3 + 2); the (b4, b5) pairs after b3 follow in order
+    std::vector<int> binq((size_t)nr * nr * nr, 0);
+    for (int b = 0; b < nb; ++b) {
+        const int* B = &o.bins[(size_t)b * 5];
+        if (B[3] == B[2] + 1 && B[4] == B[2] + 2) binq[((size_t)B[0] * nr + B[1]) * nr + B[2]] = b;
+    }
+    // items (L, b3), grouped by b3 (the kernel's specialisation), heaviest multiplets first
+    std::vector<std::pair<double, int2>> items;
+    for (int a = 0; a < o.n_lambda(); ++a) {
+        double cost = 0.0;
+        for (int q = lam2[a].y; q < lam2[a].y + lam[a].y + 1; ++q) {
+            cost += seg3[q].y - seg3[q].x;
+            for (int e = seg2[q].x; e < seg2[q].y; ++e) cost += 1 + seg1[t2[e].x].y - seg1[t2[e].x].x;
+        }
+        for (int b3 = 2; b3 <= nr - 3; ++b3) items.push_back({1e12 * (nr - b3) + cost, make_int2(a, b3)});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) { return x.first > y.first; });
+    std::vector<int2> it;
+    for (const auto& x : items) it.push_back(x.second);
+    ctx->c6nitem = (int)it.size();
+    CU(upload(ctx->c6lam, lam));
+    CU(upload(ctx->c6lam2, lam2));
+    CU(upload(ctx->c6seg1, seg1));
+    CU(upload(ctx->c6seg2, seg2));
+    CU(upload(ctx->c6seg3, seg3));
+    CU(upload(ctx->c6terms1, t1));
+    CU(upload(ctx->c6terms2, t2));
+    CU(upload(ctx->c6terms3, t3));
+    CU(upload(ctx->c6binq, binq));
+    CU(upload(ctx->c6items, it));
+    return NPCF_OK;
+}
+
 npcf_status setup_tables(npcf_ctx* ctx) {
     ctx->nlm = nlm(ctx->lmax);
     // Y_lm conversion matrix
@@ -383,7 +485,7 @@ npcf_status setup_tables(npcf_ctx* ctx) {
     std::vector<float> Kf(K.begin(), K.end());
     CU(upload(ctx->kmat, Kf));
     ctx->total = 0;
-    for (int N = 3; N <= 5; ++N) {
+    for (int N = 3; N <= 6; ++N) {
         if (!(ctx->mask & (1u << N))) continue;
         ctx->orders.push_back(make_order(N, ctx->lmax, ctx->nr, ctx->allparity != 0));
         ctx->order_off.push_back(ctx->total);
@@ -398,7 +500,8 @@ npcf_status setup_tables(npcf_ctx* ctx) {
             const int* l = &o.lam[(size_t)L * o.width];
             double f = 1.0;
             for (int k = 0; k < o.width; ++k)
-                if (!(o.N == 5 && k == 2)) f *= ylm_l_norm(l[k]);   // l12 couples, it is no harmonic
+                if (!((o.N == 5 && k == 2) || (o.N == 6 && (k == 2 || k == 4))))
+                    f *= ylm_l_norm(l[k]);   // l12 and l123 couple, they are no harmonics
             zs.insert(zs.end(), o.n_bins(), f);
         }
     CU(upload(ctx->zscale, zs));
@@ -485,6 +588,9 @@ npcf_status setup_tables(npcf_ctx* ctx) {
             }
         } else if (o.N == 5) {
             npcf_status st = setup_c5_tables(ctx, o, off);
+            if (st != NPCF_OK) return st;
+        } else if (o.N == 6) {
+            npcf_status st = setup_c6_tables(ctx, o, off);
             if (st != NPCF_OK) return st;
         }
     }
@@ -608,7 +714,7 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     CU(ctx->count.ensure(cells));
     CU(ctx->start.ensure(cells + 1));
     CU(ctx->cursor.ensure(cells));
-    CU(ctx->work.ensure(3));
+    CU(ctx->work.ensure(4));
 
     // contraction chunks of the 3PCF and 5PCF kernels: ranges of about n / (4 x SMs)
     // primaries (a multiple of 64), never crossing a catalog
@@ -767,7 +873,7 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
     const size_t cells = (size_t)g.ncell * ncat;
     if (timed) CU(cudaEventRecord(ctx->ev[0], s));
     CU(cudaMemsetAsync(ctx->count.p, 0, cells * sizeof(uint32_t), s));
-    CU(cudaMemsetAsync(ctx->work.p, 0, 3 * sizeof(int), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 4 * sizeof(int), s));
     launch_sumw(d_w, ctx->d_off.p, ncat, ctx->sumw.p, s);
 
     BinArgs b{};
@@ -907,6 +1013,34 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
             c.nout = o.n_lambda() * o.n_bins();
             c.chunk_counter = ctx->work.p + 2;
             launch_contract5w(c, std::max(1, std::min(2 * ctx->nsm, P.nchunk)), s);
+        } else if (o.N == 6) {
+            if (ctx->c6nitem == 0) continue;
+            Contract6Args c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.lmax = ctx->lmax;
+            c.lam = ctx->c6lam.p;
+            c.lam2 = ctx->c6lam2.p;
+            c.seg1 = ctx->c6seg1.p;
+            c.terms1 = ctx->c6terms1.p;
+            c.seg2 = ctx->c6seg2.p;
+            c.terms2 = ctx->c6terms2.p;
+            c.seg3 = ctx->c6seg3.p;
+            c.terms3 = ctx->c6terms3.p;
+            c.binq = ctx->c6binq.p;
+            c.items = ctx->c6items.p;
+            c.nitem = ctx->c6nitem;
+            c.chunks = ctx->chunks.p;
+            c.nchunk = P.nchunk;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            c.out_off = ctx->order_off[k];
+            c.nout = o.n_lambda() * o.n_bins();
+            c.chunk_counter = ctx->work.p + 3;
+            launch_contract6(c, std::max(1, std::min(2 * ctx->nsm, P.nchunk)), s);
         }
         CU(cudaGetLastError());
     }
@@ -1007,8 +1141,8 @@ npcf_status npcf_create(npcf_ctx** out, int lmax, unsigned order_mask, int nr, c
     if (lmax < 0 || lmax > kMaxL) return bad(fail(ctx, NPCF_EINVAL, "lmax %d outside [0, %d]", lmax, kMaxL));
     if (nr < 1 || nr > kMaxNr) return bad(fail(ctx, NPCF_EINVAL, "nr %d outside [1, %d]", nr, kMaxNr));
     if (!edges) return bad(fail(ctx, NPCF_EINVAL, "edges is null"));
-    if ((order_mask & ~((1u << 3) | (1u << 4) | (1u << 5))) || order_mask == 0)
-        return bad(fail(ctx, NPCF_EINVAL, "order_mask 0x%x must select orders among 3, 4, 5", order_mask));
+    if ((order_mask & ~((1u << 3) | (1u << 4) | (1u << 5) | (1u << 6))) || order_mask == 0)
+        return bad(fail(ctx, NPCF_EINVAL, "order_mask 0x%x must select orders among 3, 4, 5, 6", order_mask));
     if (prec != NPCF_FP32 && prec != NPCF_SPLIT_BF16)
         return bad(fail(ctx, NPCF_EINVAL, "unknown precision %d", prec));
     for (int i = 0; i <= nr; ++i)
@@ -1096,7 +1230,8 @@ npcf_status npcf_truncate(const npcf_ctx* ctx, const double* in, size_t in_len, 
     auto keep = [&](const OrderTable& o, int a) {
         const int* L = &o.lam[(size_t)a * o.width];
         for (int k = 0; k < o.width; ++k) {
-            const int cap = (o.N == 5 && k == 2) ? 2 * lmax_out : lmax_out;   // l12 couples two l's
+            // l12 and l123 couple two l's
+            const int cap = ((o.N == 5 && k == 2) || (o.N == 6 && (k == 2 || k == 4))) ? 2 * lmax_out : lmax_out;
             if (L[k] > cap) return false;
         }
         return true;
@@ -1349,7 +1484,7 @@ npcf_status npcf_edge_correct(npcf_ctx* nctx, npcf_ctx* rctx, double* out) {
     if (nctx->allparity) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction takes parity-even multiplets");
     if (nctx->ncat > 1 || rctx->ncat > 1) return fail(nctx, NPCF_EINVAL, "edge correction takes single catalogs");
     for (const OrderTable& o : nctx->orders)
-        if (o.N == 5) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction is built for orders 3 and 4");
+        if (o.N >= 5) return fail(nctx, NPCF_EUNSUPPORTED, "edge correction is built for orders 3 and 4");
     CU(cudaDeviceSynchronize());
     int errbits = 0, rerr = 0;
     CU(cudaMemcpy(&errbits, nctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));

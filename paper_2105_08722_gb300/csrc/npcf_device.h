@@ -214,6 +214,32 @@ void launch_contract5w(const Contract5WArgs& a, int nblocks, cudaStream_t s);
 size_t contract5w_smem_bytes(const Contract5WArgs& a);
 size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
 
+// 6PCF contraction (FP32 CUDA cores, npcf_contract6.cu): Eq. basis-coupling at N = 6
+// through m12 and m123, primaries on the lanes, items (L, b3); 5 <= nr <= 8.
+struct Contract6Args {
+    const float2* alm;         // [n][nr][nlm]
+    const float* wp;
+    int n, nr, nlm, lmax;
+    const int4* lam;           // per multiplet: (l12, l123, odd, first output of L)
+    const int4* lam2;          // per multiplet: (first P12 segment, first m123 segment, prefactor bits, 0)
+    const int2* seg1;          // P12 segments: term range of (L, m12)
+    const int4* terms1;        // (lm of (l1, m1), lm of (l2, m2), coefficient bits, 0); lm = l^2 + l + m
+    const int2* seg2;          // per (L, m123): range of Q terms
+    const int4* terms2;        // (P12 segment of m12, lm of (l3, m3), coefficient bits, 0)
+    const int2* seg3;          // per (L, m123): range of P45 terms
+    const int4* terms3;        // (lm of (l4, m4), lm of (l5, m5), coefficient bits, 0)
+    const int* binq;           // [nr][nr][nr]: bin index of (b1, b2, b3, b3 + 1, b3 + 2)
+    const int2* items;         // (multiplet, b3)
+    int nitem;
+    const int2* chunks;        // primary ranges, none crossing a catalog
+    int nchunk;
+    double* partial;           // [nchunk][total]
+    int total, out_off, nout;
+    int* chunk_counter;        // zeroed before the launch
+};
+void launch_contract6(const Contract6Args& a, int nblocks, cudaStream_t s);
+size_t contract6_smem_bytes(const Contract6Args& a);
+
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- edge correction (a7)

@@ -493,6 +493,49 @@ def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev):
     assert_orders_close(got, want, (3, 4, 5), 2, 5, allparity=True)
 
 
+# ------------------------------------------------------------------ 6PCF
+
+@pytest.mark.parametrize("n,lmax,nr,allparity", [
+    (400, 2, 8, False),   # 327 multiplets x 56 bin tuples
+    (300, 3, 6, False),   # 2,212 multiplets (intermediates up to 2 lmax) x 6 bin tuples
+    (400, 1, 8, True),    # all parities: 42 multiplets, parity-odd ones imaginary
+    (300, 2, 5, False),   # one bin tuple
+    (300, 2, 7, True),
+])
+def test_6pcf_periodic(torch_dev, n, lmax, nr, allparity):
+    # Eq. (basis-coupling) with two intermediates, contracted through m12 and m123 on the
+    # GPU; the oracle sums the full M range of Eq. (NPCF-mult-discrete-binned-estimator)
+    pos = catalogs.lognormal_box(n, 150.0, 32, seed=60 + nr)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(6.0, 42.0, nr + 1)
+    _, got, counts = gpu_run(torch_dev, pos, w, (6,), lmax, edges, 150.0, allparity=allparity)
+    want, wcounts = oracle.npcf(pos, w, (6,), lmax, edges, 150.0, allparity=allparity)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (6,), lmax, nr, allparity=allparity)
+
+
+def test_6pcf_with_lower_orders_weighted_open_box(torch_dev):
+    # orders 3 to 6 in one context (output offsets), signed weights, no periodicity
+    pos, w = _catalog(350, 80.0, 66)
+    w = w - np.float32(0.8)
+    edges = np.linspace(5.0, 30.0, 7)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4, 5, 6), 2, edges, 0.0)
+    want, wcounts = oracle.npcf(pos, w, (3, 4, 5, 6), 2, edges, 0.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4, 5, 6), 2, 6)
+
+
+def test_6pcf_limits(torch_dev):
+    from paper_2105_08722_gb300._lib import NPCF, NPCFError, NPCF_EUNSUPPORTED
+    with pytest.raises(NPCFError) as e:
+        NPCF(2, (6,), np.linspace(1.0, 10.0, 10), 100.0)   # 9 shells: the contraction takes 8
+    assert e.value.status == NPCF_EUNSUPPORTED
+    # fewer than 5 shells: no bin tuple, nothing to compute, an empty order
+    est = NPCF(2, (3, 6), np.linspace(1.0, 10.0, 5), 100.0)
+    assert est.layout(6)[1].shape[0] == 0
+    est.close()
+
+
 def test_lognormal_100k_5pcf_lmax4_sampled_primaries(torch_dev):
     wl = catalogs.lognormal100k_5pcf()
     rng = np.random.default_rng(2026)

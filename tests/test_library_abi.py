@@ -57,7 +57,7 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
         NPCF(3, (3,), edges, box=20.0)              # periodic box must exceed 3 r_max
     assert e.value.status == NPCF_EINVAL
     with pytest.raises(NPCFError) as e:
-        NPCF(3, (6,), edges)                        # unsupported order
+        NPCF(3, (7,), edges)                        # unsupported order
     assert e.value.status == NPCF_EINVAL
     with pytest.raises(NPCFError) as e:
         NPCF(3, (3,), np.linspace(1, 2, 18))        # more than 16 shells
