@@ -114,6 +114,25 @@ npcf_status npcf_accumulate_ex(npcf_ctx* ctx, const float* d_pos, const float* d
 npcf_status npcf_accumulate_host(npcf_ctx* ctx, const float* h_pos, const float* h_w,
                                  int64_t n, void* stream);
 
+/* Random splits with the data harmonics kept (Sec. 4.2: the data particles' contributions
+ * to a_lm are the same in every data-minus-randoms split, so they are formed once).
+ * npcf_cache_data: for every data point as a primary, its a_lm from the data as secondaries
+ * and its per-shell counts, and the data-data pair counts, kept in the context with a device
+ * copy of the data (d_pos, d_w as in npcf_accumulate, 1 <= n < 2^26; a new call replaces
+ * them). It does not touch the accumulators.
+ * npcf_accumulate_split: adds what npcf_accumulate would add for the catalog made of the
+ * cached data followed by this split's randoms (d_pos, d_w, n as in npcf_accumulate, n >= 0;
+ * random weights typically -N_D/N_R), without searching the data-data pairs again: a data
+ * primary takes its cached a_lm plus the randoms as secondaries, a random primary takes the
+ * data and the randoms as secondaries; the counts include the cached data-data pairs. Calls
+ * on the same context are stream-ordered (use one stream, or synchronise between streams);
+ * single catalogs only (NPCF_EINVAL when the accumulators hold a batch); NPCF_EINVAL
+ * before npcf_cache_data. With box == 0 each call reads a bounding box back to the host
+ * (one stream synchronisation); the grid covers the data and the randoms. */
+npcf_status npcf_cache_data(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream);
+npcf_status npcf_accumulate_split(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n,
+                                  void* stream);
+
 /* Number of doubles npcf_finalize writes. */
 npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len);
 

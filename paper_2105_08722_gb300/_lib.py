@@ -26,6 +26,8 @@ SIGNATURES = {
     "npcf_accumulate": (_i, [_vp, _vp, _vp, _i64, _vp]),
     "npcf_accumulate_ex": (_i, [_vp, _vp, _vp, _vp, _i64, _vp]),
     "npcf_accumulate_host": (_i, [_vp, _vp, _vp, _i64, _vp]),
+    "npcf_cache_data": (_i, [_vp, _vp, _vp, _i64, _vp]),
+    "npcf_accumulate_split": (_i, [_vp, _vp, _vp, _i64, _vp]),
     "npcf_output_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "npcf_layout": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp, _vp]),
     "npcf_finalize": (_i, [_vp, _vp, _sz, _i]),
@@ -198,6 +200,18 @@ class NPCF:
         else:
             self._check(self._lib.npcf_accumulate_ex(self._h, _ptr(pos), _ptr(w), _ptr(wprim), n,
                                                      _stream_handle(stream)))
+
+    def cache_data(self, pos, w, stream=None):
+        """Keep the data's harmonics for later random splits (npcf_cache_data); pos [n, 3]
+        and w [n] CUDA float32 tensors."""
+        self._check(self._lib.npcf_cache_data(self._h, _ptr(pos), _ptr(w), int(pos.shape[0]),
+                                              _stream_handle(stream)))
+
+    def accumulate_split(self, pos, w, stream=None):
+        """Accumulate the cached data followed by these randoms (npcf_accumulate_split)."""
+        n = int(pos.shape[0])
+        self._check(self._lib.npcf_accumulate_split(self._h, _ptr(pos) if n else None, _ptr(w) if n else None, n,
+                                                    _stream_handle(stream)))
 
     def accumulate_host(self, pos: np.ndarray, w: np.ndarray, stream=None):
         pos = np.ascontiguousarray(pos, dtype=np.float32)

@@ -126,6 +126,15 @@ struct npcf_ctx {
     DevBuf<int> errflag, work;
     DevBuf<float> bbox;
     DevBuf<float> hpos_stage, hw_stage;
+    // data harmonics kept across random splits (npcf_cache_data): the data positions and
+    // weights (input order), their a_lm from the data alone and per-shell counts (input
+    // order) and the data-data pair counts
+    DevBuf<float> sd_pos, sd_w;
+    DevBuf<float2> sd_alm;
+    DevBuf<uint32_t> sd_cnt;
+    DevBuf<unsigned long long> sd_counts;
+    DevBuf<long long> sd_off;      // {0, n_data, 0, n_randoms}
+    int64_t sd_n = 0;              // data points cached (0: none)
     // catalogs the accumulators hold (0: none yet; fixed by the first accumulate call)
     int ncat = 0;
     // tables of the current batch (host copies decide whether an upload is needed)
@@ -614,9 +623,10 @@ int auto_cells_per_rmax(double points, double volume, double rmax) {
     return nb < 630.0 ? 2 : 3;
 }
 
-npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, int ncat, cudaStream_t s) {
+npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, int ncat, cudaStream_t s,
+                       const float* d_pos2 = nullptr, int n2 = 0) {
     const double rmax = ctx->edges[ctx->nr];
-    const double per_cat = (double)n / std::max(ncat, 1);
+    const double per_cat = (double)(n + (d_pos2 ? n2 : 0)) / std::max(ncat, 1);
     GridInfo g{};
     std::vector<int> rows;
     if (ctx->box > 0) {
@@ -626,9 +636,11 @@ npcf_status setup_grid(npcf_ctx* ctx, const float* d_pos, int n, int ncat, cudaS
             return fail(ctx, NPCF_EINVAL, "box %.6g too small for r_max %.6g", ctx->box, rmax);
     } else {
         // bounding box of the catalog (one stream synchronisation)
-        const int nb = 256;
+        // (a second list of points, if given, is bounded together with the first)
+        const int nb = d_pos2 && n2 > 0 ? 512 : 256;
         CU(ctx->bbox.ensure(nb * 6));
-        launch_bbox(d_pos, n, ctx->bbox.p, nb, s);
+        launch_bbox(d_pos, n, ctx->bbox.p, 256, s);
+        if (nb > 256) launch_bbox(d_pos2, n2, ctx->bbox.p + 256 * 6, 256, s);
         CU(cudaGetLastError());
         std::vector<float> part(nb * 6);
         CU(cudaMemcpyAsync(part.data(), ctx->bbox.p, nb * 6 * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -675,7 +687,7 @@ bool same_table(const DevBuf<T>& b, const std::vector<T>& host, const std::vecto
 // (catalog offsets, contraction chunks). Uploads happen only when a table changes, so a
 // repeated call with the same shapes does no synchronous work here.
 npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const std::vector<long long>& off,
-                    cudaStream_t s, Plan& P) {
+                    cudaStream_t s, Plan& P, const float* d_pos2 = nullptr, int n2 = 0) {
     const long long n64 = off.back();
     const int ncat = (int)off.size() - 1;
     if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", n64);
@@ -698,7 +710,7 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         CU(cudaMemset(ctx->sumw.p, 0, ncat * sizeof(double)));
         ctx->ncat = ncat;
     }
-    npcf_status st = setup_grid(ctx, d_pos, n, ncat, s);
+    npcf_status st = setup_grid(ctx, d_pos, d_pos2 ? n - n2 : n, ncat, s, d_pos2, n2);
     if (st != NPCF_OK) return st;
     const GridInfo& g = ctx->grid;
     const size_t cells = (size_t)g.ncell * ncat;
@@ -769,6 +781,11 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     pa.pts = ctx->pts.p;
     pa.wp = ctx->wp.p;
     pa.cell_of = ctx->cell_of.p;
+    pa.ppts = ctx->pts.p;
+    pa.pwp = ctx->wp.p;
+    pa.pcell = ctx->cell_of.p;
+    pa.np = n;
+    pa.add = 0;
     pa.cell_start = ctx->start.p;
     pa.rows = ctx->rows.p;
     pa.nrows = (int)(ctx->rows_host.size() / 4);
@@ -864,6 +881,8 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     return NPCF_OK;
 }
 
+npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool timed);
+
 // Device part of an accumulate call: memsets and kernels only, all on stream s, so that a
 // batch can be captured into a CUDA graph and replayed. Stage events only when timed.
 npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const float* d_wprim, const Plan& P,
@@ -902,7 +921,13 @@ npcf_status enqueue(npcf_ctx* ctx, const float* d_pos, const float* d_w, const f
     launch_pair(pa, ctx->nsm, s);   // persistent: one block per SM, work units taken dynamically
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecord(ctx->ev[2], s));
+    return enqueue_contract(ctx, P, s, timed);
+}
 
+// The contractions over the primaries of a plan (a4 to a6): every order's kernel into the
+// chunk rows, then the FP64 reduction of each catalog's rows into its accumulators.
+npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool timed) {
+    const int n = P.n, ncat = P.ncat;
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
         if (o.N == 3) {
@@ -1122,6 +1147,95 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
     return NPCF_OK;
 }
 
+// One list of points binned into a region of the context's buffers: sorted points, weights,
+// input index and cell from first; cell counts, starts and cursors from cell0 (ncell + 1
+// starts per list).
+void bin_list(npcf_ctx* ctx, const float* pos, const float* w, int n, int first, size_t cell0,
+              const long long* d_off, cudaStream_t s) {
+    BinArgs b{};
+    b.pos = pos;
+    b.w = w;
+    b.wprim = nullptr;
+    b.n = n;
+    b.g = ctx->grid;
+    b.cid = ctx->cid.p + first;
+    b.count = ctx->count.p + cell0;
+    b.start = ctx->start.p + cell0 + cell0 / ctx->grid.ncell;   // ncell + 1 starts per list
+    b.cursor = ctx->cursor.p + cell0;
+    b.pts = ctx->pts.p + first;
+    b.wp = ctx->wp.p + first;
+    b.idx = ctx->idx.p + first;
+    b.cell_of = ctx->cell_of.p + first;
+    b.err = ctx->errflag.p;
+    b.off = d_off;
+    b.ncat = 1;
+    launch_bin(b, s);
+}
+
+// Data-minus-randoms split with the data harmonics kept from npcf_cache_data (Sec. 4.2):
+// the data (n_d points, cached) and this split's randoms (n_r) are binned as two lists on one
+// grid; a_lm of the data primaries = cached data part + the randoms as secondaries; a_lm of the
+// random primaries = the data as secondaries + the randoms as secondaries; then the usual
+// contractions over all n_d + n_r primaries.
+npcf_status run_split(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n_r, cudaStream_t s) {
+    if (ctx->sd_n <= 0) return fail(ctx, NPCF_EINVAL, "no cached data: call npcf_cache_data first");
+    if (n_r < 0) return fail(ctx, NPCF_EINVAL, "negative number of randoms");
+    if (n_r > 0 && (!d_pos || !d_w)) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+    if (ctx->ncat > 1) return fail(ctx, NPCF_EINVAL, "the accumulators hold a batch (npcf_reset first)");
+    const int n_d = (int)ctx->sd_n;
+    const long long N = (long long)n_d + n_r;
+    Plan P;
+    npcf_status st = prepare(ctx, ctx->sd_pos.p, ctx->sd_w.p, std::vector<long long>{0, N}, s, P,
+                             n_r > 0 ? d_pos : nullptr, (int)n_r);
+    if (st != NPCF_OK) return st;
+    const size_t cells = (size_t)ctx->grid.ncell;
+    CU(ctx->count.ensure(2 * cells));
+    CU(ctx->start.ensure(2 * cells + 2));
+    CU(ctx->cursor.ensure(2 * cells));
+    const bool timed = ctx->timed;
+    if (timed) CU(cudaEventRecord(ctx->ev[0], s));
+    launch_set4(ctx->sd_off.p, 0, n_d, 0, n_r, s);   // the two lists' ranges
+    CU(cudaMemsetAsync(ctx->count.p, 0, 2 * cells * sizeof(uint32_t), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 4 * sizeof(int), s));
+    launch_sumw(ctx->sd_w.p, ctx->sd_off.p, 1, ctx->sumw.p, s);
+    if (n_r > 0) launch_sumw(d_w, ctx->sd_off.p + 2, 1, ctx->sumw.p, s);
+    bin_list(ctx, ctx->sd_pos.p, ctx->sd_w.p, n_d, 0, 0, ctx->sd_off.p, s);
+    bin_list(ctx, d_pos, d_w, (int)n_r, n_d, cells, ctx->sd_off.p + 2, s);
+    CU(cudaGetLastError());
+    if (timed) CU(cudaEventRecord(ctx->ev[1], s));
+    const int row = ctx->nr * ctx->nlm;
+    launch_alm_from_input(ctx->sd_alm.p, ctx->sd_cnt.p, ctx->idx.p, n_d, row, ctx->nr, ctx->alm.p, ctx->cnt.p, s);
+    // the three passes: (data, randoms) added to the cached part, (randoms, data), (randoms, randoms) added
+    const uint32_t* start_d = ctx->start.p;
+    const uint32_t* start_r = ctx->start.p + cells + 1;
+    struct Pass { int prim0, np, sec0, nsec; const uint32_t* start; int add; };
+    const Pass passes[3] = {{0, n_d, n_d, (int)n_r, start_r, 1},
+                            {n_d, (int)n_r, 0, n_d, start_d, 0},
+                            {n_d, (int)n_r, n_d, (int)n_r, start_r, 1}};
+    for (const Pass& q : passes) {
+        if (q.np == 0 || q.nsec == 0) continue;
+        CU(cudaMemsetAsync(ctx->work.p, 0, sizeof(int), s));
+        PairArgs pa = P.pa;
+        pa.ppts = ctx->pts.p + q.prim0;
+        pa.pwp = ctx->wp.p + q.prim0;
+        pa.pcell = ctx->cell_of.p + q.prim0;
+        pa.np = q.np;
+        pa.pts = ctx->pts.p + q.sec0;
+        pa.wp = ctx->wp.p + q.sec0;
+        pa.cell_of = ctx->cell_of.p + q.sec0;
+        pa.cell_start = q.start;
+        pa.alm = ctx->alm.p + (size_t)q.prim0 * row;
+        pa.cnt = ctx->cnt.p + (size_t)q.prim0 * ctx->nr;
+        pa.add = q.add;
+        pa.skip_zero = 0;
+        launch_pair(pa, ctx->nsm, s);
+        CU(cudaGetLastError());
+    }
+    launch_add_counts(ctx->counts.p, ctx->sd_counts.p, ctx->nr, s);
+    if (timed) CU(cudaEventRecord(ctx->ev[2], s));
+    return enqueue_contract(ctx, P, s, timed);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1214,6 +1328,45 @@ npcf_status npcf_accumulate_host(npcf_ctx* ctx, const float* h_pos, const float*
     if (st != NPCF_OK) return st;
     CU(cudaStreamSynchronize(s));
     return NPCF_OK;
+}
+
+npcf_status npcf_cache_data(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (n <= 0 || n >= (int64_t(1) << 26)) return fail(ctx, NPCF_EINVAL, "n = %lld outside [1, 2^26)", (long long)n);
+    if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+    if (ctx->ncat > 1) return fail(ctx, NPCF_EINVAL, "the accumulators hold a batch (npcf_reset first)");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(ctx->sd_pos.ensure((size_t)3 * n));
+    CU(ctx->sd_w.ensure((size_t)n));
+    CU(cudaMemcpyAsync(ctx->sd_pos.p, d_pos, (size_t)3 * n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(ctx->sd_w.p, d_w, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    Plan P;
+    npcf_status st = prepare(ctx, ctx->sd_pos.p, ctx->sd_w.p, std::vector<long long>{0, n}, s, P);
+    if (st != NPCF_OK) return st;
+    const int row = ctx->nr * ctx->nlm;
+    CU(ctx->sd_alm.ensure((size_t)n * row));
+    CU(ctx->sd_cnt.ensure((size_t)n * ctx->nr));
+    CU(ctx->sd_counts.ensure(ctx->nr));
+    CU(ctx->sd_off.ensure(4));
+    launch_set4(ctx->sd_off.p, 0, n, 0, 0, s);
+    const size_t cells = (size_t)ctx->grid.ncell;
+    CU(cudaMemsetAsync(ctx->count.p, 0, cells * sizeof(uint32_t), s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 4 * sizeof(int), s));
+    CU(cudaMemsetAsync(ctx->sd_counts.p, 0, ctx->nr * sizeof(unsigned long long), s));
+    bin_list(ctx, ctx->sd_pos.p, ctx->sd_w.p, (int)n, 0, 0, ctx->sd_off.p, s);
+    PairArgs pa = P.pa;
+    pa.counts = ctx->sd_counts.p;   // the data-data counts are added by every split
+    pa.skip_zero = 0;
+    launch_pair(pa, ctx->nsm, s);
+    launch_alm_to_input(ctx->alm.p, ctx->cnt.p, ctx->idx.p, (int)n, row, ctx->nr, ctx->sd_alm.p, ctx->sd_cnt.p, s);
+    CU(cudaGetLastError());
+    ctx->sd_n = n;
+    return NPCF_OK;
+}
+
+npcf_status npcf_accumulate_split(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    return run_split(ctx, d_pos, d_w, n, (cudaStream_t)stream);
 }
 
 npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len) {

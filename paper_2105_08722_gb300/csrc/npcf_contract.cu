@@ -97,7 +97,60 @@ __global__ void k_sumw(const float* __restrict__ w, const long long* __restrict_
     }
 }
 
+// Cached harmonics of data primaries (the re-use of the data part across random splits):
+// per-primary rows of `row` float2 and `rc` counts moved between cell order and input order.
+__global__ void k_alm_to_input(const float2* __restrict__ alm, const uint32_t* __restrict__ cnt,
+                               const uint32_t* __restrict__ idx, int n, int row, int rc, float2* __restrict__ alm_in,
+                               uint32_t* __restrict__ cnt_in) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n * row;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(i / row), r = (int)(i - (long long)p * row);
+        alm_in[(size_t)idx[p] * row + r] = alm[i];
+        if (r < rc) cnt_in[(size_t)idx[p] * rc + r] = cnt[(size_t)p * rc + r];
+    }
+}
+
+__global__ void k_alm_from_input(const float2* __restrict__ alm_in, const uint32_t* __restrict__ cnt_in,
+                                 const uint32_t* __restrict__ idx, int n, int row, int rc, float2* __restrict__ alm,
+                                 uint32_t* __restrict__ cnt) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n * row;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(i / row), r = (int)(i - (long long)p * row);
+        alm[i] = alm_in[(size_t)idx[p] * row + r];
+        if (r < rc) cnt[(size_t)p * rc + r] = cnt_in[(size_t)idx[p] * rc + r];
+    }
+}
+
+__global__ void k_add_counts(unsigned long long* dst, const unsigned long long* src, int n) {
+    if (threadIdx.x < n) dst[threadIdx.x] += src[threadIdx.x];
+}
+
+__global__ void k_set4(long long* dst, long long a, long long b, long long c, long long d) {
+    dst[0] = a;
+    dst[1] = b;
+    dst[2] = c;
+    dst[3] = d;
+}
+
 }  // namespace
+
+void launch_alm_to_input(const float2* alm, const uint32_t* cnt, const uint32_t* idx, int n, int row, int rc,
+                         float2* alm_in, uint32_t* cnt_in, cudaStream_t s) {
+    if (n > 0) k_alm_to_input<<<1024, 256, 0, s>>>(alm, cnt, idx, n, row, rc, alm_in, cnt_in);
+}
+
+void launch_alm_from_input(const float2* alm_in, const uint32_t* cnt_in, const uint32_t* idx, int n, int row, int rc,
+                           float2* alm, uint32_t* cnt, cudaStream_t s) {
+    if (n > 0) k_alm_from_input<<<1024, 256, 0, s>>>(alm_in, cnt_in, idx, n, row, rc, alm, cnt);
+}
+
+void launch_add_counts(unsigned long long* dst, const unsigned long long* src, int n, cudaStream_t s) {
+    k_add_counts<<<1, 32, 0, s>>>(dst, src, n);
+}
+
+void launch_set4(long long* dst, long long a, long long b, long long c, long long d, cudaStream_t s) {
+    k_set4<<<1, 1, 0, s>>>(dst, a, b, c, d);
+}
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s) {
     const int per = a.nr * a.nlm;

@@ -58,10 +58,15 @@ void launch_bin(const BinArgs& a, cudaStream_t s);
 constexpr int kPairWarps = 16;     // independent warps per pair-kernel block (one block per SM)
 constexpr int kPairShellTab = 512; // bins of r2 of the pair kernel's shell table
 struct PairArgs {
-    const float4* pts;
+    const float4* pts;         // secondaries: (x, y, z, w) in cell order
     const float* wp;
     const uint32_t* cell_of;
-    const uint32_t* cell_start;
+    const uint32_t* cell_start;// cell starts of the secondaries
+    const float4* ppts;        // primaries in cell order (the same list as pts, or another one
+    const float* pwp;          //   binned on the same grid), their weights u and cells
+    const uint32_t* pcell;
+    int np;                    // primaries
+    int add;                   // add to a_lm and cnt (another pass over other secondaries)
     const int4* rows;          // (dy, dz, dx_lo, dx_hi) neighbour rows
     int nrows;
     GridInfo g;
@@ -262,5 +267,14 @@ size_t edge_smem_bytes(int nl);
 void launch_reduce(const double* partial, const int* cbeg, int ncat, int total, int off, int count,
                    const double* scale, double* zeta, cudaStream_t s);
 void launch_sumw(const float* w, const long long* off, int ncat, double* sumw, cudaStream_t s);
+// Per-primary a_lm rows (row float2) and shell counts (rc) between cell order (p) and input
+// order (idx[p]): the cached data harmonics of npcf_cache_data / npcf_accumulate_split.
+void launch_alm_to_input(const float2* alm, const uint32_t* cnt, const uint32_t* idx, int n, int row, int rc,
+                         float2* alm_in, uint32_t* cnt_in, cudaStream_t s);
+void launch_alm_from_input(const float2* alm_in, const uint32_t* cnt_in, const uint32_t* idx, int n, int row, int rc,
+                           float2* alm, uint32_t* cnt, cudaStream_t s);
+void launch_add_counts(unsigned long long* dst, const unsigned long long* src, int n, cudaStream_t s);
+// dst[0..3] = (a, b, c, d), stream-ordered (offset tables written without host buffers)
+void launch_set4(long long* dst, long long a, long long b, long long c, long long d, cudaStream_t s);
 
 }  // namespace npcf

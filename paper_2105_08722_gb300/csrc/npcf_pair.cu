@@ -437,14 +437,16 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const int4* ro
     // A primary of weight 0 adds nothing to zeta, but its neighbours are still counted
     // (every primary's pairs enter the counts) unless separate primary weights select a
     // sample of primaries: then a weight of 0 means "not in the sample".
-    if (a.skip_zero && a.wp[p] == 0.f) {
-        for (int i = lane; i < nr * NLM; i += 32) out[i] = make_float2(0.f, 0.f);
-        if (lane < nr) a.cnt[(size_t)p * nr + lane] = 0u;
+    if (a.skip_zero && a.pwp[p] == 0.f) {
+        if (!a.add) {
+            for (int i = lane; i < nr * NLM; i += 32) out[i] = make_float2(0.f, 0.f);
+            if (lane < nr) a.cnt[(size_t)p * nr + lane] = 0u;
+        }
         return;
     }
     const GridInfo& g = a.g;
-    const float4 pi = __ldg(&a.pts[p]);
-    const int cell = (int)__ldg(&a.cell_of[p]);
+    const float4 pi = __ldg(&a.ppts[p]);
+    const int cell = (int)__ldg(&a.pcell[p]);
     const int cat = cell / g.ncell, lc = cell - cat * g.ncell;
     const int cx = lc % g.gx, cy = (lc / g.gx) % g.gy, cz = lc / (g.gx * g.gy);
     for (int i = lane; i < nr * NC; i += 32) psum[i] = 0.f;
@@ -482,7 +484,7 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const int4* ro
             const int row = min(srow + below + __popc(W[j] & le), nrow - 1);
             below += __popc(W[j]);
             const int2 dc = tdc[row];
-            q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + dc.x : p;
+            q[j] = 32 * j + lane < lim ? cursor + 32 * j + lane + dc.x : 0;
             code[j] = dc.y;
             sf[j] = sh.shift[code[j]];
         }
@@ -528,11 +530,16 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const int4* ro
             re = fmaf(kk, sr, re);
             im = fmaf(kk, sim, im);
         }
+        if (a.add) {   // a further pass over another list of secondaries: a_lm is linear in them
+            const float2 o = out[i];
+            re += o.x;
+            im += o.y;
+        }
         __stcs(&out[i], make_float2(re, im));
     }
     if (lane < nr) {
         const uint32_t c = sh.tot[warp][lane];
-        a.cnt[(size_t)p * nr + lane] = c;
+        a.cnt[(size_t)p * nr + lane] = a.add ? a.cnt[(size_t)p * nr + lane] + c : c;
         if (c) atomicAdd(&a.counts[(size_t)cat * nr + lane], (unsigned long long)c);
     }
     __syncwarp();   // psum, ne and tot are reset by the next primary
@@ -612,9 +619,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) k_pair(const PairArgs a) {
             if (lane == 0) atomicOr(a.err, 2);
             break;
         }
-        if (base >= a.n) break;   // past the last primary: so is every later chunk
+        if (base >= a.np) break;   // past the last primary: so is every later chunk
         const int p = base + r;
-        if (p >= a.n) continue;
+        if (p >= a.np) continue;
         one_primary<L>(a, sh, rows, tpref, tdc, psum, bucket, trim, p, warp, lane);
     }
 }

@@ -493,6 +493,69 @@ def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev):
     assert_orders_close(got, want, (3, 4, 5), 2, 5, allparity=True)
 
 
+# ------------------------------------------------------------------ random splits, data harmonics kept
+
+@pytest.mark.parametrize("box", [150.0, 0.0])
+def test_split_with_cached_data_matches_uncached_and_oracle(torch_dev, box):
+    # Sec. 4.2: the data's a_lm contributions are the same in every data-minus-randoms
+    # split; npcf_cache_data forms them once and npcf_accumulate_split adds only what the
+    # randoms change. Two co-added splits must equal two plain accumulate calls on the
+    # concatenated catalogs (counts exactly) and the oracle.
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF
+    rng = np.random.default_rng(700)
+    data = catalogs.lognormal_box(1200, 150.0, 32, seed=71)
+    if box == 0.0:   # randoms reach beyond the data's bounding box in an open geometry
+        r1 = rng.uniform(-10.0, 160.0, size=(1800, 3)).astype(np.float32)
+        r2 = rng.uniform(-10.0, 160.0, size=(1500, 3)).astype(np.float32)
+    else:
+        r1 = rng.uniform(0.0, 150.0, size=(1800, 3)).astype(np.float32)
+        r2 = rng.uniform(0.0, 150.0, size=(1500, 3)).astype(np.float32)
+    wd = np.ones(len(data), np.float32)
+    w1 = np.full(len(r1), -len(data) / len(r1), np.float32)
+    w2 = np.full(len(r2), -len(data) / len(r2), np.float32)
+    edges = np.linspace(5.0, 35.0, 6)
+    orders, lmax = (3, 4, 5), 2
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    plain = NPCF(lmax, orders, edges, box)
+    cached = NPCF(lmax, orders, edges, box)
+    cached.cache_data(t(data), t(wd))
+    want = 0.0
+    wcounts = 0
+    for r, wr in ((r1, w1), (r2, w2)):
+        pos = np.concatenate([data, r])
+        w = np.concatenate([wd, wr])
+        plain.accumulate(t(pos), t(w))
+        cached.accumulate_split(t(r), t(wr))
+        z, c = oracle.npcf(pos, w, orders, lmax, edges, box)
+        want = want + z
+        wcounts = wcounts + c
+    got, ref = cached.finalize(), plain.finalize()
+    assert np.array_equal(cached.pair_counts(), plain.pair_counts())
+    assert np.array_equal(cached.pair_counts(), wcounts)
+    assert_orders_close(got, ref, orders, lmax, len(edges) - 1)
+    assert_orders_close(got, want, orders, lmax, len(edges) - 1)
+    # a split without randoms adds the data alone
+    solo = NPCF(lmax, orders, edges, box)
+    solo.cache_data(t(data), t(wd))
+    solo.accumulate_split(t(np.zeros((0, 3), np.float32)), t(np.zeros(0, np.float32)))
+    zd, cd = oracle.npcf(data, wd, orders, lmax, edges, box)
+    assert np.array_equal(solo.pair_counts(), cd)
+    assert_orders_close(solo.finalize(), zd, orders, lmax, len(edges) - 1)
+    for e in (plain, cached, solo):
+        e.close()
+
+
+def test_split_needs_cached_data(torch_dev):
+    torch, dev = torch_dev
+    from paper_2105_08722_gb300._lib import NPCF, NPCFError, NPCF_EINVAL
+    est = NPCF(2, (3,), np.linspace(5.0, 35.0, 6), 150.0)
+    with pytest.raises(NPCFError) as e:
+        est.accumulate_split(torch.zeros((10, 3), device=dev), torch.zeros(10, device=dev))
+    assert e.value.status == NPCF_EINVAL
+    est.close()
+
+
 # ------------------------------------------------------------------ 6PCF
 
 @pytest.mark.parametrize("n,lmax,nr,allparity", [
