@@ -133,6 +133,22 @@ npcf_status npcf_cache_data(npcf_ctx* ctx, const float* d_pos, const float* d_w,
 npcf_status npcf_accumulate_split(npcf_ctx* ctx, const float* d_pos, const float* d_w, int64_t n,
                                   void* stream);
 
+/* Gridded data (Sec. 3.2.2, Eq. alm-binned-def-fft): a density field delta on a periodic
+ * ngrid^3 mesh over the context's box (cell side h = box / ngrid; d_delta: device float32
+ * [ngrid^3], cells x fastest, then y, z; caller-owned; 1 <= ngrid <= 406). Adds to the
+ * accumulators the multiplets of the field with every cell a primary and a secondary of
+ * weight delta at its centre: the harmonic coefficients of every cell come from FFTs (the
+ * correlation of delta with the kernel Y_lm(unit(r)) Theta^b(r) sampled on cell offsets,
+ * whose shell is the FP32 rule on the offset's separation), then the same contractions
+ * as for particles. Equal, up to FP32 rounding, to npcf_accumulate of the cell centres with
+ * weights delta when the cell-centre coordinates are exact in FP32. Raw sums (the
+ * normalisation of npcf_finalize is for particle catalogs); pair counts and the sum of
+ * weights are not updated. Keeps the kernel spectra of the mesh in the context (nr x
+ * (lmax+1)(lmax+2)/2 x ngrid^3 x 16 bytes, plus one such field set per shell and one
+ * spectrum of delta); FP64 transforms by cuFFT. NPCF_EUNSUPPORTED without a periodic
+ * box; NPCF_ENOMEM when the spectra do not fit. */
+npcf_status npcf_accumulate_grid(npcf_ctx* ctx, const float* d_delta, int ngrid, void* stream);
+
 /* Number of doubles npcf_finalize writes. */
 npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len);
 

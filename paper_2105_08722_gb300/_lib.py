@@ -28,6 +28,7 @@ SIGNATURES = {
     "npcf_accumulate_host": (_i, [_vp, _vp, _vp, _i64, _vp]),
     "npcf_cache_data": (_i, [_vp, _vp, _vp, _i64, _vp]),
     "npcf_accumulate_split": (_i, [_vp, _vp, _vp, _i64, _vp]),
+    "npcf_accumulate_grid": (_i, [_vp, _vp, _i, _vp]),
     "npcf_output_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "npcf_layout": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp, _vp]),
     "npcf_finalize": (_i, [_vp, _vp, _sz, _i]),
@@ -212,6 +213,12 @@ class NPCF:
         n = int(pos.shape[0])
         self._check(self._lib.npcf_accumulate_split(self._h, _ptr(pos) if n else None, _ptr(w) if n else None, n,
                                                     _stream_handle(stream)))
+
+    def accumulate_grid(self, delta, stream=None):
+        """A density field on a periodic n^3 mesh over the box (npcf_accumulate_grid):
+        delta, CUDA float32 tensor [n, n, n] indexed [z, y, x] (x fastest in memory)."""
+        n = int(delta.shape[-1])
+        self._check(self._lib.npcf_accumulate_grid(self._h, _ptr(delta), n, _stream_handle(stream)))
 
     def accumulate_host(self, pos: np.ndarray, w: np.ndarray, stream=None):
         pos = np.ascontiguousarray(pos, dtype=np.float32)

@@ -74,7 +74,9 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + ".tmp%d" % os.getpid()
-    link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcufft", "-lcudart_static", "-lrt", "-lpthread", "-ldl",
+                                                          "-Xlinker", "-rpath," + cuda_lib]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

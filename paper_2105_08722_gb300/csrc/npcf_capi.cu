@@ -135,6 +135,8 @@ struct npcf_ctx {
     DevBuf<unsigned long long> sd_counts;
     DevBuf<long long> sd_off;      // {0, n_data, 0, n_randoms}
     int64_t sd_n = 0;              // data points cached (0: none)
+    // gridded fields: FFT plans, kernel spectra and work fields (created on first use)
+    GridFFT* gfft = nullptr;
     // catalogs the accumulators hold (0: none yet; fixed by the first accumulate call)
     int ncat = 0;
     // tables of the current batch (host copies decide whether an upload is needed)
@@ -683,51 +685,11 @@ bool same_table(const DevBuf<T>& b, const std::vector<T>& host, const std::vecto
     return b.p && host.size() == v.size() && std::memcmp(host.data(), v.data(), v.size() * sizeof(T)) == 0;
 }
 
-// Host part of an accumulate call: validation, grid, buffers and the tables of this batch
-// (catalog offsets, contraction chunks). Uploads happen only when a table changes, so a
-// repeated call with the same shapes does no synchronous work here.
-npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const std::vector<long long>& off,
-                    cudaStream_t s, Plan& P, const float* d_pos2 = nullptr, int n2 = 0) {
+// Contraction chunks of a batch (primary ranges that never cross a catalog), the catalog
+// offsets and the chunk rows of the FP64 partial sums.
+npcf_status plan_chunks(npcf_ctx* ctx, const std::vector<long long>& off, Plan& P) {
     const long long n64 = off.back();
     const int ncat = (int)off.size() - 1;
-    if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", n64);
-    if (n64 >= (int64_t(1) << 26))
-        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^26 points per call", n64);
-    if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
-    if (ctx->ncat != 0 && ctx->ncat != ncat)
-        return fail(ctx, NPCF_EINVAL, "the accumulators hold %d catalogs, this call has %d (npcf_reset first)",
-                    ctx->ncat, ncat);
-    const int n = (int)n64;
-    P.n = n;
-    P.ncat = ncat;
-    if (ctx->ncat == 0) {
-        // the first call fixes how many catalogs the accumulators hold
-        CU(ctx->zeta.ensure((size_t)ncat * std::max(ctx->total, 1)));
-        CU(ctx->counts.ensure((size_t)ncat * ctx->nr));
-        CU(ctx->sumw.ensure(ncat));
-        if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, (size_t)ncat * ctx->total * sizeof(double)));
-        CU(cudaMemset(ctx->counts.p, 0, (size_t)ncat * ctx->nr * sizeof(unsigned long long)));
-        CU(cudaMemset(ctx->sumw.p, 0, ncat * sizeof(double)));
-        ctx->ncat = ncat;
-    }
-    npcf_status st = setup_grid(ctx, d_pos, d_pos2 ? n - n2 : n, ncat, s, d_pos2, n2);
-    if (st != NPCF_OK) return st;
-    const GridInfo& g = ctx->grid;
-    const size_t cells = (size_t)g.ncell * ncat;
-    if (cells >= (size_t)1 << 31) return fail(ctx, NPCF_EUNSUPPORTED, "%zu cells in the batch's grids", cells);
-
-    CU(ctx->pts.ensure(n));
-    CU(ctx->wp.ensure(n));
-    CU(ctx->idx.ensure(n));
-    CU(ctx->cell_of.ensure(n));
-    CU(ctx->cid.ensure(n));
-    CU(ctx->alm.ensure((size_t)n * ctx->nr * ctx->nlm));
-    CU(ctx->cnt.ensure((size_t)n * ctx->nr));
-    CU(ctx->count.ensure(cells));
-    CU(ctx->start.ensure(cells + 1));
-    CU(ctx->cursor.ensure(cells));
-    CU(ctx->work.ensure(4));
-
     // contraction chunks of the 3PCF and 5PCF kernels: ranges of about n / (4 x SMs)
     // primaries (a multiple of 64), never crossing a catalog
     const int waves = 4;
@@ -775,6 +737,57 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
         ctx->h_cbeg = cbeg;
     }
     CU(ctx->partial.ensure((size_t)std::max({P.nchunk, P.nchunk4, 1}) * std::max(ctx->total, 1)));
+
+    return NPCF_OK;
+}
+
+// Host part of an accumulate call: validation, grid, buffers and the tables of this batch
+// (catalog offsets, contraction chunks). Uploads happen only when a table changes, so a
+// repeated call with the same shapes does no synchronous work here.
+npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const std::vector<long long>& off,
+                    cudaStream_t s, Plan& P, const float* d_pos2 = nullptr, int n2 = 0) {
+    const long long n64 = off.back();
+    const int ncat = (int)off.size() - 1;
+    if (n64 < 0 || n64 >= (int64_t(1) << 31)) return fail(ctx, NPCF_EINVAL, "n = %lld out of range", n64);
+    if (n64 >= (int64_t(1) << 26))
+        return fail(ctx, NPCF_EUNSUPPORTED, "n = %lld: the pair kernel indexes at most 2^26 points per call", n64);
+    if (!d_pos || !d_w) return fail(ctx, NPCF_EINVAL, "null position or weight pointer");
+    if (ctx->ncat != 0 && ctx->ncat != ncat)
+        return fail(ctx, NPCF_EINVAL, "the accumulators hold %d catalogs, this call has %d (npcf_reset first)",
+                    ctx->ncat, ncat);
+    const int n = (int)n64;
+    P.n = n;
+    P.ncat = ncat;
+    if (ctx->ncat == 0) {
+        // the first call fixes how many catalogs the accumulators hold
+        CU(ctx->zeta.ensure((size_t)ncat * std::max(ctx->total, 1)));
+        CU(ctx->counts.ensure((size_t)ncat * ctx->nr));
+        CU(ctx->sumw.ensure(ncat));
+        if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, (size_t)ncat * ctx->total * sizeof(double)));
+        CU(cudaMemset(ctx->counts.p, 0, (size_t)ncat * ctx->nr * sizeof(unsigned long long)));
+        CU(cudaMemset(ctx->sumw.p, 0, ncat * sizeof(double)));
+        ctx->ncat = ncat;
+    }
+    npcf_status st = setup_grid(ctx, d_pos, d_pos2 ? n - n2 : n, ncat, s, d_pos2, n2);
+    if (st != NPCF_OK) return st;
+    const GridInfo& g = ctx->grid;
+    const size_t cells = (size_t)g.ncell * ncat;
+    if (cells >= (size_t)1 << 31) return fail(ctx, NPCF_EUNSUPPORTED, "%zu cells in the batch's grids", cells);
+
+    CU(ctx->pts.ensure(n));
+    CU(ctx->wp.ensure(n));
+    CU(ctx->idx.ensure(n));
+    CU(ctx->cell_of.ensure(n));
+    CU(ctx->cid.ensure(n));
+    CU(ctx->alm.ensure((size_t)n * ctx->nr * ctx->nlm));
+    CU(ctx->cnt.ensure((size_t)n * ctx->nr));
+    CU(ctx->count.ensure(cells));
+    CU(ctx->start.ensure(cells + 1));
+    CU(ctx->cursor.ensure(cells));
+    CU(ctx->work.ensure(4));
+
+    npcf_status cst = plan_chunks(ctx, off, P);
+    if (cst != NPCF_OK) return cst;
 
     PairArgs& pa = P.pa;
     pa = PairArgs{};
@@ -1369,6 +1382,48 @@ npcf_status npcf_accumulate_split(npcf_ctx* ctx, const float* d_pos, const float
     return run_split(ctx, d_pos, d_w, n, (cudaStream_t)stream);
 }
 
+npcf_status npcf_accumulate_grid(npcf_ctx* ctx, const float* d_delta, int ngrid, void* stream) {
+    if (check_ctx(ctx) != NPCF_OK) return NPCF_EINVAL;
+    if (!(ctx->box > 0)) return fail(ctx, NPCF_EUNSUPPORTED, "gridded fields need a periodic box");
+    if (ngrid < 1 || ngrid > 406) return fail(ctx, NPCF_EINVAL, "ngrid %d outside [1, 406]", ngrid);
+    if (!d_delta) return fail(ctx, NPCF_EINVAL, "null field pointer");
+    if (ctx->ncat > 1) return fail(ctx, NPCF_EINVAL, "the accumulators hold a batch (npcf_reset first)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long cells = (long long)ngrid * ngrid * ngrid;
+    if (ctx->ncat == 0) {
+        CU(ctx->zeta.ensure(std::max(ctx->total, 1)));
+        CU(ctx->counts.ensure(ctx->nr));
+        CU(ctx->sumw.ensure(1));
+        if (ctx->total > 0) CU(cudaMemset(ctx->zeta.p, 0, (size_t)ctx->total * sizeof(double)));
+        CU(cudaMemset(ctx->counts.p, 0, (size_t)ctx->nr * sizeof(unsigned long long)));
+        CU(cudaMemset(ctx->sumw.p, 0, sizeof(double)));
+        ctx->ncat = 1;
+    }
+    Plan P;
+    P.n = (int)cells;
+    P.ncat = 1;
+    npcf_status st = plan_chunks(ctx, std::vector<long long>{0, cells}, P);
+    if (st != NPCF_OK) return st;
+    CU(ctx->alm.ensure((size_t)cells * ctx->nr * ctx->nlm));
+    CU(ctx->wp.ensure((size_t)cells));
+    CU(ctx->work.ensure(4));
+    if (!ctx->gfft) ctx->gfft = gridfft_create();
+    GridFFTArgs ga{};
+    for (int i = 0; i <= ctx->nr; ++i) ga.e2[i] = ctx->e2[i];
+    ga.nr = ctx->nr;
+    ga.lmax = ctx->lmax;
+    const bool timed = ctx->timed;
+    if (timed) CU(cudaEventRecord(ctx->ev[0], s));
+    if (timed) CU(cudaEventRecord(ctx->ev[1], s));
+    CU(cudaMemsetAsync(ctx->work.p, 0, 4 * sizeof(int), s));
+    char msg[256] = {};
+    const int rc = gridfft_alm(ctx->gfft, d_delta, ngrid, (float)ctx->box, ga, ctx->alm.p, ctx->wp.p, s, msg, sizeof(msg));
+    if (rc != 0) return fail(ctx, rc == 2 ? NPCF_ENOMEM : NPCF_ECUDA, "gridded a_lm: %s", msg);
+    ctx->last_n = 0;   // the a_lm of this call are cells', not particles' (no npcf_debug_alm)
+    if (timed) CU(cudaEventRecord(ctx->ev[2], s));
+    return enqueue_contract(ctx, P, s, timed);
+}
+
 npcf_status npcf_output_size(const npcf_ctx* ctx, size_t* len) {
     if (!ctx || !len) return NPCF_EINVAL;
     *len = (size_t)ctx->total;
@@ -1800,6 +1855,7 @@ void npcf_destroy(npcf_ctx* ctx) {
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gfft) gridfft_destroy(ctx->gfft);
     delete ctx;  // device buffers are released by their destructors
 }
 

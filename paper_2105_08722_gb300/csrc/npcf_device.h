@@ -247,6 +247,20 @@ size_t contract6_smem_bytes(const Contract6Args& a);
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- gridded fields (FFT)
+// a_lm of a density field on a periodic n^3 mesh by FFT (npcf_fftgrid.cu).
+struct GridFFTArgs {
+    float e2[kMaxNr + 1];      // squared shell edges of the FP32 rule
+    int nr, lmax;
+};
+struct GridFFT;
+GridFFT* gridfft_create();
+void gridfft_destroy(GridFFT* g);
+// alm [n^3][nr][nlm] (cells x fastest) and wp [n^3] = delta; 0 on success, 2 (out of
+// memory) or 3 (CUDA or cuFFT error) with a message in err.
+int gridfft_alm(GridFFT* G, const float* delta, int n, float box, const GridFFTArgs& a, float2* alm, float* wp,
+                cudaStream_t s, char* err, size_t errlen);
+
 // ---------------------------------------------------------------- edge correction (a7)
 struct EdgeArgs {
     const double* nraw;        // [nl][nb] raw multiplets of the data-minus-randoms run
