@@ -721,6 +721,200 @@ def run_gpu_5pcf(args):
     return 0
 
 
+def run_gpu_6pcf(args):
+    """6PCF: 50k log-normal points, periodic 1000 Mpc/h, 8 shells 20-160, lmax 2 (327
+    parity-even multiplets with intermediates up to 2 lmax, 56 bin tuples). One step = one
+    npcf_accumulate."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    wl = catalogs.lognormal_6pcf()
+    est = NPCF(wl.lmax, wl.orders, wl.edges, wl.box, FP32)
+    pos, w = torch.from_numpy(wl.pos).to(dev), torch.from_numpy(wl.w).to(dev)
+    ms, clk = _timed_steps(args, lambda: est.accumulate(pos, w), dev)
+    st = est.timings()
+    line = {
+        "metric": "primaries/sec for the 6PCF (lmax=2, 8 shells)", "value": wl.n / (ms * 1e-3),
+        "unit": "primaries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "lognormal_50k_L1000_6pcf_lmax2_nr8_20-160", "n_points": wl.n,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
+        "gpu_launches": (KERNELS_PER_STEP - 2) * args.steps,
+        "stages_ms": {"cell_list": float(st[0]), "pair": float(st[1]), "contraction": float(st[2]),
+                      "reduction": float(st[3])},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
+def run_gpu_survey_splits(args):
+    """Survey data (400k, weight +1) with 1.6M randoms in 4 splits (weights -N_D/N_k), 3PCF +
+    4PCF, lmax 5, 10 shells, open geometry: the 4 data-minus-randoms splits co-added (Sec.
+    4.2), once through npcf_accumulate of each concatenated split and once with the data
+    harmonics kept (npcf_cache_data once, then npcf_accumulate_split per split). One step =
+    the whole set of splits (the cached arm includes its npcf_cache_data)."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    d, wd, splits, edges = catalogs.survey_splits()
+    lmax, orders = 5, (3, 4)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dd, dw = t(d), t(wd)
+    cat = [(t(np.concatenate([d, r])), t(np.concatenate([wd, wr]))) for r, wr in splits]
+    rs = [(t(r), t(wr)) for r, wr in splits]
+    plain = NPCF(lmax, orders, edges, 0.0, FP32)
+    cached = NPCF(lmax, orders, edges, 0.0, FP32)
+
+    def step_plain():
+        plain.reset()
+        for p_, w_ in cat:
+            plain.accumulate(p_, w_)
+
+    def step_cached():
+        cached.reset()
+        cached.cache_data(dd, dw)
+        for p_, w_ in rs:
+            cached.accumulate_split(p_, w_)
+
+    ms_plain, _ = _timed_steps(args, step_plain, dev)
+    ms_cached, clk = _timed_steps(args, step_cached, dev)
+    a, b = plain.finalize(), cached.finalize()
+    rel = float(np.max(np.abs(a - b)) / np.sqrt(np.mean(a ** 2)))
+    prim = sum(len(d) + len(r) for r, _ in splits)
+    line = {
+        "metric": "primaries/sec for the survey D-R 4PCF + 3PCF over 4 random splits (lmax=5, 10 shells)",
+        "value": prim / (ms_cached * 1e-3), "unit": "primaries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_cached, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "survey_400k_data_4x400k_random_splits_4pcf3pcf_lmax5_nr10_20-160",
+                   "n_primaries_per_step": prim, "l2": "inputs larger than L2", "parallelism": "single GPU"},
+        "without_cache": {"value": prim / (ms_plain * 1e-3), "ms_per_step": ms_plain},
+        "max_diff_vs_without_cache_over_rms": rel,
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
+def run_gpu_grid(args):
+    """Gridded field (Sec. 3.2.2): the log-normal overdensity on a 64^3 mesh in a periodic
+    1000 Mpc/h box, 3PCF + 4PCF, lmax 5, 10 shells 20-160; a_lm of every cell by FFT, cells
+    as primaries. One step = one npcf_accumulate_grid (kernel spectra kept from warm-up)."""
+    import torch
+
+    from paper_2105_08722_gb300 import build, catalogs
+    build()
+    from paper_2105_08722_gb300._lib import NPCF, FP32
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    n = args.ngrid
+    delta = torch.from_numpy(catalogs.lognormal_mesh(n, 1000.0, seed=1007)).to(dev)
+    est = NPCF(5, (3, 4), catalogs.linear_edges(20.0, 160.0, 10), 1000.0, FP32)
+    ms, clk = _timed_steps(args, lambda: est.accumulate_grid(delta), dev)
+    st = est.timings()
+    cells = n ** 3
+    line = {
+        "metric": "cells/sec for the 4PCF + 3PCF of a gridded field (lmax=5, 10 shells)",
+        "value": cells / (ms * 1e-3), "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 FFT, f32",
+        "data": "synthetic",
+        "config": {"workload": "lognormal_mesh_%d3_L1000_4pcf3pcf_lmax5_nr10_20-160" % n, "cells": cells,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
+        "stages_ms": {"fft_alm": float(st[1]), "contraction": float(st[2]), "reduction": float(st[3])},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
+def run_fp16_range(args):
+    """Range of the contraction operands the FP16-scaled precision would have to hold, on
+    the 200k log-normal workload: for a seeded sample of primaries, their a_lm (from the
+    GPU, npcf_debug_alm) as the contraction kernels hold them (reduced harmonics a_lm /
+    sqrt((2l+1)/(4 pi))) and the 4PCF products P^{L,m3}(b1,b2) = sum_m1 E C a^{b1} a^{b2} of
+    those (couplings from the library, npcf_coupling); per primary the largest |P| and |a|.
+    A GEMM over primaries with one scale s_p per primary (A = P / s_p, B = a s_p) fits FP16
+    only if max|P| max|a| <= 65504^2."""
+    import torch
+
+    from paper_2105_08722_gb300 import build
+    build()
+    from paper_2105_08722_gb300 import _lib
+    from paper_2105_08722_gb300._lib import NPCF, FP32
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    wl = lognormal_workload(args.n)
+    est = NPCF(wl.lmax, (3,), wl.edges, wl.box, FP32)
+    est.accumulate(torch.from_numpy(wl.pos).to(dev), torch.from_numpy(wl.w).to(dev))
+    rng = np.random.default_rng(909)
+    sample = np.sort(rng.choice(wl.n, args.fp16_sample, replace=False))
+    a_pos, _ = est.debug_alm(sample)                    # [k, nr, nlm] complex, m >= 0
+    k, nr, lmax = len(sample), len(wl.edges) - 1, wl.lmax
+    a = {}
+    for l in range(lmax + 1):
+        for m in range(l + 1):
+            v = a_pos[:, :, l * (l + 1) // 2 + m].astype(np.complex128)
+            a[(l, m)] = v
+            if m:
+                a[(l, -m)] = ((-1) ** m) * np.conj(v)
+    # the contraction kernels work on the reduced harmonics a_lm / sqrt((2l+1)/(4 pi))
+    red = np.array([math.sqrt(4.0 * math.pi / (2 * l + 1)) for l in range(lmax + 1) for m in range(l + 1)])
+    for key in list(a):
+        a[key] = a[key] * math.sqrt(4.0 * math.pi / (2 * key[0] + 1))
+    amax = np.max(np.abs(a_pos * red[None, None, :]), axis=(1, 2))
+    pmax = np.zeros(k)
+    iu = np.triu_indices(nr, 1)
+    for L in _lib.multiplets(4, lmax):
+        l1, l2, l3 = (int(x) for x in L)
+        E = (-1) ** (l1 + l2 + l3)
+        for m3 in range(l3 + 1):
+            P = np.zeros((k, nr, nr), np.complex128)
+            for m1 in range(-l1, l1 + 1):
+                m2 = -m1 - m3
+                if abs(m2) > l2:
+                    continue
+                c = E * _lib.coupling(4, [l1, l2, l3], [m1, m2, m3])
+                if c:
+                    P += c * a[(l1, m1)][:, :, None] * a[(l2, m2)][:, None, :]
+            pmax = np.maximum(pmax, np.max(np.abs(P[:, iu[0], iu[1]]), axis=1))
+    prod = pmax * amax
+    edges_hist = [0, 3, 4, 5, 6, 7, 8, 9, 9.63, 10, 11, 12, 13, 14]
+    hist, _ = np.histogram(np.log10(np.maximum(prod, 1e-30)), bins=edges_hist)
+    limit = 65504.0 ** 2
+    line = {
+        "metric": "FP16 range of the 4PCF contraction operands (reduced harmonics; lmax=5, 10 shells)",
+        "config": {"workload": wl.name if wl.n != 200_000 else WORKLOAD, "primaries_sampled": int(k)},
+        "max_abs_a": {"median": float(np.median(amax)), "p99": float(np.percentile(amax, 99)), "max": float(amax.max())},
+        "max_abs_P": {"median": float(np.median(pmax)), "p99": float(np.percentile(pmax, 99)), "max": float(pmax.max())},
+        "max_P_times_max_a": {"median": float(np.median(prod)), "p99": float(np.percentile(prod, 99)),
+                              "max": float(prod.max())},
+        "log10_histogram": {"bin_edges": edges_hist, "counts": [int(x) for x in hist]},
+        "fraction_beyond_one_fp16_scale": float(np.mean(prod > limit)),
+        "fp16_limit_65504_squared": limit,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -733,11 +927,15 @@ def main():
                     help="points of the 200k log-normal workload at the same density (default 200,000)")
     ap.add_argument("--workload", default="lognormal200k",
                     choices=["uniform4k", "lognormal200k", "survey", "lognormal100k-5pcf", "batch64", "paper4",
-                             "paper5"],
+                             "paper5", "lognormal50k-6pcf", "survey-splits", "grid", "fp16-range"],
                     help="uniform4k: 4,096 uniform points, 3PCF; lognormal200k: one 200k log-normal catalog "
                          "(4PCF + 3PCF); survey: 400k data + 1.6M randoms (D-R and R runs) with edge correction; "
                          "lognormal100k-5pcf: 100k points, 5PCF; batch64: 64 catalogs in one batch; "
-                         "paper4 / paper5: the paper's timing catalog (5e4 uniform, L 1500), 4PCF / 5PCF")
+                         "paper4 / paper5: the paper's timing catalog (5e4 uniform, L 1500), 4PCF / 5PCF; "
+                         "lognormal50k-6pcf: 50k points, 6PCF; survey-splits: 4 random splits with and without "
+                         "the data harmonics kept; grid: a log-normal field on an ngrid^3 mesh by FFT")
+    ap.add_argument("--ngrid", type=int, default=64, help="mesh side of the grid workload")
+    ap.add_argument("--fp16-sample", type=int, default=4096, help="primaries sampled by fp16-range")
     ap.add_argument("--cpu-sample", type=int, default=1500)
     ap.add_argument("--cpu-sample-1core", type=int, default=120)
     ap.add_argument("--ref-sample", type=int, default=400)
@@ -761,6 +959,14 @@ def main():
         return run_gpu_paper(args, 4 if args.workload == "paper4" else 5)
     if args.workload == "survey":
         return run_gpu_survey(args)
+    if args.workload == "lognormal50k-6pcf":
+        return run_gpu_6pcf(args)
+    if args.workload == "survey-splits":
+        return run_gpu_survey_splits(args)
+    if args.workload == "grid":
+        return run_gpu_grid(args)
+    if args.workload == "fp16-range":
+        return run_fp16_range(args)
     return run_gpu(args)
 
 

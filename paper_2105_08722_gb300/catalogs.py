@@ -13,7 +13,10 @@ generators stand in for them:
   1 + delta and placed uniformly inside their cell.
 * ``survey``       -- log-normal data cut to a non-periodic shell-and-cap mask
   (comoving radius 600-1400 Mpc/h, 60 degree cap about +z) plus uniform
-  randoms in the same mask.
+  randoms in the same mask; ``survey_splits`` cuts the randoms into disjoint
+  seeded splits (Sec. 4.2).
+* ``lognormal_mesh`` -- the log-normal overdensity exp(G)/<exp(G)> - 1 itself on a
+  periodic mesh (a gridded field, Sec. 3.2.2).
 
 Positions are float32 in [0, L) for periodic boxes. All draws use numpy's
 PCG64 with explicit seeds.
@@ -64,6 +67,14 @@ def gaussian_field(mesh: int, box: float, rng, slope: float = -1.5, kcut: float 
     c2 = sigma_g ** 2 * mesh ** 3 / psum
     g = np.fft.irfftn(nk * np.sqrt(pk * c2), s=(mesh, mesh, mesh), axes=(0, 1, 2))
     return g
+
+
+def lognormal_mesh(mesh: int, box: float, seed: int, **kw) -> np.ndarray:
+    """Overdensity delta = exp(G) / <exp(G)> - 1 of the log-normal field on a periodic
+    mesh^3 grid (float32, C order; read as [z][y][x] with x fastest)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eg = np.exp(gaussian_field(mesh, box, rng, **kw))
+    return np.ascontiguousarray(eg / eg.mean() - 1.0, dtype=np.float32)
 
 
 def _sample_cells(density: np.ndarray, n: int, rng) -> np.ndarray:
@@ -199,6 +210,24 @@ def survey_dmr_and_randoms(n_data: int = 400_000, n_rand: int = 1_600_000, mesh:
     rr = Workload("survey_R_%dk" % (n_rand // 1000), r, np.full(n_rand, ratio, np.float32),
                   edges, 5, (3, 4), 0.0)
     return dr, rr
+
+
+def survey_splits(n_data: int = 400_000, n_rand: int = 1_600_000, nsplit: int = 4, mesh: int = 256):
+    """Survey data (weight +1) and its randoms cut into nsplit disjoint seeded splits, split k
+    weighted -N_D / N_k (Sec. 4.2: random splits co-added)."""
+    d = survey_data(n_data, seed=1003, mesh=mesh)
+    r = survey_randoms(n_rand, seed=2003)
+    rng = np.random.Generator(np.random.PCG64(4003))
+    parts = np.array_split(rng.permutation(n_rand), nsplit)
+    splits = [(r[np.sort(p)], np.full(len(p), -n_data / len(p), np.float32)) for p in parts]
+    return d, np.ones(n_data, np.float32), splits, linear_edges(20.0, 160.0, 10)
+
+
+def lognormal_6pcf(n: int = 50_000, mesh: int = 128) -> Workload:
+    """50k log-normal points, periodic 1000 Mpc/h cube, 8 shells 20-160, lmax 2, 6PCF."""
+    pos = lognormal_box(n, 1000.0, mesh, seed=1006)
+    return Workload("6pcf_lognormal_%dk_L1000" % (n // 1000), pos, np.ones(n, np.float32),
+                    linear_edges(20.0, 160.0, 8), 2, (6,), 1000.0)
 
 
 def survey_subset(dr: "Workload", rr: "Workload", n_data: int = 4000, n_rand: int = 16000,
