@@ -77,7 +77,10 @@ typedef enum {
  *   order_mask  bit N set to compute the N-point function; N in {3, 4, 5, 6}. The 6PCF
  *               takes at most 8 shells (NPCF_EUNSUPPORTED above; with fewer than 5 it has
  *               no bin tuple and an empty output) and (lmax + 1)^2 x nr x 264 bytes of
- *               shared memory (NPCF_EUNSUPPORTED beyond the device's limit).
+ *               shared memory (NPCF_EUNSUPPORTED beyond the device's limit). The FP32
+ *               4PCF needs nr (lmax + 1)(lmax + 2) / 2 x 264 bytes of shared memory (every
+ *               lmax <= 10 up to 10 shells); the split-BF16 4PCF stages more and takes
+ *               lmax <= 5 (NPCF_EUNSUPPORTED beyond, with the byte count).
  *   nr, edges   nr radial shells (1 <= nr <= 16) with host edges[nr+1] strictly
  *               increasing, edges[0] >= 0 (the binning functions Theta^b, Sec. 3.2).
  *   box         > 0: periodic cube of that side (Table 1 "periodic"); positions must
@@ -232,7 +235,10 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
  * 2048..65536, default 8192; every shell gets at least 128, the rest in proportion to
  * the shell volumes; a bucket that fills is summed early, so larger buckets mean fewer
  * reductions for dense primaries; device scratch of SMs x 16 x 4 bytes per entry),
- * key 5 = pair kernel: consecutive (cell-sorted) primaries per chunk that a block takes
+ * key 4 = FP32 4PCF contraction: 0 (default) stages the coupling terms with a tile of 64
+ * primaries in shared memory where they fit (lmax <= 6 at 4 shells) and takes the
+ * high-lmax kernel (tiles of 32 primaries, terms read through L1) beyond; 1 takes the
+ * high-lmax kernel always, key 5 = pair kernel: consecutive (cell-sorted) primaries per chunk that a block takes
  * from the global counter (1..1024, default 16; small chunks keep a block's warps on
  * nearby primaries, whose neighbourhoods then share L1), key 6 = split-bf16 contraction:
  * steps of 16 primaries between drains of the tensor-memory accumulators into FP64 (>= 1;

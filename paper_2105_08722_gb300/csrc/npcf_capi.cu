@@ -72,6 +72,7 @@ struct npcf_ctx {
     int drain_steps = 2;       // tensor-core contraction: steps of 16 primaries per TMEM drain
     int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
     int use_stab = 1;          // pair kernel: shell by table lookup when the table is valid
+    int c4g_force = 0;         // FP32 4PCF: the high-lmax contraction even where the staged one fits
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -87,6 +88,12 @@ struct npcf_ctx {
     DevBuf<int4> c4segs, c4items;
     DevBuf<int> c4lamseg0;
     int c4nitem = 0, c4nterms = 0, c4nseg = 0, c4nlam = 0;
+    // high-lmax FP32 4PCF contraction (npcf_contract4g.cu): used where the kernel above
+    // does not fit in shared memory, or when tuning key 4 asks for it
+    DevBuf<float4> c4g_coef;
+    DevBuf<int> c4g_tlm;
+    DevBuf<int4> c4g_groups, c4g_pairs, c4g_items;
+    bool c4g_needed = false;
     // tensor-core (split bf16) 4PCF contraction tables
     DevBuf<int4> tc_groups, tc_tiles, tc_runs;
     DevBuf<int> tc_tile_run0;
@@ -582,10 +589,31 @@ npcf_status setup_tables(npcf_ctx* ctx) {
                 int dev = 0, optin = 0;
                 CU(cudaGetDevice(&dev));
                 CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-                if (ctx->prec == NPCF_FP32 && contract4w_smem_bytes(c) + 1024 > (size_t)optin)
-                    return fail(ctx, NPCF_EUNSUPPORTED, "4PCF: %d shells x %d harmonics and %d coupling terms "
-                                "need %zu B of shared memory (limit %d)", ctx->nr, ctx->nlm, ctx->c4nterms,
-                                contract4w_smem_bytes(c), optin);
+                ctx->c4g_needed = contract4w_smem_bytes(c) + 1024 > (size_t)optin;
+                if (ctx->prec == NPCF_FP32 && ctx->c4g_needed &&
+                    contract4g_smem_bytes(ctx->nr, ctx->nlm) + 1024 > (size_t)optin)
+                    return fail(ctx, NPCF_EUNSUPPORTED, "4PCF: a tile of %d shells x %d harmonics needs %zu B of "
+                                "shared memory (limit %d)", ctx->nr, ctx->nlm,
+                                contract4g_smem_bytes(ctx->nr, ctx->nlm), optin);
+            }
+            if (ctx->prec == NPCF_FP32) {
+                ContractTable4G tg = make_contract4g(t);
+                std::vector<int4> itg;   // the same items over segment pairs
+                for (const int4& x : it) {
+                    int a = 0;
+                    while (t.lam_seg0[a] != x.x) ++a;
+                    itg.push_back(make_int4(tg.lam_pair0[a], tg.lam_pair0[a + 1], x.z, x.w));
+                }
+                std::vector<float4> cf(tg.tlm.size());
+                std::vector<int4> gr(tg.groups.size() / 4), pr(tg.pairs.size() / 4);
+                if (!cf.empty()) std::memcpy(cf.data(), tg.coef.data(), cf.size() * sizeof(float4));
+                if (!gr.empty()) std::memcpy(gr.data(), tg.groups.data(), gr.size() * sizeof(int4));
+                if (!pr.empty()) std::memcpy(pr.data(), tg.pairs.data(), pr.size() * sizeof(int4));
+                CU(upload(ctx->c4g_coef, cf));
+                CU(upload(ctx->c4g_tlm, tg.tlm));
+                CU(upload(ctx->c4g_groups, gr));
+                CU(upload(ctx->c4g_pairs, pr));
+                CU(upload(ctx->c4g_items, itg));
             }
             CU(upload(ctx->c4terms, t.terms));
             CU(upload(ctx->c4segs, segs));
@@ -998,6 +1026,28 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
             c.total = ctx->total;
             c.err = ctx->errflag.p;
             launch_contract4_tc(c, P.nchunk4, s);
+        } else if (o.N == 4 && (ctx->c4g_needed || ctx->c4g_force)) {
+            if (ctx->c4nitem == 0) continue;
+            Contract4GArgs c{};
+            c.alm = ctx->alm.p;
+            c.wp = ctx->wp.p;
+            c.n = n;
+            c.nr = ctx->nr;
+            c.nlm = ctx->nlm;
+            c.coef = ctx->c4g_coef.p;
+            c.tlm = ctx->c4g_tlm.p;
+            c.groups = ctx->c4g_groups.p;
+            c.pairs = ctx->c4g_pairs.p;
+            c.items = ctx->c4g_items.p;
+            c.nitem = ctx->c4nitem;
+            c.chunks = ctx->chunks4.p;
+            c.nchunk = P.nchunk4;
+            c.partial = ctx->partial.p;
+            c.total = ctx->total;
+            c.out_off = ctx->order_off[k];
+            c.nout = o.n_lambda() * o.n_bins();
+            c.chunk_counter = ctx->work.p + 1;
+            launch_contract4g(c, contract4w_blocks(ctx->nsm, P.nchunk4), s);
         } else if (o.N == 4) {
             if (ctx->c4nitem == 0) continue;
             Contract4WArgs c{};
@@ -1813,6 +1863,10 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
                 return fail(ctx, NPCF_EINVAL, "pair bucket entries per warp must be a multiple of 256 in "
                             "[2048, 65536]");
             ctx->pair_cap = value;
+            return NPCF_OK;
+        case 4:
+            if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "high-lmax 4PCF contraction is 0 or 1");
+            ctx->c4g_force = value;
             return NPCF_OK;
         case 5:
             if (value < 1 || value > 1024) return fail(ctx, NPCF_EINVAL, "primaries per chunk in [1, 1024]");

@@ -140,6 +140,29 @@ void launch_contract4w(const Contract4WArgs& a, int nblocks, cudaStream_t s);
 size_t contract4w_smem_bytes(const Contract4WArgs& a);
 int contract4w_blocks(int nsm, int nchunk);
 
+// 4PCF contraction for lmax beyond what the kernel above stages (npcf_contract4g.cu):
+// one primary per lane, coupling terms read through L1, two m3 segments at a time with
+// their terms grouped by the a^{b2} row they read.
+struct Contract4GArgs {
+    const float2* alm;         // [n][nr][nlm]
+    const float* wp;           // [n] primary weights
+    int n, nr, nlm;
+    const float4* coef;        // per term (cA, cB, cC, cD)
+    const int* tlm;            // per term: lm of a^{b1}_{l1 |m1|}
+    const int4* groups;        // (first term of segment 0, of segment 1, end, lm of a^{b2}_{l2 |m2|})
+    const int4* pairs;         // per segment pair: (first group, end, lm of a_{l3 m3} of segment 0,
+                               //   of segment 1 or -1), (2 S(m3) bits of both, m3 == 0 of segment 0, 0)
+    const int4* items;         // (first pair of L, end, b1 | odd << 8 | (nr - 1 - b1) << 16, first output)
+    int nitem;
+    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
+    int nchunk;
+    double* partial;           // [nchunk][total]: chunk c sums into row c
+    int total, out_off, nout;
+    int* chunk_counter;        // zeroed before the launch
+};
+void launch_contract4g(const Contract4GArgs& a, int nblocks, cudaStream_t s);
+size_t contract4g_smem_bytes(int nr, int nlm);
+
 // 4PCF contraction on the tensor cores (split bf16, fp32 accumulation in tensor memory).
 // Rows (multiplet, b1, b2) are grouped by (l3, parity); each group's rows form 128-row
 // tiles whose 128 x 16 (b3) accumulators stay in tensor memory for a block's whole chunk

@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 
 namespace npcf {
 
@@ -289,6 +290,56 @@ ContractTable4 make_contract4(const OrderTable& o) {
     }
     t.lam_seg0.push_back((int)t.seg_begin.size());
     return t;
+}
+
+ContractTable4G make_contract4g(const ContractTable4& t) {
+    ContractTable4G p;
+    auto bits = [](float f) {
+        int b;
+        std::memcpy(&b, &f, 4);
+        return b;
+    };
+    const int na = (int)t.lam_seg0.size() - 1;
+    for (int a = 0; a < na; ++a) {
+        p.lam_pair0.push_back((int)(p.pairs.size() / 8));
+        const int s0 = t.lam_seg0[a], s1 = t.lam_seg0[a + 1];
+        for (int sa = s0; sa < s1; sa += 2) {
+            const int sb = sa + 1 < s1 ? sa + 1 : -1;
+            const bool m0 = t.seg_factor[sa] == 1.0f;   // m3 = 0: a_{l3 0} is real
+            p.pairs.push_back((int)(p.groups.size() / 4));
+            // distinct lm2 of the two segments, ascending
+            std::vector<int> lm2s;
+            for (int sg : {sa, sb}) {
+                if (sg < 0) continue;
+                for (int i = t.seg_begin[sg]; i < t.seg_end[sg]; ++i) lm2s.push_back(t.terms[i].lm2);
+            }
+            std::sort(lm2s.begin(), lm2s.end());
+            lm2s.erase(std::unique(lm2s.begin(), lm2s.end()), lm2s.end());
+            for (int lm2 : lm2s) {
+                for (int sg : {sa, sb}) {
+                    p.groups.push_back((int)p.tlm.size());
+                    if (sg < 0) continue;
+                    for (int i = t.seg_begin[sg]; i < t.seg_end[sg]; ++i) {
+                        const PairTerm& q = t.terms[i];
+                        if (q.lm2 != lm2) continue;
+                        p.coef.insert(p.coef.end(), {q.cA, q.cB, q.cC, q.cD});
+                        p.tlm.push_back((int)q.lm1);
+                    }
+                }
+                p.groups.push_back((int)p.tlm.size());
+                p.groups.push_back(lm2);
+            }
+            p.pairs.push_back((int)(p.groups.size() / 4));
+            p.pairs.push_back(t.seg_lm3[sa]);
+            p.pairs.push_back(sb >= 0 ? t.seg_lm3[sb] : -1);
+            p.pairs.push_back(bits(t.seg_factor[sa]));
+            p.pairs.push_back(sb >= 0 ? bits(t.seg_factor[sb]) : 0);
+            p.pairs.push_back(m0 ? 1 : 0);
+            p.pairs.push_back(0);
+        }
+    }
+    p.lam_pair0.push_back((int)(p.pairs.size() / 8));
+    return p;
 }
 
 ContractTable5 make_contract5(const OrderTable& o) {

@@ -88,6 +88,22 @@ struct ContractTable4 {
 
 ContractTable4 make_contract4(const OrderTable& o);
 
+// The same terms regrouped for the high-lmax kernel, which holds two segments of one
+// multiplet at a time: segments m3 = 0..l3 are taken in pairs (0,1), (2,3), ..., and within
+// a pair the terms are grouped by the stored harmonic a^{b2}_{l2 |m2|} they read (the
+// first segment's terms, then the second's), so each a^{b2} value is loaded once per group.
+// A pair whose first segment has m3 = 0 needs one part of that segment's P only.
+struct ContractTable4G {
+    std::vector<float> coef;        // 4 per term (cA, cB, cC, cD)
+    std::vector<int> tlm;           // lm1 per term
+    std::vector<int> groups;        // 4 per group: first term of segment 0, of segment 1, end, lm2
+    std::vector<int> pairs;         // 8 per pair: first group, end, lm3 of segment 0, of segment 1
+                                    //   (-1 if none), 2 S(m3) bits of both, m3 == 0 of segment 0, 0
+    std::vector<int> lam_pair0;     // first pair of multiplet a (n_lambda + 1 entries)
+};
+
+ContractTable4G make_contract4g(const ContractTable4& t);
+
 // 5PCF coupling tables: the distinct (l1 l2 l12) and (l12 l3 l4) triples of the order's
 // multiplets, each with one term segment per m12 = 0..l12:
 //   P12: terms over m1 with m2 = m12 - m1, coefficient (l1 l2 l12; m1, m2, -m12);

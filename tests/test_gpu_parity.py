@@ -168,22 +168,26 @@ def test_3pcf_uniform_4096_box250_full(torch_dev):
     assert_orders_close(got, want, wl.orders, wl.lmax, len(wl.edges) - 1)
 
 
+@pytest.mark.parametrize("highl", [0, 1])
 @pytest.mark.parametrize("nr,lmax,n", [(3, 4, 1500), (13, 3, 2100), (16, 2, 901)])
-def test_4pcf_shell_counts_and_ragged_tiles(torch_dev, nr, lmax, n):
-    # the FP32 contraction specialises on the number of shells after b1 and takes
-    # primaries in tiles of 64: few and many shells, n not a multiple of the tile
+def test_4pcf_shell_counts_and_ragged_tiles(torch_dev, nr, lmax, n, highl):
+    # the FP32 contractions specialise on the number of shells after b1 and take
+    # primaries in tiles of 64 (staged coupling terms) or 32 (the high-lmax kernel, forced
+    # by tuning key 4): few and many shells, n not a multiple of either tile
     pos, w = _catalog(n, 160.0, 900 + nr)
     edges = np.linspace(4.0, 40.0, nr + 1)
-    _, got, _ = gpu_run(torch_dev, pos, w, (4,), lmax, edges, 160.0, allparity=True)
+    _, got, _ = gpu_run(torch_dev, pos, w, (4,), lmax, edges, 160.0, allparity=True,
+                        tuning={4: highl})
     want, _ = oracle.npcf(pos, w, (4,), lmax, edges, 160.0, allparity=True)
     assert_orders_close(got, want, (4,), lmax, nr, allparity=True)
 
 
-def test_4pcf_3pcf_periodic_lmax5_10_shells(torch_dev):
+@pytest.mark.parametrize("highl", [0, 1])
+def test_4pcf_3pcf_periodic_lmax5_10_shells(torch_dev, highl):
     pos = catalogs.lognormal_box(2500, 300.0, 64, seed=31)
     w = np.ones(len(pos), np.float32)
     edges = np.linspace(8.0, 60.0, 11)
-    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 5, edges, 300.0)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 5, edges, 300.0, tuning={4: highl})
     want, wcounts = oracle.npcf(pos, w, (3, 4), 5, edges, 300.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (3, 4), 5, 10)
@@ -192,9 +196,10 @@ def test_4pcf_3pcf_periodic_lmax5_10_shells(torch_dev):
 @pytest.mark.parametrize("lmax", [6, 8, 10])
 def test_high_lmax_3pcf_and_4pcf_or_refusal(torch_dev, lmax):
     # the paper's lmax = 10 setting on a small catalog. The 3PCF takes any lmax <= 10; the
-    # 4PCF contractions stage the coupling terms and a tile of a_lm (split-bf16: also one
-    # 128-row operand slab per m3) in shared memory and are refused at create (or
-    # accumulate) where those exceed it: FP32 beyond lmax 6, split-bf16 beyond lmax 5
+    # FP32 4PCF stages the coupling terms and a tile of a_lm up to lmax 6 and switches to
+    # the high-lmax kernel (terms through L1) beyond; the split-bf16 one stages them and
+    # one 128-row operand slab per m3 in shared memory and is refused at create (or
+    # accumulate) where those exceed it, beyond lmax 5
     from paper_2105_08722_gb300._lib import NPCFError
     pos = catalogs.lognormal_box(400, 100.0, 32, seed=81)
     w = np.ones(len(pos), np.float32)
@@ -204,7 +209,7 @@ def test_high_lmax_3pcf_and_4pcf_or_refusal(torch_dev, lmax):
     _, got3, counts = gpu_run(torch_dev, pos, w, (3,), lmax, edges, 100.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got3, want3, (3,), lmax, 4)
-    for prec, tol, lmax_ok in ((0, TOL_FP32, 6), (1, TOL_BF16, 5)):
+    for prec, tol, lmax_ok in ((0, TOL_FP32, 10), (1, TOL_BF16, 5)):
         try:
             _, got, _ = gpu_run(torch_dev, pos, w, (3, 4), lmax, edges, 100.0, prec=prec)
         except NPCFError as e:
@@ -213,11 +218,30 @@ def test_high_lmax_3pcf_and_4pcf_or_refusal(torch_dev, lmax):
             assert_orders_close(got, want, (3, 4), lmax, 4, tol=tol)
 
 
-def test_4pcf_all_parity_non_periodic_weighted(torch_dev):
+def test_4pcf_lmax10_10_shells_paper_setting(torch_dev):
+    # Table 2's 4PCF at lmax = 10 with N_r = 10 shells (the high-lmax kernel), on a small
+    # periodic log-normal catalog against the oracle; and lmax 7 all-parity with 16 shells
+    pos = catalogs.lognormal_box(400, 250.0, 32, seed=83)
+    w = np.ones(len(pos), np.float32)
+    edges = np.linspace(10.0, 80.0, 11)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 10, edges, 250.0)
+    want, wcounts = oracle.npcf(pos, w, (3, 4), 10, edges, 250.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3, 4), 10, 10)
+    pos, w = _catalog(300, 120.0, 84)
+    edges = np.linspace(5.0, 45.0, 17)
+    _, got, _ = gpu_run(torch_dev, pos, w, (4,), 7, edges, 0.0, allparity=True)
+    want, _ = oracle.npcf(pos, w, (4,), 7, edges, 0.0, allparity=True)
+    assert_orders_close(got, want, (4,), 7, 16, allparity=True)
+
+
+@pytest.mark.parametrize("highl", [0, 1])
+def test_4pcf_all_parity_non_periodic_weighted(torch_dev, highl):
     pos, w = _catalog(1500, 120.0, 41)
     w = w - np.float32(0.9)          # mixed-sign weights, like data minus randoms
     edges = np.linspace(6.0, 36.0, 7)
-    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 0.0, allparity=True)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 4, edges, 0.0, allparity=True,
+                             tuning={4: highl})
     want, wcounts = oracle.npcf(pos, w, (3, 4), 4, edges, 0.0, allparity=True)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (3, 4), 4, 6, allparity=True)
