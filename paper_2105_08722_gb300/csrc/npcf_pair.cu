@@ -402,22 +402,17 @@ __device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh
 }
 
 // Append one accepted pair per lane (shell b, -1 for none) to the warp's per-shell
-// buckets; a bucket that cannot take its lanes' entries is summed and emptied first.
+// buckets. The caller has made room: every bucket takes at least a scan step's entries.
 template <int L>
-__device__ __forceinline__ void bucket_insert(const PairArgs& a, PairShared<L>& sh, uint32_t* bucket, float* psum,
-                                              int b, uint32_t entry, float4 pi, int warp, int lane, unsigned lt) {
+__device__ __forceinline__ void bucket_insert(PairShared<L>& sh, uint32_t* bucket, int b, uint32_t entry, int warp,
+                                              unsigned lt) {
     const unsigned gm = __match_any_sync(kFull, b);
     const int rank = __popc(gm & lt);
     const int bi = b < 0 ? kMaxNr : b;
-    int2 ne = sh.ne[warp][bi];
-    if (__any_sync(kFull, ne.x + rank >= ne.y)) {   // rare: some lane's bucket is full
-        const unsigned fullm = __reduce_or_sync(kFull, ne.x + rank >= ne.y ? 1u << bi : 0u);
-        for (unsigned mm = fullm; mm; mm &= mm - 1) flush_shell<L>(a, sh, bucket, psum, __ffs(mm) - 1, pi, warp, lane);
-        ne = sh.ne[warp][bi];
-    }
-    if (b >= 0) __stcg(bucket + ne.x + rank, entry);
+    const int nx = sh.ne[warp][bi].x;
+    if (b >= 0) __stcg(bucket + nx + rank, entry);
     __syncwarp();
-    if (b >= 0 && rank == 0) sh.ne[warp][bi].x = ne.x + __popc(gm);
+    if (b >= 0 && rank == 0) sh.ne[warp][bi].x = nx + __popc(gm);
     __syncwarp();
 }
 
@@ -507,10 +502,16 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const int4* ro
         }
         srow += __popc(__ballot_sync(kFull, d <= lim));   // the run of cursor + lim
         cursor += lim;
+        {
+            // a step adds at most 32 kKC entries to a bucket: sum and empty (rarely) every
+            // bucket with less room left (each holds at least 2 x 32 kKC entries)
+            const int2 ne = sh.ne[warp][lane < nr ? lane : kMaxNr];
+            for (unsigned lowm = __ballot_sync(kFull, lane < nr && ne.y - ne.x < 32 * kKC); lowm; lowm &= lowm - 1)
+                flush_shell<L>(a, sh, bucket, psum, __ffs(lowm) - 1, pi, warp, lane);
+        }
 #pragma unroll
         for (int j = 0; j < kKC; ++j)
-            bucket_insert<L>(a, sh, bucket, psum, b[j], (uint32_t)q[j] | ((uint32_t)code[j] << kIdxBits), pi, warp,
-                             lane, lt);
+            bucket_insert<L>(sh, bucket, b[j], (uint32_t)q[j] | ((uint32_t)code[j] << kIdxBits), warp, lt);
     }
     for (int t = 0; t < nr; ++t)
         if (sh.ne[warp][t].x > sh.boff[t]) flush_shell<L>(a, sh, bucket, psum, t, pi, warp, lane);
