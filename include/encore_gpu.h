@@ -232,8 +232,8 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
  * per chunk, rounded up to a multiple of 64, for every contraction kernel (0 = automatic:
  * about n / (4 x SMs) for the 3PCF and 5PCF, n / SMs for the 4PCF), key 3 = pair kernel:
  * entries of each warp's per-shell buckets of accepted pairs (multiple of 256 in
- * max(1024, 256 x shells)..65536, default 8192; every shell gets at least 256, the rest in
- * proportion to the shell volumes; a bucket with room for less than one scan step (128
+ * max(1024, 512 x shells)..65536, default 8192; every shell gets at least 512, the rest in
+ * proportion to the shell volumes; a bucket with room for less than one scan step (256
  * entries) is summed early, so larger buckets mean fewer reductions for dense primaries;
  * device scratch of SMs x 16 x 4 bytes per entry),
  * key 4 = FP32 4PCF contraction: 0 (default) stages the coupling terms with a tile of 64

@@ -843,18 +843,18 @@ npcf_status prepare(npcf_ctx* ctx, const float* d_pos, const float* d_w, const s
     pa.work = ctx->work.p;
     pa.err = ctx->errflag.p;
     {
-        // buckets: every shell at least 256 entries (twice what one scan step can add),
-        // the rest shared in proportion to the shell volumes (the expected share of pairs
-        // of an unclustered catalog)
-        const int nr = ctx->nr, C = std::max(ctx->pair_cap, 256 * nr);
+        // buckets: every shell at least kPairBucketMin entries (twice what one scan step
+        // can add), the rest shared in proportion to the shell volumes (the expected share
+        // of pairs of an unclustered catalog)
+        const int nr = ctx->nr, C = std::max(ctx->pair_cap, kPairBucketMin * nr);
         const double e0 = ctx->edges[0], en = ctx->edges[nr];
         const double vtot = en * en * en - e0 * e0 * e0;
-        const int spare = C - 256 * nr;
+        const int spare = C - kPairBucketMin * nr;
         pa.boff[0] = 0;
         for (int t = 0; t < nr; ++t) {
             const double lo = ctx->edges[t], hi = ctx->edges[t + 1];
             const double f = (hi * hi * hi - lo * lo * lo) / vtot;
-            pa.boff[t + 1] = pa.boff[t] + 256 + (int)std::floor(f * spare);
+            pa.boff[t + 1] = pa.boff[t] + kPairBucketMin + (int)std::floor(f * spare);
         }
         CU(ctx->bucket.ensure((size_t)ctx->nsm * kPairWarps * pa.boff[nr]));
         pa.bucket = ctx->bucket.p;
@@ -1858,11 +1858,11 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             ctx->chunk_target = value;
             return NPCF_OK;
         case 3:
-            // every shell's bucket gets at least 256 entries (a scan step appends at most
-            // 128 per shell, and a bucket with less room is summed first)
-            if (value < 1024 || value > 65536 || (value % 256) || value < 256 * ctx->nr)
+            // every shell's bucket gets at least kPairBucketMin = 512 entries (a scan step
+            // appends at most 256 per shell, and a bucket with less room is summed first)
+            if (value < 1024 || value > 65536 || (value % 256) || value < kPairBucketMin * ctx->nr)
                 return fail(ctx, NPCF_EINVAL, "pair bucket entries per warp must be a multiple of 256 in "
-                            "[max(1024, 256 x shells), 65536]");
+                            "[max(1024, %d x shells), 65536]", kPairBucketMin);
             ctx->pair_cap = value;
             return NPCF_OK;
         case 4:

@@ -57,6 +57,9 @@ void launch_bin(const BinArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------- pair kernel (a2 + a3)
 constexpr int kPairWarps = 16;     // independent warps per pair-kernel block (one block per SM)
 constexpr int kPairShellTab = 512; // bins of r2 of the pair kernel's shell table
+constexpr int kPairKC = 8;         // pair kernel: candidates per lane per scan step
+// smallest per-shell bucket: twice the entries one scan step can add to a shell
+constexpr int kPairBucketMin = 2 * 32 * kPairKC;
 struct PairArgs {
     const float4* pts;         // secondaries: (x, y, z, w) in cell order
     const float* wp;

@@ -19,7 +19,7 @@
 // barrier at which a block idles):
 //   cut: the primary's neighbour rows (cells within r_max, read as runs of the cell-sorted
 //        points) are cut to its x-window and form one flat index space;
-//   scan: each lane tests four candidates a step with the exact FP32 neighbour/shell
+//   scan: each lane tests eight candidates a step with the exact FP32 neighbour/shell
 //        rule, reading them through L1 (the neighbourhoods of a block's primaries
 //        overlap); accepted pairs go straight to per-shell buckets (a private region of
 //        global scratch per warp, sized by shell volume and resident in L2) as (point
@@ -146,7 +146,7 @@ __device__ __forceinline__ int pair_shell_fast(const float4 pj, const float4 pi,
 
 
 constexpr int kShiftCodes = 64;   // 2 bits per axis
-constexpr int kKC = 4;            // candidates per lane per scan step (independent chains)
+constexpr int kKC = kPairKC;      // candidates per lane per scan step (independent chains)
 constexpr int kShellTab = kPairShellTab;
 // Chunk ring of a block (tagged entries). Each warp holds at most one position whose
 // chunk it has not read yet, and a position fetches at most one chunk (two ahead), so at
@@ -504,7 +504,7 @@ __device__ void one_primary(const PairArgs& a, PairShared<L>& sh, const int4* ro
         cursor += lim;
         {
             // a step adds at most 32 kKC entries to a bucket: sum and empty (rarely) every
-            // bucket with less room left (each holds at least 2 x 32 kKC entries)
+            // bucket with less room left (each holds at least kPairBucketMin = 2 x 32 kKC)
             const int2 ne = sh.ne[warp][lane < nr ? lane : kMaxNr];
             for (unsigned lowm = __ballot_sync(kFull, lane < nr && ne.y - ne.x < 32 * kKC); lowm; lowm &= lowm - 1)
                 flush_shell<L>(a, sh, bucket, psum, __ffs(lowm) - 1, pi, warp, lane);

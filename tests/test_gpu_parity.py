@@ -265,15 +265,15 @@ def test_lmax0_single_shell_and_tiny_catalogs(torch_dev):
 
 @pytest.mark.parametrize("tuning", [
     {},                 # every bucket summed once per primary
-    {3: 1024},          # buckets that fill and are summed during the scan
+    {3: 2048},          # buckets that fill and are summed during the scan
     {5: 1},             # one primary per chunk
-    {5: 1000, 3: 1024}, # chunks larger than a block's share, buckets summed during the scan
+    {5: 1000, 3: 2048}, # chunks larger than a block's share, buckets summed during the scan
     {7: 0},             # whole rows, no x-window cut
     {0: 1},             # one cell per r_max: long rows
 ])
 def test_dense_primaries_tuning_variants(torch_dev, tuning):
-    # ~1000 neighbours per primary: with 1024 bucket entries per warp (256 per shell) the
-    # buckets of the outer shells are summed several times per primary
+    # ~1000 neighbours per primary: with 2048 bucket entries per warp (512 per shell) the
+    # buckets of the outer shells are summed during the scan
     pos, w = _catalog(9000, 60.0, 61)
     edges = np.linspace(2.0, 18.0, 5)
     _, got, counts = gpu_run(torch_dev, pos, w, (3, 4), 3, edges, 60.0, tuning=tuning)
@@ -312,12 +312,12 @@ def test_shell_table_and_computed_shell_agree(torch_dev, edges):
 
 
 def test_sixteen_shells_minimum_buckets(torch_dev):
-    # 16 shells and 4096 bucket entries per warp: every shell's bucket holds the minimum
-    # of 256 entries, so nearly every bucket is summed many times per primary
+    # 16 shells and 8192 bucket entries per warp: every shell's bucket holds the minimum
+    # of 512 entries, so the outer buckets are summed during the scan
     pos, w = _catalog(6000, 70.0, 63)
     edges = np.linspace(1.0, 20.0, 17)
     want, wcounts = oracle.npcf(pos, w, (3,), 4, edges, 70.0)
-    for tuning in ({}, {3: 4096}):
+    for tuning in ({}, {3: 8192}):
         _, got, counts = gpu_run(torch_dev, pos, w, (3,), 4, edges, 70.0, tuning=tuning)
         assert np.array_equal(counts, wcounts), tuning
         assert_orders_close(got, want, (3,), 4, 16)
