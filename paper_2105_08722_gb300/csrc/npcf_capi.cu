@@ -81,9 +81,9 @@ struct npcf_ctx {
     // device tables
     DevBuf<float> kmat;
     DevBuf<int4> rows;
-    DevBuf<int2> c3rows, c3pairs;
+    DevBuf<int4> c3items;
     DevBuf<float> c3coef;
-    int c3nrows = 0;
+    int c3nitem = 0;
     DevBuf<PairTerm> c4terms;
     DevBuf<int4> c4segs, c4items;
     DevBuf<int> c4lamseg0;
@@ -527,19 +527,26 @@ npcf_status setup_tables(npcf_ctx* ctx) {
         const OrderTable& o = ctx->orders[k];
         const int off = ctx->order_off[k];
         if (o.N == 3) {
-            std::vector<int2> rows, pairs;
+            // items (l, b1) over the shells b2 > b1; the bins (b1, b2) are in lexicographic
+            // order, so those of one b1 are consecutive
+            std::vector<int4> items;
             std::vector<float> coef;
-            for (int b = 0; b < o.n_bins(); ++b) pairs.push_back(make_int2(o.bins[2 * b], o.bins[2 * b + 1]));
             for (int l = 0; l <= ctx->lmax; ++l) {
                 // E(L) C^{ll}_{m,-m} (-1)^m = (l l 0; 0 0 0) for every m (Eq. N=3-coeff)
                 coef.push_back((float)wigner3j(l, l, 0, 0, 0, 0));
-                for (int b = 0; b < o.n_bins(); ++b) rows.push_back(make_int2(l, b));
+                for (int b1 = 0; b1 + 1 < ctx->nr; ++b1) {
+                    int first = -1;
+                    for (int b = 0; b < o.n_bins() && first < 0; ++b)
+                        if (o.bins[2 * b] == b1 && o.bins[2 * b + 1] == b1 + 1) first = b;
+                    const int nb2 = ctx->nr - 1 - b1;
+                    for (int k = 0; k < nb2; ++k)
+                        if (first < 0 || o.bins[2 * (first + k)] != b1 || o.bins[2 * (first + k) + 1] != b1 + 1 + k)
+                            return fail(ctx, NPCF_EINVAL, "3PCF bins are not in lexicographic order");
+                    items.push_back(make_int4(l, l * (l + 1) / 2, b1 | (nb2 << 16), l * o.n_bins() + first));
+                }
             }
-            ctx->c3nrows = (int)rows.size();
-            if (ctx->c3nrows > 1024)
-                return fail(ctx, NPCF_EUNSUPPORTED, "3PCF with %d outputs exceeds one block", ctx->c3nrows);
-            CU(upload(ctx->c3rows, rows));
-            CU(upload(ctx->c3pairs, pairs));
+            ctx->c3nitem = (int)items.size();
+            CU(upload(ctx->c3items, items));
             CU(upload(ctx->c3coef, coef));
             (void)off;
         } else if (o.N == 4) {
@@ -973,7 +980,7 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
     for (size_t k = 0; k < ctx->orders.size(); ++k) {
         const OrderTable& o = ctx->orders[k];
         if (o.N == 3) {
-            if (ctx->c3nrows == 0) continue;
+            if (ctx->c3nitem == 0) continue;
             Contract3Args c{};
             c.alm = ctx->alm.p;
             c.wp = ctx->wp.p;
@@ -983,14 +990,13 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
             c.lmax = ctx->lmax;
             c.chunks = ctx->chunks.p;
             c.nchunk = P.nchunk;
-            c.rows = ctx->c3rows.p;
-            c.pairs = ctx->c3pairs.p;
+            c.items = ctx->c3items.p;
+            c.nitem = ctx->c3nitem;
             c.coef = ctx->c3coef.p;
-            c.nrows = ctx->c3nrows;
             c.partial = ctx->partial.p;
             c.total = ctx->total;
             c.out_off = ctx->order_off[k];
-            c.nbins = o.n_bins();
+            c.nout = (ctx->lmax + 1) * o.n_bins();
             launch_contract3(c, s);
         } else if (o.N == 4 && ctx->prec == NPCF_SPLIT_BF16) {
             if (ctx->c4nitem == 0) continue;

@@ -4,67 +4,99 @@
 // 3PCF (Eq. N=3-coeff with App. B halving):
 //   zeta_l(b1,b2) = sum_i u_i (l l 0; 0 0 0) sum_{m=-l..l} a^{b1}_{lm} conj(a^{b2}_{lm})
 //                 = sum_i u_i (-1)^l / sqrt(2l+1) [a_{l0} a_{l0} + 2 sum_{m>0} Re(a1 conj a2)].
-// Each block owns a chunk of cell-sorted primaries (a range within one catalog) and a set
-// of output rows; FP32 sums over the chunk go to the chunk's FP64 partial row, and the
-// reduction adds a catalog's rows in chunk order, so results do not depend on scheduling.
+// Each block owns a chunk of cell-sorted primaries (a range within one catalog); FP32 sums
+// over a tile go to the chunk's FP64 partial row, and the reduction adds a catalog's rows
+// in chunk order, so results do not depend on scheduling.
 #include "npcf_device.h"
+#include "npcf_warp.cuh"
 
 namespace npcf {
 namespace {
 
-constexpr int kTile = 8;   // primaries staged in shared memory at a time
+constexpr int kC3Threads = 256;
 
-__device__ __forceinline__ void stage_tile(const float2* __restrict__ alm, const float* __restrict__ wp,
-                                           int p0, int np, int per, float2* X, float* su) {
-    // per = nr * nlm complex values per primary; copy np primaries (contiguous)
-    const float2* src = alm + (size_t)p0 * per;
-    int total = np * per;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) X[i] = src[i];
-    for (int i = threadIdx.x; i < np; i += blockDim.x) su[i] = wp[p0 + i];
+// A primary's staged a_lm: [b][lm] with an odd stride (in float2), so lanes reading the
+// same (b, lm) of different primaries hit different banks.
+__host__ __device__ inline int c3_stride(int nr, int nlm) { return (nr * nlm) | 1; }
+__host__ __device__ inline size_t c3_su_offset(int nr, int nlm, int T) {
+    return ((size_t)T * c3_stride(nr, nlm) * sizeof(float2) + 15) & ~size_t(15);
+}
+__host__ __device__ inline size_t c3_smem(int nr, int nlm, int T) {
+    return c3_su_offset(nr, nlm, T) + (size_t)T * sizeof(float);
 }
 
-__global__ void k_contract3(const Contract3Args a) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    const int per = a.nr * a.nlm;
-    float2* X = reinterpret_cast<float2*>(dsm);
-    float* su = reinterpret_cast<float*>(X + kTile * per);
-    const int chunk = blockIdx.x;
-    const int2 C = a.chunks[chunk];   // primaries [C.x, C.y) of one catalog
-    const int p0 = C.x, p1 = C.y;
-    const int r = threadIdx.x;
-    int l = 0, b1 = 0, b2 = 0, pr = 0;
-    if (r < a.nrows) {
-        int2 rw = a.rows[r];
-        l = rw.x;
-        pr = rw.y;
-        int2 bb = a.pairs[pr];
-        b1 = bb.x;
-        b2 = bb.y;
-    }
-    // FP32 sums over one tile of primaries, folded into FP64 after every tile, so the
-    // rounding does not grow with the chunk length
-    double dacc = 0.0;
-    const int lm0 = l * (l + 1) / 2;
-    for (int t0 = p0; t0 < p1; t0 += kTile) {
-        const int np = min(kTile, p1 - t0);
-        __syncthreads();
-        stage_tile(a.alm, a.wp, t0, np, per, X, su);
-        __syncthreads();
-        if (r < a.nrows) {
-            float acc = 0.f;
-            for (int q = 0; q < np; ++q) {
-                const float2* A1 = X + q * per + b1 * a.nlm + lm0;
-                const float2* A2 = X + q * per + b2 * a.nlm + lm0;
-                float s = A1[0].x * A2[0].x;
-                float s2 = 0.f;
-                for (int m = 1; m <= l; ++m) s2 = fmaf(A1[m].x, A2[m].x, fmaf(A1[m].y, A2[m].y, s2));
-                acc = fmaf(su[q], fmaf(2.f, s2, s), acc);
+// Item (l, b1): lane q of the tile adds u_q sum_m f_m Re(a^{b1}_{lm} conj a^{b2}_{lm}) for the
+// NB2 shells b2 > b1 (f_0 = 1, f_m = 2), the warp reduces the sums across lanes and adds
+// (l l 0; 0 0 0) times them to the outputs (l, b1, b1 + 1 ..), consecutive in the order.
+template <int NB2, int T>
+__device__ __forceinline__ void c3_item(const int4 item, const float2* __restrict__ X, const float* __restrict__ su,
+                                        int nlm, int S, double coef, double* __restrict__ dst, int lane) {
+    const int l = item.x, lm0 = item.y, b1 = item.z & 0xff;
+    float acc[NB2];
+#pragma unroll
+    for (int k = 0; k < NB2; ++k) acc[k] = 0.f;
+    if (lane < T) {
+        const int q = lane;
+        const float2* A1 = X + q * S + b1 * nlm + lm0;
+        const float u = su[q];
+        for (int m = 0; m <= l; ++m) {
+            const float2 x1 = A1[m];
+            const float f = m == 0 ? u : 2.f * u;
+            const float a0 = f * x1.x, a1 = f * x1.y;
+#pragma unroll
+            for (int k = 0; k < NB2; ++k) {
+                const float2 x2 = A1[(k + 1) * nlm + m];
+                acc[k] = fmaf(a0, x2.x, fmaf(a1, x2.y, acc[k]));
             }
-            dacc += (double)acc;
         }
     }
-    if (r < a.nrows && chunk < a.nchunk)
-        a.partial[(size_t)chunk * a.total + a.out_off + l * a.nbins + pr] = (double)a.coef[l] * dacc;
+    using R = warp::TR<NB2>;
+    R::run(acc, lane);
+#pragma unroll
+    for (int i = 0; i < R::F; ++i) {
+        const int e = R::origin(i, lane);
+        if (e >= 0) dst[item.w + e] += coef * (double)acc[i];
+    }
+}
+
+// Primaries on the lanes: a block stages the a_lm of T primaries of its chunk (each
+// primary's [b][lm] at an odd stride; whole primaries copied by warps, coalesced) and its
+// warps take the items (l, b1).
+template <int T>
+__global__ void __launch_bounds__(kC3Threads) k_contract3(const Contract3Args a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float2* X = reinterpret_cast<float2*>(dsm);
+    float* su = reinterpret_cast<float*>(dsm + c3_su_offset(a.nr, a.nlm, T));
+    const int chunk = blockIdx.x;
+    const int2 C = a.chunks[chunk];   // primaries [C.x, C.y) of one catalog
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rows = a.nr * a.nlm, S = c3_stride(a.nr, a.nlm);
+    double* dst = a.partial + (size_t)chunk * a.total + a.out_off;
+    for (int i = tid; i < a.nout; i += blockDim.x) dst[i] = 0.0;
+    for (int p0 = C.x; p0 < C.y; p0 += T) {
+        const int np = min(T, C.y - p0);
+        __syncthreads();   // the previous tile is done (and the row is zeroed)
+        for (int q = warp; q < T; q += kC3Threads / 32) {
+            const float2* src = a.alm + (size_t)(p0 + q) * rows;
+            for (int r = lane; r < rows; r += 32) X[q * S + r] = q < np ? src[r] : make_float2(0.f, 0.f);
+        }
+        if (tid < T) su[tid] = tid < np ? a.wp[p0 + tid] : 0.f;
+        __syncthreads();
+        // item it always goes to the same warp, so an output is only ever added to by one warp
+        for (int it = warp; it < a.nitem; it += kC3Threads / 32) {
+            const int4 item = __ldg(&a.items[it]);
+            const double coef = (double)__ldg(&a.coef[item.x]);
+            switch (item.z >> 16) {
+#define NPCF_C3_CASE(K) \
+    case K: c3_item<K, T>(item, X, su, a.nlm, S, coef, dst, lane); break;
+                NPCF_C3_CASE(1) NPCF_C3_CASE(2) NPCF_C3_CASE(3) NPCF_C3_CASE(4) NPCF_C3_CASE(5)
+                NPCF_C3_CASE(6) NPCF_C3_CASE(7) NPCF_C3_CASE(8) NPCF_C3_CASE(9) NPCF_C3_CASE(10)
+                NPCF_C3_CASE(11) NPCF_C3_CASE(12) NPCF_C3_CASE(13) NPCF_C3_CASE(14) NPCF_C3_CASE(15)
+#undef NPCF_C3_CASE
+                default: break;
+            }
+        }
+    }
 }
 
 // Catalog blockIdx.y: its chunks' partial rows in order, times the harmonic scale.
@@ -153,11 +185,22 @@ void launch_set4(long long* dst, long long a, long long b, long long c, long lon
 }
 
 void launch_contract3(const Contract3Args& a, cudaStream_t s) {
-    const int per = a.nr * a.nlm;
-    size_t smem = (size_t)kTile * per * sizeof(float2) + kTile * sizeof(float);
-    int threads = ((a.nrows + 31) / 32) * 32;
-    if (threads > 1024) threads = 1024;
-    k_contract3<<<a.nchunk, threads, smem, s>>>(a);
+    if (a.nchunk <= 0 || a.nitem <= 0) return;
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // tiles of 32 primaries (a full warp) where they fit, else 16 or 8 (64, two per lane,
+    // measured slower: fewer blocks fit on an SM)
+    if (c3_smem(a.nr, a.nlm, 32) <= (size_t)optin) {
+        cudaFuncSetAttribute(k_contract3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c3_smem(a.nr, a.nlm, 32));
+        k_contract3<32><<<a.nchunk, kC3Threads, c3_smem(a.nr, a.nlm, 32), s>>>(a);
+    } else if (c3_smem(a.nr, a.nlm, 16) <= (size_t)optin) {
+        cudaFuncSetAttribute(k_contract3<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c3_smem(a.nr, a.nlm, 16));
+        k_contract3<16><<<a.nchunk, kC3Threads, c3_smem(a.nr, a.nlm, 16), s>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_contract3<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c3_smem(a.nr, a.nlm, 8));
+        k_contract3<8><<<a.nchunk, kC3Threads, c3_smem(a.nr, a.nlm, 8), s>>>(a);
+    }
 }
 
 void launch_reduce(const double* partial, const int* cbeg, int ncat, int total, int off, int count,

@@ -107,18 +107,17 @@ size_t pair_static_smem(int lmax);   // static shared memory of the pair kernel 
 
 // ---------------------------------------------------------------- contraction (a4 + a5)
 struct Contract3Args {
-    const float2* alm;
+    const float2* alm;         // [n][nr][nlm]
     const float* wp;
     int n, nr, nlm, lmax;
-    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog
+    const int2* chunks;        // [nchunk] primary ranges, none crossing a catalog (one block each)
     int nchunk;
-    const int2* rows;          // (l, pair index) rows
-    const int2* pairs;         // (b1, b2)
-    const float* coef;         // per l
-    int nrows;
+    const int4* items;         // (l, l(l+1)/2, b1 | (nr - 1 - b1) << 16, output of (l, b1, b1 + 1) in the order)
+    int nitem;
+    const float* coef;         // per l: (l l 0; 0 0 0)
     double* partial;           // [nchunk][total]
     int total, out_off;        // entries of the whole output, first entry of this order
-    int nbins;
+    int nout;                  // entries of this order
 };
 
 // 4PCF contraction, FP32 on the CUDA cores: lanes are primaries, warps take items

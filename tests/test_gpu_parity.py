@@ -218,6 +218,18 @@ def test_high_lmax_3pcf_and_4pcf_or_refusal(torch_dev, lmax):
             assert_orders_close(got, want, (3, 4), lmax, 4, tol=tol)
 
 
+@pytest.mark.parametrize("lmax,nr,n", [(10, 16, 700), (10, 10, 333), (0, 2, 97)])
+def test_3pcf_tiles_of_32_16_primaries_and_few_shells(torch_dev, lmax, nr, n):
+    # the 3PCF stages tiles of 32 primaries where they fit in shared memory and of 16
+    # beyond (lmax 10 with 16 shells: 11 x 120 outputs); n is not a multiple of a tile
+    pos, w = _catalog(n, 150.0, 1100 + nr)
+    edges = np.linspace(3.0, 45.0, nr + 1)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3,), lmax, edges, 0.0)
+    want, wcounts = oracle.npcf(pos, w, (3,), lmax, edges, 0.0)
+    assert np.array_equal(counts, wcounts)
+    assert_orders_close(got, want, (3,), lmax, nr)
+
+
 def test_4pcf_lmax10_10_shells_paper_setting(torch_dev):
     # Table 2's 4PCF at lmax = 10 with N_r = 10 shells (the high-lmax kernel), on a small
     # periodic log-normal catalog against the oracle; and lmax 7 all-parity with 16 shells
