@@ -73,6 +73,7 @@ struct npcf_ctx {
     int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
     int use_stab = 1;          // pair kernel: shell by table lookup when the table is valid
     int c4g_force = 0;         // FP32 4PCF: the high-lmax contraction even where the staged one fits
+    int c5_regonly = 0;        // 5PCF: the register-only contraction even where the P34 cache fits
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -110,6 +111,11 @@ struct npcf_ctx {
     DevBuf<int4> c5parts;        // multiplets of each item
     int c5npart = 0;
     DevBuf<int2> c5segs12, c5segs34;
+    // 5PCF contraction with the P34 cache (npcf_contract5c.cu), where its shared memory fits
+    DevBuf<int4> c5c_work;
+    DevBuf<int> c5c_phase;
+    int c5c_nphase = 0, c5c_slot = 0, c5c_bps = 0;
+    bool c5c_ok = false;
     int c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
     // 6PCF contraction tables
     DevBuf<int4> c6lam, c6lam2, c6terms1, c6terms2, c6terms3;
@@ -380,6 +386,90 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
         if (!it.empty() && contract5w_smem_bytes(c) + 1024 > (size_t)optin)
             return fail(ctx, NPCF_EUNSUPPORTED, "5PCF: coupling tables and staged harmonics need %zu B of shared "
                         "memory (limit %d)", contract5w_smem_bytes(c), optin);
+    }
+    // P34-cache kernel: right triples packed into groups whose P34^{m12}(b3 < b4, b3 >= 2)
+    // fit one cache slot; phase g holds the items of group g - 1 and the P34 builds of
+    // group g (slots alternate), each list heaviest first
+    ctx->c5c_ok = false;
+    if (!it.empty()) {
+        const int npall = (nr - 3) * (nr - 2) / 2;
+        int maxsize = 0;
+        for (int t34 = 0; t34 < (int)by34.size(); ++t34)
+            if (!by34[t34].empty()) maxsize = std::max(maxsize, (t.t34_l12[t34] + 1) * npall);
+        int dev = 0, optin = 0, per_sm = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        CU(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        Contract5CArgs cc{};
+        cc.nr = nr;
+        cc.nlm = ctx->nlm;
+        cc.slot_entries = 0;
+        const long long base = (long long)contract5c_smem_bytes(cc) + (long long)contract5c_static_smem() + 1024;
+        const long long entry2 = 2LL * kT5 * sizeof(float2);   // one entry in both slots
+        const long long slot2 = (per_sm / 2 - base) / entry2, slot1 = (optin - base) / entry2;
+        int slot = 0, bps = 0;
+        if (slot2 >= maxsize) {
+            slot = (int)slot2;
+            bps = 2;
+        } else if (slot1 >= maxsize) {
+            slot = (int)slot1;
+            bps = 1;
+        }
+        if (slot > 0 && maxsize > 0) {
+            std::vector<std::vector<std::pair<double, int4>>> phase(1);
+            int g = 0, used = 0;
+            for (int t34 = 0; t34 < (int)by34.size(); ++t34) {
+                const std::vector<int>& mult = by34[t34];
+                if (mult.empty()) continue;
+                const int l12 = t.t34_l12[t34], size = (l12 + 1) * npall;
+                if (used + size > slot) {
+                    ++g;
+                    used = 0;
+                    phase.emplace_back();
+                }
+                const int tbase = used, sl = g & 1;
+                used += size;
+                for (int m12 = 0; m12 <= l12; ++m12) {
+                    const int sg = t.t34_seg0[t34] + m12;
+                    const int k34 = t.seg34_end[sg] - t.seg34_begin[sg];
+                    for (int b3 = 2; b3 + 1 < nr; ++b3)
+                        phase[g].push_back({(double)k34 * (nr - 1 - b3),
+                                            make_int4(sg, b3 | (sl << 24) | (1 << 30), tbase + m12 * npall, 0)});
+                }
+                if ((int)phase.size() <= g + 1) phase.resize(g + 2);
+                for (int a : mult) {
+                    const int t12 = t.lam_t12[a];
+                    for (int beta = 1; beta + 2 < nr; ++beta) {
+                        const int m = nr - 1 - beta;
+                        double cost = 0;
+                        for (int m12 = 0; m12 <= l12; ++m12) {
+                            const int sg = t.t12_seg0[t12] + m12;
+                            cost += 2.0 * (t.seg12_end[sg] - t.seg12_begin[sg]) * beta + beta * m * (m - 1) / 2.0;
+                        }
+                        phase[g + 1].push_back(
+                            {cost, make_int4(t.t12_seg0[t12], beta | ((o.odd(a) ? 1 : 0) << 8) | (l12 << 16) | (sl << 24),
+                                             tbase, off + a * nb)});
+                    }
+                }
+            }
+            std::vector<int4> work;
+            std::vector<int> pb;
+            for (auto& ph : phase) {
+                std::stable_sort(ph.begin(), ph.end(),
+                                 [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+                                     return x.first > y.first;
+                                 });
+                pb.push_back((int)work.size());
+                for (const auto& x : ph) work.push_back(x.second);
+            }
+            pb.push_back((int)work.size());
+            ctx->c5c_nphase = (int)phase.size();
+            ctx->c5c_slot = slot;
+            ctx->c5c_bps = bps;
+            CU(upload(ctx->c5c_work, work));
+            CU(upload(ctx->c5c_phase, pb));
+            ctx->c5c_ok = true;
+        }
     }
     ctx->c5nitem = (int)it.size();
     ctx->c5npart = (int)parts.size();
@@ -1079,6 +1169,35 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
             launch_contract4w(c, contract4w_blocks(ctx->nsm, P.nchunk4), s);
         } else if (o.N == 5) {
             if (ctx->c5nitem == 0) continue;
+            if (ctx->c5c_ok && !ctx->c5_regonly) {
+                Contract5CArgs c{};
+                c.alm = ctx->alm.p;
+                c.wp = ctx->wp.p;
+                c.n = n;
+                c.nr = ctx->nr;
+                c.nlm = ctx->nlm;
+                c.c12 = ctx->c5c12.p;
+                c.o12 = ctx->c5i12.p;
+                c.c34 = ctx->c5c34.p;
+                c.o34 = ctx->c5i34.p;
+                c.segs12 = ctx->c5segs12.p;
+                c.segs34 = ctx->c5segs34.p;
+                c.binq = ctx->c5binq.p;
+                c.work = ctx->c5c_work.p;
+                c.phase_begin = ctx->c5c_phase.p;
+                c.nphase = ctx->c5c_nphase;
+                c.slot_entries = ctx->c5c_slot;
+                c.blocks_per_sm = ctx->c5c_bps;
+                c.chunks = ctx->chunks.p;
+                c.nchunk = P.nchunk;
+                c.partial = ctx->partial.p;
+                c.total = ctx->total;
+                c.out_off = ctx->order_off[k];
+                c.nout = o.n_lambda() * o.n_bins();
+                c.chunk_counter = ctx->work.p + 2;
+                launch_contract5c(c, std::max(1, std::min(ctx->c5c_bps * ctx->nsm, P.nchunk)), s);
+                continue;
+            }
             Contract5WArgs c{};
             c.alm = ctx->alm.p;
             c.wp = ctx->wp.p;
@@ -1874,6 +1993,10 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
         case 4:
             if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "high-lmax 4PCF contraction is 0 or 1");
             ctx->c4g_force = value;
+            return NPCF_OK;
+        case 9:
+            if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "register-only 5PCF contraction is 0 or 1");
+            ctx->c5_regonly = value;
             return NPCF_OK;
         case 5:
             if (value < 1 || value > 1024) return fail(ctx, NPCF_EINVAL, "primaries per chunk in [1, 1024]");

@@ -1,0 +1,247 @@
+// 5PCF contraction with P34 built once per block and tile: FP32 products, FP64 partials,
+// primaries on the lanes.
+//
+// Eq. (basis-coupling) at N = 5 through the intermediate m12 (App. B halving over m12):
+//   zeta_L(b1,b2,b3,b4) += u sqrt(2 l12 + 1) sum_{m12 >= 0} 2 S(m12) (-1)^{l12-m12}
+//                          Q_L[P12^{m12}(b1,b2) P34^{m12}(b3,b4)]
+//   P12^{m12}(b1,b2) = sum_{m1} (l1 l2 l12; m1, m12 - m1, -m12) a^{b1}_{l1 m1} a^{b2}_{l2,m12-m1}
+//   P34^{m12}(b3,b4) = sum_{m3} (l12 l3 l4; m12, m3, -m12 - m3) a^{b3}_{l3 m3} a^{b4}_{l4,-m12-m3}.
+//
+// P34 depends on the right triple (l12 l3 l4), m12 and (b3, b4) only, but every multiplet
+// of that triple and every b2 < b3 uses it. The register-only kernel (npcf_contract5w.cu)
+// builds it again for every b2 and every item of at most two multiplets. Here a block
+// builds P34 of a group of right triples once per tile of 32 primaries into shared memory
+// ([m12][pair (b3 < b4), b3 >= 2][primary]), and its warps then take items (multiplet,
+// b2): each lane builds P12(b1, b2) for every b1 < b2 in registers and multiplies it with
+// the cached P34 of every pair after b2 into its (b1, b3, b4) sums. Two cache slots
+// alternate: in one phase the warps take, from one work list, the items of group g - 1
+// (reading one slot) and the P34 builds of group g (writing the other), so one block
+// barrier separates the phases. Coupling terms are read through L1 (warp-uniform).
+#include "npcf_device.h"
+#include "npcf_warp.cuh"
+
+#include <algorithm>
+
+namespace npcf {
+namespace {
+
+constexpr int kC5CThreads = 256;
+
+struct C5CLayout {
+    size_t X, u, cache, total;
+};
+
+__host__ __device__ inline size_t al128c(size_t x) { return (x + 127) & ~size_t(127); }
+
+__host__ __device__ inline C5CLayout c5c_layout(int nr, int nlm, int slot_entries) {
+    C5CLayout l;
+    l.X = 0;
+    l.u = al128c(l.X + (size_t)nr * nlm * kRS5 * sizeof(float2));
+    l.cache = al128c(l.u + kT5 * sizeof(float));
+    l.total = al128c(l.cache + (size_t)2 * slot_entries * kT5 * sizeof(float2));
+    return l;
+}
+
+// first pair (b3, b3 + 1) of shell b3 >= 2 in the cache's pair order (lexicographic)
+__host__ __device__ constexpr int pair_off(int nr, int b3) { return (b3 - 2) * (2 * nr - 3 - b3) / 2; }
+static_assert(pair_off(8, 2) == 0 && pair_off(8, 3) == 5 && pair_off(8, 6) == 14 && pair_off(8, 7) == 15,
+              "pairs (b3, b4), 2 <= b3 < b4 < 8, in lexicographic order");
+
+// P34^{m12}(b3, b4) of one (triple, m12) for every b4 > b3 into the cache.
+template <int NR>
+__device__ __forceinline__ void c5c_build34(const int4 w, const Contract5CArgs& a, const float2* __restrict__ X,
+                                            float2* __restrict__ cache, int lane) {
+    constexpr int MX = NR - 3;   // b3 >= 2: at most NR - 3 shells after it
+    const int b3 = w.y & 0xff;
+    const int nb4 = NR - 1 - b3;
+    float pr[MX], pi[MX];
+#pragma unroll
+    for (int q = 0; q < MX; ++q) pr[q] = pi[q] = 0.f;
+    const int2 S = __ldg(&a.segs34[w.x]);
+    const float2* Xl = X + lane;
+    for (int k = S.x; k < S.y; ++k) {
+        const float4 c = __ldg(&a.c34[k]);
+        const uint32_t o = __ldg(&a.o34[k]);
+        const float2 x3 = Xl[(o & 0xffffu) + b3 * kRS5];
+        const float2* X4 = Xl + (o >> 16) + (b3 + 1) * kRS5;
+        // re += cA x3 x4 + cB y3 y4 ; im += cC y3 x4 + cD x3 y4 (conjugations folded in c)
+        const float a0 = c.x * x3.x, a1 = c.y * x3.y, a2 = c.z * x3.y, a3 = c.w * x3.x;
+#pragma unroll
+        for (int q = 0; q < MX; ++q) {
+            if (q < nb4) {
+                const float2 x4 = X4[q * kRS5];
+                pr[q] = fmaf(a0, x4.x, fmaf(a1, x4.y, pr[q]));
+                pi[q] = fmaf(a2, x4.x, fmaf(a3, x4.y, pi[q]));
+            }
+        }
+    }
+    float2* dst = cache + (size_t)(w.z + pair_off(NR, b3)) * kT5 + lane;
+#pragma unroll
+    for (int q = 0; q < MX; ++q)
+        if (q < nb4) dst[q * kT5] = make_float2(pr[q], pi[q]);
+}
+
+// Item (multiplet, beta = b2): NB = beta shells b1 < beta, M = NR - 1 - beta shells after it
+// (NP = M (M - 1) / 2 pairs b3 < b4).
+template <int NR, int NB, int M>
+__device__ __forceinline__ void c5c_item(const int4 w, const Contract5CArgs& a, const float2* __restrict__ X,
+                                         const float2* __restrict__ cache, float u, const int* __restrict__ binq,
+                                         double* __restrict__ dst, int lane) {
+    constexpr int NP = M * (M - 1) / 2;
+    constexpr int NOUT = NB * NP;
+    constexpr int NPALL = (NR - 3) * (NR - 2) / 2;
+    const bool odd = ((w.y >> 8) & 1) != 0;
+    const int l12 = (w.y >> 16) & 0xff;
+    const float rcf = sqrtf((float)(2 * l12 + 1));
+    const float2* Xl = X + lane;
+    const float2* C34 = cache + (size_t)(w.z + pair_off(NR, NB + 1)) * kT5 + lane;
+    float acc[NOUT];
+#pragma unroll
+    for (int i = 0; i < NOUT; ++i) acc[i] = 0.f;
+    for (int m12 = 0; m12 <= l12; ++m12) {
+        // P12(b1, beta) for b1 < beta; the b2 factor is the same for every b1
+        float p12r[NB], p12i[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) p12r[j] = p12i[j] = 0.f;
+        const int2 S12 = __ldg(&a.segs12[w.x + m12]);
+        for (int k = S12.x; k < S12.y; ++k) {
+            const float4 c = __ldg(&a.c12[k]);
+            const uint32_t o = __ldg(&a.o12[k]);
+            const float2 x2 = Xl[(o >> 16) + NB * kRS5];
+            // re += cA x1 x2 + cB y1 y2 ; im += cC y1 x2 + cD x1 y2 (conjugations folded in c)
+            const float a0 = c.x * x2.x, a1 = c.y * x2.y, a2 = c.z * x2.x, a3 = c.w * x2.y;
+            const float2* X1 = Xl + (o & 0xffffu);
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const float2 x1 = X1[j * kRS5];
+                p12r[j] = fmaf(a0, x1.x, fmaf(a1, x1.y, p12r[j]));
+                p12i[j] = fmaf(a2, x1.y, fmaf(a3, x1.x, p12i[j]));
+            }
+        }
+        // u 2 S(m12) (-1)^{l12 - m12} sqrt(2 l12 + 1); Re (even L) or Im (odd L) of P12 P34
+        const float cm = u * (m12 == 0 ? 1.f : 2.f) * (((l12 - m12) & 1) ? -1.f : 1.f) * rcf;
+        float A[NB], B[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            A[j] = cm * (odd ? p12i[j] : p12r[j]);
+            B[j] = cm * (odd ? p12r[j] : -p12i[j]);
+        }
+        const float2* P34 = C34 + (size_t)m12 * NPALL * kT5;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const float2 q = P34[p * kT5];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) acc[j * NP + p] = fmaf(A[j], q.x, fmaf(B[j], q.y, acc[j * NP + p]));
+        }
+    }
+    using R = warp::TR<NOUT>;
+    R::run(acc, lane);
+#pragma unroll
+    for (int i = 0; i < R::F; ++i) {
+        const int e = R::origin(i, lane);
+        if (e >= 0) {
+            const int j = e / NP, p = e - j * NP;
+            dst[w.w + binq[j * NR + NB] + p] += (double)acc[i];
+        }
+    }
+}
+
+template <int NR, int MINB>
+__global__ void __launch_bounds__(kC5CThreads, MINB) k_contract5c(const Contract5CArgs a) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const C5CLayout lay = c5c_layout(NR, a.nlm, a.slot_entries);
+    float2* X = reinterpret_cast<float2*>(dsm + lay.X);
+    float* su = reinterpret_cast<float*>(dsm + lay.u);
+    float2* cache = reinterpret_cast<float2*>(dsm + lay.cache);
+    __shared__ int chunk_s, next[2];
+    __shared__ int binq[NR * NR];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < NR * NR; i += blockDim.x) binq[i] = a.binq[i];
+    const int rows = NR * a.nlm;
+
+    // chunks (primary ranges of one catalog) taken dynamically; chunk c sums into row c
+    for (;;) {
+        if (tid == 0) chunk_s = atomicAdd(a.chunk_counter, 1);
+        __syncthreads();
+        const int c = chunk_s;
+        if (c >= a.nchunk) break;
+        const int2 C = a.chunks[c];
+        double* dst = a.partial + (size_t)c * a.total;
+        for (int i = tid; i < a.nout; i += blockDim.x) dst[a.out_off + i] = 0.0;
+        for (int p0 = C.x; p0 < C.y; p0 += kT5) {
+            const int np = min(kT5, C.y - p0);
+            // stage [lm][b][q] from the pair kernel's [q][b][lm]
+            const float2* src = a.alm + (size_t)p0 * rows;
+            for (int i = tid; i < kT5 * rows; i += blockDim.x) {
+                const int q = i / rows, r = i - q * rows;   // r = b * nlm + lm
+                const int b = r / a.nlm, lm = r - b * a.nlm;
+                X[(lm * NR + b) * kRS5 + q] = q < np ? src[i] : make_float2(0.f, 0.f);
+            }
+            if (tid < kT5) su[tid] = tid < np ? a.wp[p0 + tid] : 0.f;
+            if (tid == 0) next[0] = next[1] = 0;
+            __syncthreads();   // also orders the row's zeroing before the first sums
+            const float u = su[lane];
+            for (int ph = 0; ph < a.nphase; ++ph) {
+                const int w0 = __ldg(&a.phase_begin[ph]), nw = __ldg(&a.phase_begin[ph + 1]) - w0;
+                if (tid == 0) next[(ph + 1) & 1] = 0;   // nobody uses it in this phase
+                for (;;) {
+                    int it = 0;
+                    if (lane == 0) it = atomicAdd(&next[ph & 1], 1);
+                    it = __shfl_sync(warp::kFullMask, it, 0);
+                    if (it >= nw) break;
+                    const int4 w = __ldg(&a.work[w0 + it]);
+                    float2* slot = cache + (size_t)((w.y >> 24) & 1) * a.slot_entries * kT5;
+                    if (w.y & (1 << 30)) {
+                        c5c_build34<NR>(w, a, X, slot, lane);
+                    } else {
+                        switch (w.y & 0xff) {   // beta
+#define NPCF_C5C_CASE(B) \
+    case B:              \
+        if (B <= NR - 3) c5c_item<NR, (B <= NR - 3 ? B : 1), (B <= NR - 3 ? NR - 1 - B : 2)>(w, a, X, slot, u, binq, dst, lane); \
+        break;
+                            NPCF_C5C_CASE(1) NPCF_C5C_CASE(2) NPCF_C5C_CASE(3) NPCF_C5C_CASE(4)
+                            NPCF_C5C_CASE(5) NPCF_C5C_CASE(6) NPCF_C5C_CASE(7)
+#undef NPCF_C5C_CASE
+                            default: break;
+                        }
+                    }
+                }
+                __syncthreads();   // the slot written in this phase is read in the next
+            }
+        }
+        __syncthreads();   // every thread has read chunk_s before it is taken again
+    }
+}
+
+template <int NR>
+void launch_nr_c(const Contract5CArgs& a, int nblocks, cudaStream_t s) {
+    const size_t smem = contract5c_smem_bytes(a);
+    if (a.blocks_per_sm >= 2) {
+        cudaFuncSetAttribute(k_contract5c<NR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_contract5c<NR, 2><<<nblocks, kC5CThreads, smem, s>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_contract5c<NR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_contract5c<NR, 1><<<nblocks, kC5CThreads, smem, s>>>(a);
+    }
+}
+
+}  // namespace
+
+size_t contract5c_smem_bytes(const Contract5CArgs& a) { return c5c_layout(a.nr, a.nlm, a.slot_entries).total; }
+
+size_t contract5c_static_smem() { return 1024; }
+
+void launch_contract5c(const Contract5CArgs& a, int nblocks, cudaStream_t s) {
+    switch (a.nr) {
+        case 4: launch_nr_c<4>(a, nblocks, s); break;
+        case 5: launch_nr_c<5>(a, nblocks, s); break;
+        case 6: launch_nr_c<6>(a, nblocks, s); break;
+        case 7: launch_nr_c<7>(a, nblocks, s); break;
+        case 8: launch_nr_c<8>(a, nblocks, s); break;
+        case 9: launch_nr_c<9>(a, nblocks, s); break;
+        case 10: launch_nr_c<10>(a, nblocks, s); break;
+        default: break;
+    }
+}
+
+}  // namespace npcf

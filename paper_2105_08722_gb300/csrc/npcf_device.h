@@ -241,6 +241,37 @@ __host__ __device__ constexpr int c5_group(int nb, int m) {
     return g < 1 ? 1 : (g > 2 ? 2 : g);
 }
 void launch_contract5w(const Contract5WArgs& a, int nblocks, cudaStream_t s);
+// 5PCF contraction with P34 built once per block and tile into shared memory
+// (npcf_contract5c.cu). The work list of each phase holds P34 builds, (segment of the
+// (triple, m12), b3 | slot << 24 | 1 << 30, cache entry of the (triple, m12) block, 0), and
+// items, (P12 segment of m12 = 0, beta | odd << 8 | l12 << 16 | slot << 24, cache entry of
+// the triple's m12 = 0 block, first output of L); a cache entry is kT5 float2.
+struct Contract5CArgs {
+    const float2* alm;         // [n][nr][nlm]
+    const float* wp;
+    int n, nr, nlm;
+    const float4* c12;         // P12 terms (cA, cB, cC, cD)
+    const uint32_t* o12;       // staged offsets lm1 nr kRS5 | lm2 nr kRS5 << 16
+    const float4* c34;
+    const uint32_t* o34;
+    const int2* segs12;        // term range of each (l1 l2 l12 triple, m12)
+    const int2* segs34;
+    const int* binq;           // [nr][nr]: bin index of (b1, b2, b2 + 1, b2 + 2)
+    const int4* work;          // the phases' work lists, back to back
+    const int* phase_begin;    // [nphase + 1]
+    int nphase;
+    int slot_entries;          // entries of one cache slot
+    int blocks_per_sm;         // 2 where two blocks' shared memory fits on an SM, else 1
+    const int2* chunks;        // primary ranges, none crossing a catalog
+    int nchunk;
+    double* partial;           // [nchunk][total]
+    int total, out_off, nout;
+    int* chunk_counter;        // zeroed before the launch
+};
+void launch_contract5c(const Contract5CArgs& a, int nblocks, cudaStream_t s);
+size_t contract5c_smem_bytes(const Contract5CArgs& a);
+size_t contract5c_static_smem();
+
 size_t contract5w_smem_bytes(const Contract5WArgs& a);
 size_t contract4_tc_smem_bytes(const Contract4TCArgs& a);
 

@@ -485,45 +485,53 @@ def test_lognormal_200k_split_bf16_sampled_primaries(torch_dev, lognormal_worklo
 
 # ------------------------------------------------------------------ 5PCF
 
-def test_5pcf_periodic_lmax3(torch_dev):
+# tuning key 9: 0 = P34 cached in shared memory per block (the default where it fits),
+# 1 = the register-only kernel; both run on the same cases
+@pytest.mark.parametrize("regonly", [0, 1])
+def test_5pcf_periodic_lmax3(torch_dev, regonly):
     pos = catalogs.lognormal_box(900, 150.0, 32, seed=51)
     w = np.ones(len(pos), np.float32)
     edges = np.linspace(6.0, 42.0, 7)
-    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 3, edges, 150.0)
+    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 3, edges, 150.0, tuning={9: regonly})
     want, wcounts = oracle.npcf(pos, w, (5,), 3, edges, 150.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (5,), 3, 6)
 
 
-@pytest.mark.parametrize("nr", [9, 10])
-def test_5pcf_many_shells(torch_dev, nr):
-    # 9 and 10 shells take items of 1 to 4 multiplets sharing (l12 l3 l4), by b2
+@pytest.mark.parametrize("regonly", [0, 1])
+@pytest.mark.parametrize("nr", [4, 9, 10])
+def test_5pcf_many_shells(torch_dev, nr, regonly):
+    # 4 shells: one bin tuple; 9 and 10 shells take items of 1 to 4 multiplets sharing
+    # (l12 l3 l4), by b2, and the widest P34 caches
     pos = catalogs.lognormal_box(700, 150.0, 32, seed=53)
     w = np.ones(len(pos), np.float32)
     edges = np.linspace(4.0, 40.0, nr + 1)
-    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 3, edges, 150.0)
+    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 3, edges, 150.0, tuning={9: regonly})
     want, wcounts = oracle.npcf(pos, w, (5,), 3, edges, 150.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (5,), 3, nr)
 
 
-def test_5pcf_lmax5_10_shells(torch_dev):
+@pytest.mark.parametrize("regonly", [0, 1])
+def test_5pcf_lmax5_10_shells(torch_dev, regonly):
     # the paper's 5PCF timing setting (lmax 5, 10 shells) on a small catalog: 1,406
     # multiplets x 210 bin tuples
     pos = catalogs.lognormal_box(300, 150.0, 32, seed=91)
     w = np.ones(len(pos), np.float32)
     edges = np.linspace(4.0, 40.0, 11)
-    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 5, edges, 150.0)
+    _, got, counts = gpu_run(torch_dev, pos, w, (5,), 5, edges, 150.0, tuning={9: regonly})
     want, wcounts = oracle.npcf(pos, w, (5,), 5, edges, 150.0)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (5,), 5, 10)
 
 
-def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev):
+@pytest.mark.parametrize("regonly", [0, 1])
+def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev, regonly):
     pos, w = _catalog(500, 80.0, 52)
     w = w - np.float32(0.8)
     edges = np.linspace(5.0, 30.0, 6)
-    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4, 5), 2, edges, 0.0, allparity=True)
+    _, got, counts = gpu_run(torch_dev, pos, w, (3, 4, 5), 2, edges, 0.0, allparity=True,
+                             tuning={9: regonly})
     want, wcounts = oracle.npcf(pos, w, (3, 4, 5), 2, edges, 0.0, allparity=True)
     assert np.array_equal(counts, wcounts)
     assert_orders_close(got, want, (3, 4, 5), 2, 5, allparity=True)
