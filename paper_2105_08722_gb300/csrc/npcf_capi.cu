@@ -1306,7 +1306,8 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
         (uintptr_t)ctx->d_off.p, (uintptr_t)ctx->chunks.p, (uintptr_t)ctx->cbeg.p, (uintptr_t)ctx->rows.p,
         (uintptr_t)ctx->chunks4.p, (uintptr_t)ctx->cbeg4.p, (uintptr_t)P.nchunk4,
         (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.chunk, (uintptr_t)P.pa.bucket, (uintptr_t)P.pa.boff[ctx->nr],
-        (uintptr_t)P.pa.trim, (uintptr_t)P.pa.tab_ok, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps};
+        (uintptr_t)P.pa.trim, (uintptr_t)P.pa.tab_ok, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps,
+        (uintptr_t)ctx->c4g_force, (uintptr_t)ctx->c5_regonly};
     for (long long v : off) sig.push_back((uintptr_t)v);
     if (ctx->gexec && sig == ctx->gsig) {
         CU(cudaGraphLaunch(ctx->gexec, s));
