@@ -239,9 +239,10 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
  * key 4 = FP32 4PCF contraction: 0 (default) stages the coupling terms with a tile of 64
  * primaries in shared memory where they fit (lmax <= 6 at 4 shells) and takes the
  * high-lmax kernel (tiles of 32 primaries, terms read through L1) beyond; 1 takes the
- * high-lmax kernel always, key 5 = pair kernel: consecutive (cell-sorted) primaries per chunk that a block takes
- * from the global counter (1..1024, default 16; small chunks keep a block's warps on
- * nearby primaries, whose neighbourhoods then share L1), key 6 = split-bf16 contraction:
+ * high-lmax kernel always, key 5 = pair kernel: consecutive (cell-sorted) primaries per
+ * chunk that a block takes from the global counter (1..1024, default 16; small chunks keep
+ * a block's warps on nearby primaries, whose neighbourhoods then share L1), key 6 =
+ * split-bf16 contraction:
  * steps of 16 primaries between drains of the tensor-memory accumulators into FP64 (>= 1;
  * fewer steps bound the accumulation error of the tensor cores more tightly), key 7 = pair
  * kernel: cut each neighbour row to the primary's x-window (1, default) or scan whole rows
