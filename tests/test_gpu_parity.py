@@ -931,6 +931,33 @@ def test_batch_matches_single_catalog_runs(torch_dev):
         assert np.max(np.abs(got[k] - want)) <= TOL_FP32 * scale, k
 
 
+@pytest.mark.parametrize("orders,lmax,tuning", [
+    ((5,), 3, {}),            # 5PCF with the P34 cache: chunk rows of several catalogs
+    ((5,), 3, {9: 1}),        # the register-only 5PCF kernel
+    ((3, 4), 4, {4: 1}),      # the high-lmax 4PCF kernel forced
+])
+def test_batch_of_each_contraction_kernel_matches_single_runs(torch_dev, orders, lmax, tuning):
+    # every contraction kernel sums a batch's catalogs into their own chunk rows: each
+    # catalog's multiplets equal those of its own run with the same kernel
+    rng = np.random.default_rng(83)
+    sizes = [500, 1, 1200, 0, 800]
+    cats = [rng.uniform(0, 110.0, size=(n, 3)).astype(np.float32) for n in sizes]
+    ws = [rng.uniform(0.5, 1.5, size=n).astype(np.float32) for n in sizes]
+    edges = np.linspace(4.0, 32.0, 7)
+    _, got, counts = _batch_run(torch_dev, cats, ws, orders, lmax, edges, 110.0, tuning=tuning)
+    for k, (c, w) in enumerate(zip(cats, ws)):
+        if len(c) == 0:
+            assert np.all(got[k] == 0) and np.all(counts[k] == 0)
+            continue
+        _, want, wcounts = gpu_run(torch_dev, c, w, orders, lmax, edges, 110.0, tuning=tuning)
+        assert np.array_equal(counts[k], wcounts), k
+        scale = max(np.sqrt(np.mean(want ** 2)), 1e-300)
+        assert np.max(np.abs(got[k] - want)) <= TOL_FP32 * scale, k
+    # and against the oracle for the largest catalog
+    want, _ = oracle.npcf(cats[2], ws[2], orders, lmax, edges, 110.0)
+    assert_orders_close(got[2], want, orders, lmax, 6)
+
+
 def test_batch_graph_replay_coadds_and_mode_errors(torch_dev):
     from paper_2105_08722_gb300._lib import NPCFError
     rng = np.random.default_rng(82)
