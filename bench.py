@@ -39,9 +39,9 @@ KERNELS_PER_STEP = 10  # k_sumw, 4 cell-list kernels, pair, contract3, contract4
 # 200k workload, with the SHA-256 prefix of the kernel's source when they were taken; the
 # roofline reports them only while the source is unchanged (profiles/ has the captures).
 TRAFFIC = {
-    "pair": {"bytes": 12_513_024 + 525_654_784, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
-             "sha256": "4e8cc1b55b9a4a43"},
-    "contraction/fp32": {"bytes": 337_059_840 + 681_472, "source": "paper_2105_08722_gb300/csrc/npcf_contract4.cu",
+    "pair": {"bytes": 12_835_072 + 428_769_536, "source": "paper_2105_08722_gb300/csrc/npcf_pair.cu",
+             "sha256": "5ab3768ce8a30c34"},
+    "contraction/fp32": {"bytes": 338_221_568 + 141_824, "source": "paper_2105_08722_gb300/csrc/npcf_contract4.cu",
                          "sha256": "ec635d2be4d339ba"},
     "contraction/bf16": {"bytes": 338_193_920 + 3_255_552,
                          "source": "paper_2105_08722_gb300/csrc/npcf_contract_tc.cu", "sha256": "9e25cf7cd3089fa9"},

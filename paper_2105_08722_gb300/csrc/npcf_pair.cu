@@ -334,11 +334,12 @@ __device__ __forceinline__ int cut_rows(const PairArgs& a, const PairShared<L>& 
 // S_{m,k} = sum w (x + i y)^m T_k(z) in registers (T_k Chebyshev, m + k <= lmax); a
 // shuffle transpose-reduction adds the lanes' sums to pw. An entry holds (point index |
 // shift code << 26): the separation is the one the neighbour rule accepted,
-// (p_j - p_i) - shift. Not inlined: called once per non-empty shell at the end of a
-// primary, and during a scan only when a bucket fills.
+// (p_j - p_i) - shift. Called once per non-empty shell at the end of a primary, and
+// during a scan only when a bucket fills; inlined for lmax 4 to 8 (fewer spills and no call
+// frame, measured 2 % faster at lmax 5), called for the other lmax (sum_bucket_call).
 template <int L>
-__device__ __noinline__ void sum_bucket(const float4* __restrict__ pts, const float4* shift, const uint32_t* e,
-                                        int n, float4 pi, float* pw, int lane) {
+__device__ __forceinline__ void sum_bucket(const float4* __restrict__ pts, const float4* shift, const uint32_t* e,
+                                           int n, float4 pi, float* pw, int lane) {
     constexpr int NC = ncomp(L);
     using R = TR<NC>;
     float acc[NC];
@@ -386,6 +387,12 @@ __device__ __noinline__ void sum_bucket(const float4* __restrict__ pts, const fl
     __syncwarp();
 }
 
+template <int L>
+__device__ __noinline__ void sum_bucket_call(const float4* __restrict__ pts, const float4* shift, const uint32_t* e,
+                                             int n, float4 pi, float* pw, int lane) {
+    sum_bucket<L>(pts, shift, e, n, pi, pw, lane);
+}
+
 // Shell t's bucket of the warp into the shell's sums; the bucket is then empty.
 template <int L>
 __device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh, const uint32_t* bucket,
@@ -393,7 +400,10 @@ __device__ __forceinline__ void flush_shell(const PairArgs& a, PairShared<L>& sh
     __syncwarp();   // the entries written by every lane are visible
     const int b0 = sh.boff[t];
     const int n = sh.ne[warp][t].x - b0;
-    sum_bucket<L>(a.pts, sh.shift, bucket + b0, n, pi, psum + t * ncomp(L), lane);
+    if constexpr (L >= 4 && L <= 8)
+        sum_bucket<L>(a.pts, sh.shift, bucket + b0, n, pi, psum + t * ncomp(L), lane);
+    else
+        sum_bucket_call<L>(a.pts, sh.shift, bucket + b0, n, pi, psum + t * ncomp(L), lane);
     if (lane == 0) {
         sh.tot[warp][t] += (uint32_t)n;
         sh.ne[warp][t].x = b0;
