@@ -73,7 +73,8 @@ struct npcf_ctx {
     int trim = 1;              // pair kernel: cut staged rows to each primary's x-window
     int use_stab = 1;          // pair kernel: shell by table lookup when the table is valid
     int c4g_force = 0;         // FP32 4PCF: the high-lmax contraction even where the staged one fits
-    int c5_regonly = 0;        // 5PCF: the register-only contraction even where the P34 cache fits
+    int c5_mode = 0;           // 5PCF: 0 automatic, 1 register-only, 2 P34 cache with the terms read
+                               // through L1, 3 P34 cache with the terms in shared memory
     int chunk_target = 0;      // primaries per contraction chunk (0 = automatic)
     GridInfo grid{};
     std::vector<int> rows_host;
@@ -115,7 +116,7 @@ struct npcf_ctx {
     DevBuf<int4> c5c_work;
     DevBuf<int> c5c_phase;
     int c5c_nphase = 0, c5c_slot = 0, c5c_bps = 0;
-    bool c5c_ok = false;
+    bool c5c_ok = false, c5c_tabs_fit = false;   // tabs_fit: the tables fit in shared memory too
     int c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
     // 6PCF contraction tables
     DevBuf<int4> c6lam, c6lam2, c6terms1, c6terms2, c6terms3;
@@ -404,6 +405,10 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
         cc.nr = nr;
         cc.nlm = ctx->nlm;
         cc.slot_entries = 0;
+        cc.nterms12 = (int)c12.size();
+        cc.nterms34 = (int)c34.size();
+        cc.nseg12 = (int)s12.size();
+        cc.nseg34 = (int)s34.size();
         const long long base = (long long)contract5c_smem_bytes(cc) + (long long)contract5c_static_smem() + 1024;
         const long long entry2 = 2LL * kT5 * sizeof(float2);   // one entry in both slots
         const long long slot2 = (per_sm / 2 - base) / entry2, slot1 = (optin - base) / entry2;
@@ -414,6 +419,18 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
         } else if (slot1 >= maxsize) {
             slot = (int)slot1;
             bps = 1;
+        }
+        {
+            // with the coupling terms in shared memory too (one block per SM), the slots take
+            // the rest of the block's shared memory
+            cc.tables_smem = 1;
+            const long long baset = (long long)contract5c_smem_bytes(cc) + (long long)contract5c_static_smem() + 1024;
+            const long long slott = (optin - baset) / entry2;
+            ctx->c5c_tabs_fit = slott >= maxsize && maxsize > 0;
+            if (ctx->c5c_tabs_fit) {
+                slot = (int)slott;
+                bps = (long long)2 * (base + entry2 * slott) <= per_sm ? 2 : 1;   // for the L1-terms kernel
+            }
         }
         if (slot > 0 && maxsize > 0) {
             std::vector<std::vector<std::pair<double, int4>>> phase(1);
@@ -1169,7 +1186,8 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
             launch_contract4w(c, contract4w_blocks(ctx->nsm, P.nchunk4), s);
         } else if (o.N == 5) {
             if (ctx->c5nitem == 0) continue;
-            if (ctx->c5c_ok && !ctx->c5_regonly) {
+            const bool tabs = ctx->c5c_tabs_fit && (ctx->c5_mode == 0 || ctx->c5_mode == 3);
+            if (ctx->c5c_ok && ctx->c5_mode != 1 && (ctx->c5_mode != 3 || tabs)) {
                 Contract5CArgs c{};
                 c.alm = ctx->alm.p;
                 c.wp = ctx->wp.p;
@@ -1188,6 +1206,11 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
                 c.nphase = ctx->c5c_nphase;
                 c.slot_entries = ctx->c5c_slot;
                 c.blocks_per_sm = ctx->c5c_bps;
+                c.tables_smem = tabs ? 1 : 0;
+                c.nterms12 = ctx->c5nterms12;
+                c.nterms34 = ctx->c5nterms34;
+                c.nseg12 = ctx->c5nseg12;
+                c.nseg34 = ctx->c5nseg34;
                 c.chunks = ctx->chunks.p;
                 c.nchunk = P.nchunk;
                 c.partial = ctx->partial.p;
@@ -1195,7 +1218,7 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
                 c.out_off = ctx->order_off[k];
                 c.nout = o.n_lambda() * o.n_bins();
                 c.chunk_counter = ctx->work.p + 2;
-                launch_contract5c(c, std::max(1, std::min(ctx->c5c_bps * ctx->nsm, P.nchunk)), s);
+                launch_contract5c(c, std::max(1, std::min((tabs ? 1 : ctx->c5c_bps) * ctx->nsm, P.nchunk)), s);
                 continue;
             }
             Contract5WArgs c{};
@@ -1307,7 +1330,7 @@ npcf_status run_batch(npcf_ctx* ctx, const float* d_pos, const float* d_w, const
         (uintptr_t)ctx->chunks4.p, (uintptr_t)ctx->cbeg4.p, (uintptr_t)P.nchunk4,
         (uintptr_t)P.n, (uintptr_t)P.ncat, (uintptr_t)P.nchunk, (uintptr_t)P.pa.chunk, (uintptr_t)P.pa.bucket, (uintptr_t)P.pa.boff[ctx->nr],
         (uintptr_t)P.pa.trim, (uintptr_t)P.pa.tab_ok, (uintptr_t)ctx->cells_per_rmax, (uintptr_t)ctx->drain_steps,
-        (uintptr_t)ctx->c4g_force, (uintptr_t)ctx->c5_regonly};
+        (uintptr_t)ctx->c4g_force, (uintptr_t)ctx->c5_mode};
     for (long long v : off) sig.push_back((uintptr_t)v);
     if (ctx->gexec && sig == ctx->gsig) {
         CU(cudaGraphLaunch(ctx->gexec, s));
@@ -1996,8 +2019,8 @@ npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value) {
             ctx->c4g_force = value;
             return NPCF_OK;
         case 9:
-            if (value != 0 && value != 1) return fail(ctx, NPCF_EINVAL, "register-only 5PCF contraction is 0 or 1");
-            ctx->c5_regonly = value;
+            if (value < 0 || value > 3) return fail(ctx, NPCF_EINVAL, "5PCF contraction mode in [0, 3]");
+            ctx->c5_mode = value;
             return NPCF_OK;
         case 5:
             if (value < 1 || value > 1024) return fail(ctx, NPCF_EINVAL, "primaries per chunk in [1, 1024]");

@@ -28,18 +28,43 @@ namespace {
 constexpr int kC5CThreads = 256;
 
 struct C5CLayout {
-    size_t X, u, cache, total;
+    size_t X, u, cache, c12, o12, c34, o34, s12, s34, total;
 };
 
 __host__ __device__ inline size_t al128c(size_t x) { return (x + 127) & ~size_t(127); }
 
-__host__ __device__ inline C5CLayout c5c_layout(int nr, int nlm, int slot_entries) {
+// tables: the coupling terms and segments staged in shared memory too (else read through L1)
+__host__ __device__ inline C5CLayout c5c_layout(int nr, int nlm, int slot_entries, bool tables, int nt12, int nt34,
+                                                int ns12, int ns34) {
     C5CLayout l;
     l.X = 0;
     l.u = al128c(l.X + (size_t)nr * nlm * kRS5 * sizeof(float2));
     l.cache = al128c(l.u + kT5 * sizeof(float));
-    l.total = al128c(l.cache + (size_t)2 * slot_entries * kT5 * sizeof(float2));
+    l.c12 = al128c(l.cache + (size_t)2 * slot_entries * kT5 * sizeof(float2));
+    if (!tables) nt12 = nt34 = ns12 = ns34 = 0;
+    l.o12 = al128c(l.c12 + (size_t)nt12 * sizeof(float4));
+    l.c34 = al128c(l.o12 + (size_t)nt12 * sizeof(uint32_t));
+    l.o34 = al128c(l.c34 + (size_t)nt34 * sizeof(float4));
+    l.s12 = al128c(l.o34 + (size_t)nt34 * sizeof(uint32_t));
+    l.s34 = al128c(l.s12 + (size_t)ns12 * sizeof(int2));
+    l.total = al128c(l.s34 + (size_t)ns34 * sizeof(int2));
     return l;
+}
+
+// where the kernel reads the coupling terms: shared memory (TS) or global memory through L1
+struct C5CTabs {
+    const float4* c12;
+    const uint32_t* o12;
+    const float4* c34;
+    const uint32_t* o34;
+    const int2* s12;
+    const int2* s34;
+};
+
+template <bool TS, typename T>
+__device__ __forceinline__ T tld(const T* p) {
+    if constexpr (TS) return *p;
+    else return __ldg(p);
 }
 
 // first pair (b3, b3 + 1) of shell b3 >= 2 in the cache's pair order (lexicographic)
@@ -48,8 +73,8 @@ static_assert(pair_off(8, 2) == 0 && pair_off(8, 3) == 5 && pair_off(8, 6) == 14
               "pairs (b3, b4), 2 <= b3 < b4 < 8, in lexicographic order");
 
 // P34^{m12}(b3, b4) of one (triple, m12) for every b4 > b3 into the cache.
-template <int NR>
-__device__ __forceinline__ void c5c_build34(const int4 w, const Contract5CArgs& a, const float2* __restrict__ X,
+template <int NR, bool TS>
+__device__ __forceinline__ void c5c_build34(const int4 w, const C5CTabs& tb, const float2* __restrict__ X,
                                             float2* __restrict__ cache, int lane) {
     constexpr int MX = NR - 3;   // b3 >= 2: at most NR - 3 shells after it
     const int b3 = w.y & 0xff;
@@ -57,11 +82,11 @@ __device__ __forceinline__ void c5c_build34(const int4 w, const Contract5CArgs& 
     float pr[MX], pi[MX];
 #pragma unroll
     for (int q = 0; q < MX; ++q) pr[q] = pi[q] = 0.f;
-    const int2 S = __ldg(&a.segs34[w.x]);
+    const int2 S = tld<TS>(&tb.s34[w.x]);
     const float2* Xl = X + lane;
     for (int k = S.x; k < S.y; ++k) {
-        const float4 c = __ldg(&a.c34[k]);
-        const uint32_t o = __ldg(&a.o34[k]);
+        const float4 c = tld<TS>(&tb.c34[k]);
+        const uint32_t o = tld<TS>(&tb.o34[k]);
         const float2 x3 = Xl[(o & 0xffffu) + b3 * kRS5];
         const float2* X4 = Xl + (o >> 16) + (b3 + 1) * kRS5;
         // re += cA x3 x4 + cB y3 y4 ; im += cC y3 x4 + cD x3 y4 (conjugations folded in c)
@@ -83,8 +108,8 @@ __device__ __forceinline__ void c5c_build34(const int4 w, const Contract5CArgs& 
 
 // Item (multiplet, beta = b2): NB = beta shells b1 < beta, M = NR - 1 - beta shells after it
 // (NP = M (M - 1) / 2 pairs b3 < b4).
-template <int NR, int NB, int M>
-__device__ __forceinline__ void c5c_item(const int4 w, const Contract5CArgs& a, const float2* __restrict__ X,
+template <int NR, int NB, int M, bool TS>
+__device__ __forceinline__ void c5c_item(const int4 w, const C5CTabs& tb, const float2* __restrict__ X,
                                          const float2* __restrict__ cache, float u, const int* __restrict__ binq,
                                          double* __restrict__ dst, int lane) {
     constexpr int NP = M * (M - 1) / 2;
@@ -103,10 +128,10 @@ __device__ __forceinline__ void c5c_item(const int4 w, const Contract5CArgs& a, 
         float p12r[NB], p12i[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) p12r[j] = p12i[j] = 0.f;
-        const int2 S12 = __ldg(&a.segs12[w.x + m12]);
+        const int2 S12 = tld<TS>(&tb.s12[w.x + m12]);
         for (int k = S12.x; k < S12.y; ++k) {
-            const float4 c = __ldg(&a.c12[k]);
-            const uint32_t o = __ldg(&a.o12[k]);
+            const float4 c = tld<TS>(&tb.c12[k]);
+            const uint32_t o = tld<TS>(&tb.o12[k]);
             const float2 x2 = Xl[(o >> 16) + NB * kRS5];
             // re += cA x1 x2 + cB y1 y2 ; im += cC y1 x2 + cD x1 y2 (conjugations folded in c)
             const float a0 = c.x * x2.x, a1 = c.y * x2.y, a2 = c.z * x2.x, a3 = c.w * x2.y;
@@ -146,10 +171,10 @@ __device__ __forceinline__ void c5c_item(const int4 w, const Contract5CArgs& a, 
     }
 }
 
-template <int NR, int MINB>
-__global__ void __launch_bounds__(kC5CThreads, MINB) k_contract5c(const Contract5CArgs a) {
+template <int NR, int THREADS, int MINB, bool TS>
+__global__ void __launch_bounds__(THREADS, MINB) k_contract5c(const Contract5CArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    const C5CLayout lay = c5c_layout(NR, a.nlm, a.slot_entries);
+    const C5CLayout lay = c5c_layout(NR, a.nlm, a.slot_entries, TS, a.nterms12, a.nterms34, a.nseg12, a.nseg34);
     float2* X = reinterpret_cast<float2*>(dsm + lay.X);
     float* su = reinterpret_cast<float*>(dsm + lay.u);
     float2* cache = reinterpret_cast<float2*>(dsm + lay.cache);
@@ -157,6 +182,20 @@ __global__ void __launch_bounds__(kC5CThreads, MINB) k_contract5c(const Contract
     __shared__ int binq[NR * NR];
     const int tid = threadIdx.x, lane = tid & 31;
     for (int i = tid; i < NR * NR; i += blockDim.x) binq[i] = a.binq[i];
+    C5CTabs tb{a.c12, a.o12, a.c34, a.o34, a.segs12, a.segs34};
+    if constexpr (TS) {
+        float4* c12 = reinterpret_cast<float4*>(dsm + lay.c12);
+        uint32_t* o12 = reinterpret_cast<uint32_t*>(dsm + lay.o12);
+        float4* c34 = reinterpret_cast<float4*>(dsm + lay.c34);
+        uint32_t* o34 = reinterpret_cast<uint32_t*>(dsm + lay.o34);
+        int2* s12 = reinterpret_cast<int2*>(dsm + lay.s12);
+        int2* s34 = reinterpret_cast<int2*>(dsm + lay.s34);
+        for (int i = tid; i < a.nterms12; i += blockDim.x) { c12[i] = a.c12[i]; o12[i] = a.o12[i]; }
+        for (int i = tid; i < a.nterms34; i += blockDim.x) { c34[i] = a.c34[i]; o34[i] = a.o34[i]; }
+        for (int i = tid; i < a.nseg12; i += blockDim.x) s12[i] = a.segs12[i];
+        for (int i = tid; i < a.nseg34; i += blockDim.x) s34[i] = a.segs34[i];
+        tb = C5CTabs{c12, o12, c34, o34, s12, s34};
+    }
     const int rows = NR * a.nlm;
 
     // chunks (primary ranges of one catalog) taken dynamically; chunk c sums into row c
@@ -192,12 +231,12 @@ __global__ void __launch_bounds__(kC5CThreads, MINB) k_contract5c(const Contract
                     const int4 w = __ldg(&a.work[w0 + it]);
                     float2* slot = cache + (size_t)((w.y >> 24) & 1) * a.slot_entries * kT5;
                     if (w.y & (1 << 30)) {
-                        c5c_build34<NR>(w, a, X, slot, lane);
+                        c5c_build34<NR, TS>(w, tb, X, slot, lane);
                     } else {
                         switch (w.y & 0xff) {   // beta
 #define NPCF_C5C_CASE(B) \
     case B:              \
-        if (B <= NR - 3) c5c_item<NR, (B <= NR - 3 ? B : 1), (B <= NR - 3 ? NR - 1 - B : 2)>(w, a, X, slot, u, binq, dst, lane); \
+        if (B <= NR - 3) c5c_item<NR, (B <= NR - 3 ? B : 1), (B <= NR - 3 ? NR - 1 - B : 2), TS>(w, tb, X, slot, u, binq, dst, lane); \
         break;
                             NPCF_C5C_CASE(1) NPCF_C5C_CASE(2) NPCF_C5C_CASE(3) NPCF_C5C_CASE(4)
                             NPCF_C5C_CASE(5) NPCF_C5C_CASE(6) NPCF_C5C_CASE(7)
@@ -216,18 +255,26 @@ __global__ void __launch_bounds__(kC5CThreads, MINB) k_contract5c(const Contract
 template <int NR>
 void launch_nr_c(const Contract5CArgs& a, int nblocks, cudaStream_t s) {
     const size_t smem = contract5c_smem_bytes(a);
-    if (a.blocks_per_sm >= 2) {
-        cudaFuncSetAttribute(k_contract5c<NR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_contract5c<NR, 2><<<nblocks, kC5CThreads, smem, s>>>(a);
+    if (a.tables_smem) {   // one block of 512 threads per SM, coupling terms in shared memory
+        cudaFuncSetAttribute(k_contract5c<NR, 512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_contract5c<NR, 512, 1, true><<<nblocks, 512, smem, s>>>(a);
+    } else if (a.blocks_per_sm >= 2) {
+        cudaFuncSetAttribute(k_contract5c<NR, kC5CThreads, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_contract5c<NR, kC5CThreads, 2, false><<<nblocks, kC5CThreads, smem, s>>>(a);
     } else {
-        cudaFuncSetAttribute(k_contract5c<NR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_contract5c<NR, 1><<<nblocks, kC5CThreads, smem, s>>>(a);
+        cudaFuncSetAttribute(k_contract5c<NR, kC5CThreads, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_contract5c<NR, kC5CThreads, 1, false><<<nblocks, kC5CThreads, smem, s>>>(a);
     }
 }
 
 }  // namespace
 
-size_t contract5c_smem_bytes(const Contract5CArgs& a) { return c5c_layout(a.nr, a.nlm, a.slot_entries).total; }
+size_t contract5c_smem_bytes(const Contract5CArgs& a) {
+    return c5c_layout(a.nr, a.nlm, a.slot_entries, a.tables_smem != 0, a.nterms12, a.nterms34, a.nseg12, a.nseg34)
+        .total;
+}
 
 size_t contract5c_static_smem() { return 1024; }
 

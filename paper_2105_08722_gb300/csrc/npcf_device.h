@@ -262,6 +262,8 @@ struct Contract5CArgs {
     int nphase;
     int slot_entries;          // entries of one cache slot
     int blocks_per_sm;         // 2 where two blocks' shared memory fits on an SM, else 1
+    int tables_smem;           // 1: one block of 512 threads per SM, coupling terms in shared memory
+    int nterms12, nterms34, nseg12, nseg34;
     const int2* chunks;        // primary ranges, none crossing a catalog
     int nchunk;
     double* partial;           // [nchunk][total]

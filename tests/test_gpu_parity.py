@@ -485,9 +485,10 @@ def test_lognormal_200k_split_bf16_sampled_primaries(torch_dev, lognormal_worklo
 
 # ------------------------------------------------------------------ 5PCF
 
-# tuning key 9: 0 = P34 cached in shared memory per block (the default where it fits),
-# 1 = the register-only kernel; both run on the same cases
-@pytest.mark.parametrize("regonly", [0, 1])
+# tuning key 9: 0 = automatic, 1 = the register-only kernel, 2 = P34 cached in shared
+# memory per block with the coupling terms read through L1, 3 = the same with the terms in
+# shared memory too; every kernel runs on the same cases
+@pytest.mark.parametrize("regonly", [0, 1, 2, 3])
 def test_5pcf_periodic_lmax3(torch_dev, regonly):
     pos = catalogs.lognormal_box(900, 150.0, 32, seed=51)
     w = np.ones(len(pos), np.float32)
@@ -498,7 +499,7 @@ def test_5pcf_periodic_lmax3(torch_dev, regonly):
     assert_orders_close(got, want, (5,), 3, 6)
 
 
-@pytest.mark.parametrize("regonly", [0, 1])
+@pytest.mark.parametrize("regonly", [0, 1, 2, 3])
 @pytest.mark.parametrize("nr", [4, 9, 10])
 def test_5pcf_many_shells(torch_dev, nr, regonly):
     # 4 shells: one bin tuple; 9 and 10 shells take items of 1 to 4 multiplets sharing
@@ -512,7 +513,7 @@ def test_5pcf_many_shells(torch_dev, nr, regonly):
     assert_orders_close(got, want, (5,), 3, nr)
 
 
-@pytest.mark.parametrize("regonly", [0, 1])
+@pytest.mark.parametrize("regonly", [0, 1, 2, 3])
 def test_5pcf_lmax5_10_shells(torch_dev, regonly):
     # the paper's 5PCF timing setting (lmax 5, 10 shells) on a small catalog: 1,406
     # multiplets x 210 bin tuples
@@ -525,7 +526,7 @@ def test_5pcf_lmax5_10_shells(torch_dev, regonly):
     assert_orders_close(got, want, (5,), 5, 10)
 
 
-@pytest.mark.parametrize("regonly", [0, 1])
+@pytest.mark.parametrize("regonly", [0, 1, 2, 3])
 def test_5pcf_all_parity_non_periodic_weighted_with_lower_orders(torch_dev, regonly):
     pos, w = _catalog(500, 80.0, 52)
     w = w - np.float32(0.8)
@@ -934,6 +935,7 @@ def test_batch_matches_single_catalog_runs(torch_dev):
 @pytest.mark.parametrize("orders,lmax,tuning", [
     ((5,), 3, {}),            # 5PCF with the P34 cache: chunk rows of several catalogs
     ((5,), 3, {9: 1}),        # the register-only 5PCF kernel
+    ((5,), 3, {9: 2}),        # the P34 cache with the coupling terms read through L1
     ((3, 4), 4, {4: 1}),      # the high-lmax 4PCF kernel forced
 ])
 def test_batch_of_each_contraction_kernel_matches_single_runs(torch_dev, orders, lmax, tuning):
