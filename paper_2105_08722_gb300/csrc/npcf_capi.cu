@@ -115,6 +115,7 @@ struct npcf_ctx {
     // 5PCF contraction with the P34 cache (npcf_contract5c.cu), where its shared memory fits
     DevBuf<int4> c5c_work;
     DevBuf<int> c5c_phase;
+    DevBuf<int4> c5c_partners;
     int c5c_nphase = 0, c5c_slot = 0, c5c_bps = 0;
     bool c5c_ok = false, c5c_tabs_fit = false;   // tabs_fit: the tables fit in shared memory too
     int c5nterms12 = 0, c5nterms34 = 0, c5nseg12 = 0, c5nseg34 = 0;
@@ -433,39 +434,69 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
             }
         }
         if (slot > 0 && maxsize > 0) {
+            // right triples in order of l12, so that a group holds triples of one l12 and the
+            // multiplets of a left triple in a group can share its P12
+            std::vector<int> order34;
+            for (int t34 = 0; t34 < (int)by34.size(); ++t34)
+                if (!by34[t34].empty()) order34.push_back(t34);
+            std::stable_sort(order34.begin(), order34.end(),
+                             [&](int x, int y) { return t.t34_l12[x] < t.t34_l12[y]; });
             std::vector<std::vector<std::pair<double, int4>>> phase(1);
+            std::vector<std::vector<int>> members(1);   // right triples of each group
+            std::vector<int> tb34(by34.size(), 0);      // cache entry of each right triple
             int g = 0, used = 0;
-            for (int t34 = 0; t34 < (int)by34.size(); ++t34) {
-                const std::vector<int>& mult = by34[t34];
-                if (mult.empty()) continue;
+            for (int t34 : order34) {
                 const int l12 = t.t34_l12[t34], size = (l12 + 1) * npall;
                 if (used + size > slot) {
                     ++g;
                     used = 0;
                     phase.emplace_back();
+                    members.emplace_back();
                 }
-                const int tbase = used, sl = g & 1;
+                tb34[t34] = used;
                 used += size;
+                members[g].push_back(t34);
                 for (int m12 = 0; m12 <= l12; ++m12) {
                     const int sg = t.t34_seg0[t34] + m12;
                     const int k34 = t.seg34_end[sg] - t.seg34_begin[sg];
                     for (int b3 = 2; b3 + 1 < nr; ++b3)
                         phase[g].push_back({(double)k34 * (nr - 1 - b3),
-                                            make_int4(sg, b3 | (sl << 24) | (1 << 30), tbase + m12 * npall, 0)});
+                                            make_int4(sg, b3 | ((g & 1) << 24) | (1 << 30), tb34[t34] + m12 * npall, 0)});
                 }
-                if ((int)phase.size() <= g + 1) phase.resize(g + 2);
-                for (int a : mult) {
-                    const int t12 = t.lam_t12[a];
+            }
+            phase.resize(g + 2);
+            std::vector<int4> partners;
+            for (int gg = 0; gg <= g; ++gg) {
+                // the group's multiplets by left triple
+                std::vector<std::vector<int>> by12;
+                for (int t34 : members[gg])
+                    for (int a : by34[t34]) {
+                        const int t12 = t.lam_t12[a];
+                        if ((int)by12.size() <= t12) by12.resize(t12 + 1);
+                        by12[t12].push_back(a);
+                    }
+                for (int t12 = 0; t12 < (int)by12.size(); ++t12) {
+                    const std::vector<int>& mult = by12[t12];
+                    if (mult.empty()) continue;
+                    const int l12 = o.lam[(size_t)mult[0] * 5 + 2];
+                    const int p0 = (int)partners.size();
+                    for (int a : mult)
+                        partners.push_back(make_int4(tb34[t.lam_t34[a]], off + a * nb, o.odd(a) ? 1 : 0, 0));
                     for (int beta = 1; beta + 2 < nr; ++beta) {
-                        const int m = nr - 1 - beta;
-                        double cost = 0;
+                        const int m = nr - 1 - beta, GM = c5c_group(beta, m);
+                        double c12cost = 0;
                         for (int m12 = 0; m12 <= l12; ++m12) {
                             const int sg = t.t12_seg0[t12] + m12;
-                            cost += 2.0 * (t.seg12_end[sg] - t.seg12_begin[sg]) * beta + beta * m * (m - 1) / 2.0;
+                            c12cost += 2.0 * (t.seg12_end[sg] - t.seg12_begin[sg]) * beta;
                         }
-                        phase[g + 1].push_back(
-                            {cost, make_int4(t.t12_seg0[t12], beta | ((o.odd(a) ? 1 : 0) << 8) | (l12 << 16) | (sl << 24),
-                                             tbase, off + a * nb)});
+                        for (int h0 = 0; h0 < (int)mult.size(); h0 += GM) {
+                            const int gcount = std::min(GM, (int)mult.size() - h0);
+                            const double cost = c12cost + (l12 + 1) * gcount * beta * m * (m - 1) / 2.0;
+                            phase[gg + 1].push_back(
+                                {cost, make_int4(t.t12_seg0[t12], beta | (l12 << 16) | ((gg & 1) << 24) |
+                                                                      ((gcount - 1) << 26),
+                                                 p0 + h0, 0)});
+                        }
                     }
                 }
             }
@@ -485,6 +516,7 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
             ctx->c5c_bps = bps;
             CU(upload(ctx->c5c_work, work));
             CU(upload(ctx->c5c_phase, pb));
+            CU(upload(ctx->c5c_partners, partners));
             ctx->c5c_ok = true;
         }
     }
@@ -1203,6 +1235,7 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
                 c.binq = ctx->c5binq.p;
                 c.work = ctx->c5c_work.p;
                 c.phase_begin = ctx->c5c_phase.p;
+                c.partners = ctx->c5c_partners.p;
                 c.nphase = ctx->c5c_nphase;
                 c.slot_entries = ctx->c5c_slot;
                 c.blocks_per_sm = ctx->c5c_bps;

@@ -106,23 +106,38 @@ __device__ __forceinline__ void c5c_build34(const int4 w, const C5CTabs& tb, con
         if (q < nb4) dst[q * kT5] = make_float2(pr[q], pi[q]);
 }
 
-// Item (multiplet, beta = b2): NB = beta shells b1 < beta, M = NR - 1 - beta shells after it
-// (NP = M (M - 1) / 2 pairs b3 < b4).
+// Item (left triple, beta = b2, g <= GM partners): the multiplets (l1 l2 l12 l3 l4) of one
+// left triple (l1 l2 l12) whose right triples sit in the same group share P12, so a lane
+// builds P12(b1, beta) for every b1 < beta once per m12 and multiplies it with the cached
+// P34 of each partner into that partner's sums. NB = beta shells b1 < beta, M = NR - 1 -
+// beta shells after it (NP = M (M - 1) / 2 pairs b3 < b4).
 template <int NR, int NB, int M, bool TS>
-__device__ __forceinline__ void c5c_item(const int4 w, const C5CTabs& tb, const float2* __restrict__ X,
-                                         const float2* __restrict__ cache, float u, const int* __restrict__ binq,
-                                         double* __restrict__ dst, int lane) {
+__device__ __forceinline__ void c5c_item(const int4 w, const C5CTabs& tb, const int4* __restrict__ partners,
+                                         const float2* __restrict__ X, const float2* __restrict__ cache, float u,
+                                         const int* __restrict__ binq, double* __restrict__ dst, int lane) {
     constexpr int NP = M * (M - 1) / 2;
     constexpr int NOUT = NB * NP;
     constexpr int NPALL = (NR - 3) * (NR - 2) / 2;
-    const bool odd = ((w.y >> 8) & 1) != 0;
+    constexpr int GM = c5c_group(NB, M);
     const int l12 = (w.y >> 16) & 0xff;
+    const int g = ((w.y >> 26) & 3) + 1;
     const float rcf = sqrtf((float)(2 * l12 + 1));
     const float2* Xl = X + lane;
-    const float2* C34 = cache + (size_t)(w.z + pair_off(NR, NB + 1)) * kT5 + lane;
-    float acc[NOUT];
+    const float2* C34[GM];
+    bool odd[GM];
+    int out0[GM];
 #pragma unroll
-    for (int i = 0; i < NOUT; ++i) acc[i] = 0.f;
+    for (int h = 0; h < GM; ++h) {
+        const int4 P = h < g ? __ldg(&partners[w.z + h]) : make_int4(0, 0, 0, 0);   // (P34 block, output, odd)
+        C34[h] = cache + (size_t)(P.x + pair_off(NR, NB + 1)) * kT5 + lane;
+        out0[h] = P.y;
+        odd[h] = P.z != 0;
+    }
+    float acc[GM][NOUT];
+#pragma unroll
+    for (int h = 0; h < GM; ++h)
+#pragma unroll
+        for (int i = 0; i < NOUT; ++i) acc[h][i] = 0.f;
     for (int m12 = 0; m12 <= l12; ++m12) {
         // P12(b1, beta) for b1 < beta; the b2 factor is the same for every b1
         float p12r[NB], p12i[NB];
@@ -145,28 +160,37 @@ __device__ __forceinline__ void c5c_item(const int4 w, const C5CTabs& tb, const 
         }
         // u 2 S(m12) (-1)^{l12 - m12} sqrt(2 l12 + 1); Re (even L) or Im (odd L) of P12 P34
         const float cm = u * (m12 == 0 ? 1.f : 2.f) * (((l12 - m12) & 1) ? -1.f : 1.f) * rcf;
-        float A[NB], B[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            A[j] = cm * (odd ? p12i[j] : p12r[j]);
-            B[j] = cm * (odd ? p12r[j] : -p12i[j]);
-        }
-        const float2* P34 = C34 + (size_t)m12 * NPALL * kT5;
+        for (int h = 0; h < GM; ++h) {
+            if (h >= g) break;
+            float A[NB], B[NB];
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const float2 q = P34[p * kT5];
+            for (int j = 0; j < NB; ++j) {
+                A[j] = cm * (odd[h] ? p12i[j] : p12r[j]);
+                B[j] = cm * (odd[h] ? p12r[j] : -p12i[j]);
+            }
+            const float2* P34 = C34[h] + (size_t)m12 * NPALL * kT5;
 #pragma unroll
-            for (int j = 0; j < NB; ++j) acc[j * NP + p] = fmaf(A[j], q.x, fmaf(B[j], q.y, acc[j * NP + p]));
+            for (int p = 0; p < NP; ++p) {
+                const float2 q = P34[p * kT5];
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    acc[h][j * NP + p] = fmaf(A[j], q.x, fmaf(B[j], q.y, acc[h][j * NP + p]));
+            }
         }
     }
     using R = warp::TR<NOUT>;
-    R::run(acc, lane);
 #pragma unroll
-    for (int i = 0; i < R::F; ++i) {
-        const int e = R::origin(i, lane);
-        if (e >= 0) {
-            const int j = e / NP, p = e - j * NP;
-            dst[w.w + binq[j * NR + NB] + p] += (double)acc[i];
+    for (int h = 0; h < GM; ++h) {
+        if (h >= g) break;
+        R::run(acc[h], lane);
+#pragma unroll
+        for (int i = 0; i < R::F; ++i) {
+            const int e = R::origin(i, lane);
+            if (e >= 0) {
+                const int j = e / NP, p = e - j * NP;
+                dst[out0[h] + binq[j * NR + NB] + p] += (double)acc[h][i];
+            }
         }
     }
 }
@@ -236,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_contract5c(const Contract5CAr
                         switch (w.y & 0xff) {   // beta
 #define NPCF_C5C_CASE(B) \
     case B:              \
-        if (B <= NR - 3) c5c_item<NR, (B <= NR - 3 ? B : 1), (B <= NR - 3 ? NR - 1 - B : 2), TS>(w, tb, X, slot, u, binq, dst, lane); \
+        if (B <= NR - 3) c5c_item<NR, (B <= NR - 3 ? B : 1), (B <= NR - 3 ? NR - 1 - B : 2), TS>(w, tb, a.partners, X, slot, u, binq, dst, lane); \
         break;
                             NPCF_C5C_CASE(1) NPCF_C5C_CASE(2) NPCF_C5C_CASE(3) NPCF_C5C_CASE(4)
                             NPCF_C5C_CASE(5) NPCF_C5C_CASE(6) NPCF_C5C_CASE(7)

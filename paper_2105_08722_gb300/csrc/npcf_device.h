@@ -244,8 +244,14 @@ void launch_contract5w(const Contract5WArgs& a, int nblocks, cudaStream_t s);
 // 5PCF contraction with P34 built once per block and tile into shared memory
 // (npcf_contract5c.cu). The work list of each phase holds P34 builds, (segment of the
 // (triple, m12), b3 | slot << 24 | 1 << 30, cache entry of the (triple, m12) block, 0), and
-// items, (P12 segment of m12 = 0, beta | odd << 8 | l12 << 16 | slot << 24, cache entry of
-// the triple's m12 = 0 block, first output of L); a cache entry is kT5 float2.
+// items, (P12 segment of m12 = 0 of a left triple, beta | l12 << 16 | slot << 24 | (g - 1)
+// << 26, first of its g partners, 0); a partner is (cache entry of its right triple's
+// m12 = 0 block, first output of the multiplet, odd, 0); a cache entry is kT5 float2.
+// Partners per item: as many as their sums fit in about 64 registers, at most 4.
+__host__ __device__ constexpr int c5c_group(int nb, int m) {
+    const int g = 64 / (nb * m * (m - 1) / 2);
+    return g < 1 ? 1 : (g > 4 ? 4 : g);
+}
 struct Contract5CArgs {
     const float2* alm;         // [n][nr][nlm]
     const float* wp;
@@ -258,6 +264,7 @@ struct Contract5CArgs {
     const int2* segs34;
     const int* binq;           // [nr][nr]: bin index of (b1, b2, b2 + 1, b2 + 2)
     const int4* work;          // the phases' work lists, back to back
+    const int4* partners;      // the items' partners
     const int* phase_begin;    // [nphase + 1]
     int nphase;
     int slot_entries;          // entries of one cache slot
