@@ -503,9 +503,14 @@ npcf_status setup_c5_tables(npcf_ctx* ctx, const OrderTable& o, int off) {
             std::vector<int4> work;
             std::vector<int> pb;
             for (auto& ph : phase) {
+                // P34 builds first, then the items by b2 (each b2 is its own specialisation of
+                // the kernel: warps that run at the same time then share one code path in the
+                // instruction cache), heaviest first within each
+                auto kind = [](const int4& w) { return (w.y & (1 << 30)) ? 0 : 1 + (w.y & 0xff); };
                 std::stable_sort(ph.begin(), ph.end(),
-                                 [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
-                                     return x.first > y.first;
+                                 [&](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+                                     const int kx = kind(x.second), ky = kind(y.second);
+                                     return kx != ky ? kx < ky : x.first > y.first;
                                  });
                 pb.push_back((int)work.size());
                 for (const auto& x : ph) work.push_back(x.second);
