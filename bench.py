@@ -831,7 +831,7 @@ def run_gpu_grid(args):
     line = {
         "metric": "cells/sec for the 4PCF + 3PCF of a gridded field (lmax=5, 10 shells)",
         "value": cells / (ms * 1e-3), "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 FFT, f32",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "lognormal_mesh_%d3_L1000_4pcf3pcf_lmax5_nr10_20-160" % n, "cells": cells,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},

@@ -147,9 +147,10 @@ npcf_status npcf_accumulate_split(npcf_ctx* ctx, const float* d_pos, const float
  * weights delta when the cell-centre coordinates are exact in FP32. Raw sums (the
  * normalisation of npcf_finalize is for particle catalogs); pair counts and the sum of
  * weights are not updated. Keeps the kernel spectra of the mesh in the context (nr x
- * (lmax+1)(lmax+2)/2 x ngrid^3 x 16 bytes, plus one such field set per shell and one
- * spectrum of delta); FP64 transforms by cuFFT. NPCF_EUNSUPPORTED without a periodic
- * box; NPCF_ENOMEM when the spectra do not fit. */
+ * (lmax+1)(lmax+2)/2 x ngrid^3 x 8 bytes, plus one shell's field set and one spectrum of
+ * delta as work space); FP32 transforms by cuFFT (their rounding is about 1e-6 of the RMS
+ * of the a_lm). NPCF_EUNSUPPORTED without a periodic box; NPCF_ENOMEM when the spectra do
+ * not fit. */
 npcf_status npcf_accumulate_grid(npcf_ctx* ctx, const float* d_delta, int ngrid, void* stream);
 
 /* Number of doubles npcf_finalize writes. */

@@ -10,9 +10,12 @@
 // kernel K(u) = Y_lm(unit(-u h)) Theta^b(|u h|) it is the circular convolution K * delta,
 // i.e. the inverse FFT of FFT(K) FFT(delta) divided by n^3 (Eq. alm-binned-def-fft on the
 // mirrored kernel: a factor (-1)^l from the paper's form). The kernel spectra of every (b, l,
-// m >= 0) depend only on the mesh and are kept between calls. Transforms are FP64 (cuFFT
-// Z2Z); the a_lm are stored as FP32 reduced harmonics a_lm / sqrt((2l+1)/(4 pi)), the layout
-// the contraction kernels read, with the cells as primaries.
+// m >= 0) depend only on the mesh and are kept between calls. Transforms are FP32 (cuFFT
+// C2C; the kernel values are computed in FP64): their rounding, about 1e-6 of the RMS of the
+// a_lm on a 64^3 log-normal field, is far below the FP32 contraction's error bar, and FP64
+// transforms ran at the GPU's much lower FP64 rate. The a_lm are stored as FP32 reduced
+// harmonics a_lm / sqrt((2l+1)/(4 pi)), the layout the contraction kernels read, with the
+// cells as primaries.
 #include "npcf_device.h"
 
 #include <cufft.h>
@@ -26,9 +29,9 @@ struct GridFFT {
     int n = 0, nr = 0, lmax = -1;
     float h = 0.f;
     float e2[kMaxNr + 1] = {};
-    double2* spec = nullptr;    // [nr][nlm][n^3] kernel spectra
-    double2* df = nullptr;      // [n^3] spectrum of delta
-    double2* work = nullptr;    // [nlm][n^3]
+    float2* spec = nullptr;     // [nr][nlm][n^3] kernel spectra
+    float2* df = nullptr;       // [n^3] spectrum of delta
+    float2* work = nullptr;     // [nlm][n^3]
     cufftHandle one = 0, many = 0;
     bool plans = false;
     void release() {
@@ -56,7 +59,7 @@ __host__ __device__ constexpr int nlm_of(int L) { return (L + 1) * (L + 2) / 2; 
 // Kernel of shell b on the mesh, for every (l, m >= 0): K(u) = Y~_lm(unit(-u h)) where the
 // FP32 rule puts the offset in shell b, else 0; Y~_lm = sqrt((l-m)!/(l+m)!) P_l^m(z) e^{i m phi}
 // (Condon-Shortley phase), written as (x + i y)^m times a polynomial in z.
-__global__ void k_mesh_kernel(double2* __restrict__ out, int n, float h, const GridFFTArgs a, int b) {
+__global__ void k_mesh_kernel(float2* __restrict__ out, int n, float h, const GridFFTArgs a, int b) {
     const long long cells = (long long)n * n * n;
     const int nlm = nlm_of(a.lmax);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
@@ -73,7 +76,7 @@ __global__ void k_mesh_kernel(double2* __restrict__ out, int n, float h, const G
             while (sb + 1 < a.nr && r2 >= a.e2[sb + 1]) ++sb;
         }
         if (sb != b) {
-            for (int q = 0; q < nlm; ++q) out[(size_t)q * cells + c] = make_double2(0.0, 0.0);
+            for (int q = 0; q < nlm; ++q) out[(size_t)q * cells + c] = make_float2(0.f, 0.f);
             continue;
         }
         const double r = sqrt((double)r2);
@@ -104,39 +107,39 @@ __global__ void k_mesh_kernel(double2* __restrict__ out, int n, float h, const G
                 }
                 if (l > m) f *= (double)(l - m) / (double)(l + m);
                 const double s = sqrt(f) * ql;
-                out[(size_t)(l * (l + 1) / 2 + m) * cells + c] = make_double2(s * cr, s * ci);
+                out[(size_t)(l * (l + 1) / 2 + m) * cells + c] = make_float2((float)(s * cr), (float)(s * ci));
             }
         }
     }
 }
 
-__global__ void k_delta_complex(double2* __restrict__ out, const float* __restrict__ delta, long long cells) {
+__global__ void k_delta_complex(float2* __restrict__ out, const float* __restrict__ delta, long long cells) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
          c += (long long)gridDim.x * blockDim.x)
-        out[c] = make_double2((double)delta[c], 0.0);
+        out[c] = make_float2(delta[c], 0.f);
 }
 
 // work[q][c] = spec[q][c] * df[c] for every harmonic q
-__global__ void k_spectral_mul(double2* __restrict__ work, const double2* __restrict__ spec,
-                               const double2* __restrict__ df, long long cells, int nlm) {
+__global__ void k_spectral_mul(float2* __restrict__ work, const float2* __restrict__ spec,
+                               const float2* __restrict__ df, long long cells, int nlm) {
     const long long tot = cells * nlm;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
          i += (long long)gridDim.x * blockDim.x) {
-        const double2 k = spec[i], d = df[i % cells];
-        work[i] = make_double2(k.x * d.x - k.y * d.y, k.x * d.y + k.y * d.x);
+        const float2 k = spec[i], d = df[i % cells];
+        work[i] = make_float2(k.x * d.x - k.y * d.y, k.x * d.y + k.y * d.x);
     }
 }
 
-// alm[c][b][q] = work[q][c] / n^3 (FP32)
-__global__ void k_store_alm(const double2* __restrict__ work, float2* __restrict__ alm, long long cells, int nlm,
-                            int nr, int b, double scale) {
+// alm[c][b][q] = work[q][c] / n^3
+__global__ void k_store_alm(const float2* __restrict__ work, float2* __restrict__ alm, long long cells, int nlm,
+                            int nr, int b, float scale) {
     const long long tot = cells * nlm;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
          i += (long long)gridDim.x * blockDim.x) {
         const long long c = i / nlm;
         const int q = (int)(i - c * nlm);
-        const double2 v = work[(size_t)q * cells + c];
-        alm[((size_t)c * nr + b) * nlm + q] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+        const float2 v = work[(size_t)q * cells + c];
+        alm[((size_t)c * nr + b) * nlm + q] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
@@ -171,15 +174,15 @@ int gridfft_alm(GridFFT* G, const float* delta, int n, float box, const GridFFTA
     if (!same) {
         G->release();
         cudaError_t e;
-        if ((e = cudaMalloc(&G->spec, sizeof(double2) * (size_t)a.nr * nlm * cells)) != cudaSuccess)
+        if ((e = cudaMalloc(&G->spec, sizeof(float2) * (size_t)a.nr * nlm * cells)) != cudaSuccess)
             return cuda_fail("kernel spectra", e);
-        if ((e = cudaMalloc(&G->df, sizeof(double2) * (size_t)cells)) != cudaSuccess) return cuda_fail("delta spectrum", e);
-        if ((e = cudaMalloc(&G->work, sizeof(double2) * (size_t)nlm * cells)) != cudaSuccess)
+        if ((e = cudaMalloc(&G->df, sizeof(float2) * (size_t)cells)) != cudaSuccess) return cuda_fail("delta spectrum", e);
+        if ((e = cudaMalloc(&G->work, sizeof(float2) * (size_t)nlm * cells)) != cudaSuccess)
             return cuda_fail("harmonic fields", e);
         cufftResult r;
-        if ((r = cufftPlan3d(&G->one, n, n, n, CUFFT_Z2Z)) != CUFFT_SUCCESS) return fft_fail("plan", r);
+        if ((r = cufftPlan3d(&G->one, n, n, n, CUFFT_C2C)) != CUFFT_SUCCESS) return fft_fail("plan", r);
         int dims[3] = {n, n, n};
-        if ((r = cufftPlanMany(&G->many, 3, dims, nullptr, 1, (int)cells, nullptr, 1, (int)cells, CUFFT_Z2Z, nlm)) !=
+        if ((r = cufftPlanMany(&G->many, 3, dims, nullptr, 1, (int)cells, nullptr, 1, (int)cells, CUFFT_C2C, nlm)) !=
             CUFFT_SUCCESS) {
             cufftDestroy(G->one);
             return fft_fail("batched plan", r);
@@ -188,10 +191,10 @@ int gridfft_alm(GridFFT* G, const float* delta, int n, float box, const GridFFTA
         // cuFFT's x is its last (fastest) dimension: dims (n, n, n) over [z][y][x] storage
         if ((r = cufftSetStream(G->many, s)) != CUFFT_SUCCESS) return fft_fail("stream", r);
         for (int b = 0; b < a.nr; ++b) {
-            double2* sb = G->spec + (size_t)b * nlm * cells;
+            float2* sb = G->spec + (size_t)b * nlm * cells;
             k_mesh_kernel<<<blocks_for(cells), 256, 0, s>>>(sb, n, h, a, b);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("mesh kernel", e);
-            if ((r = cufftExecZ2Z(G->many, (cufftDoubleComplex*)sb, (cufftDoubleComplex*)sb, CUFFT_FORWARD)) !=
+            if ((r = cufftExecC2C(G->many, (cufftComplex*)sb, (cufftComplex*)sb, CUFFT_FORWARD)) !=
                 CUFFT_SUCCESS)
                 return fft_fail("kernel transform", r);
         }
@@ -205,16 +208,16 @@ int gridfft_alm(GridFFT* G, const float* delta, int n, float box, const GridFFTA
     if ((r = cufftSetStream(G->one, s)) != CUFFT_SUCCESS || (r = cufftSetStream(G->many, s)) != CUFFT_SUCCESS)
         return fft_fail("stream", r);
     k_delta_complex<<<blocks_for(cells), 256, 0, s>>>(G->df, delta, cells);
-    if ((r = cufftExecZ2Z(G->one, (cufftDoubleComplex*)G->df, (cufftDoubleComplex*)G->df, CUFFT_FORWARD)) !=
+    if ((r = cufftExecC2C(G->one, (cufftComplex*)G->df, (cufftComplex*)G->df, CUFFT_FORWARD)) !=
         CUFFT_SUCCESS)
         return fft_fail("delta transform", r);
     for (int b = 0; b < a.nr; ++b) {
         k_spectral_mul<<<blocks_for(cells * nlm), 256, 0, s>>>(G->work, G->spec + (size_t)b * nlm * cells, G->df,
                                                               cells, nlm);
-        if ((r = cufftExecZ2Z(G->many, (cufftDoubleComplex*)G->work, (cufftDoubleComplex*)G->work, CUFFT_INVERSE)) !=
+        if ((r = cufftExecC2C(G->many, (cufftComplex*)G->work, (cufftComplex*)G->work, CUFFT_INVERSE)) !=
             CUFFT_SUCCESS)
             return fft_fail("inverse transform", r);
-        k_store_alm<<<blocks_for(cells * nlm), 256, 0, s>>>(G->work, alm, cells, nlm, a.nr, b, 1.0 / (double)cells);
+        k_store_alm<<<blocks_for(cells * nlm), 256, 0, s>>>(G->work, alm, cells, nlm, a.nr, b, (float)(1.0 / (double)cells));
     }
     k_copy_weights<<<blocks_for(cells), 256, 0, s>>>(wp, delta, cells);
     const cudaError_t e = cudaGetLastError();
