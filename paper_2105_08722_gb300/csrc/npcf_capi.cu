@@ -673,12 +673,15 @@ npcf_status setup_tables(npcf_ctx* ctx) {
         if (o.N == 3) {
             // items (l, b1) over the shells b2 > b1; the bins (b1, b2) are in lexicographic
             // order, so those of one b1 are consecutive
+            // items ordered by b1 (the kernel's specialisation on the shells after b1), so
+            // that warps running at the same time share one code path
             std::vector<int4> items;
             std::vector<float> coef;
-            for (int l = 0; l <= ctx->lmax; ++l) {
+            for (int l = 0; l <= ctx->lmax; ++l)
                 // E(L) C^{ll}_{m,-m} (-1)^m = (l l 0; 0 0 0) for every m (Eq. N=3-coeff)
                 coef.push_back((float)wigner3j(l, l, 0, 0, 0, 0));
-                for (int b1 = 0; b1 + 1 < ctx->nr; ++b1) {
+            for (int b1 = 0; b1 + 1 < ctx->nr; ++b1)
+                for (int l = 0; l <= ctx->lmax; ++l) {
                     int first = -1;
                     for (int b = 0; b < o.n_bins() && first < 0; ++b)
                         if (o.bins[2 * b] == b1 && o.bins[2 * b + 1] == b1 + 1) first = b;
@@ -688,7 +691,6 @@ npcf_status setup_tables(npcf_ctx* ctx) {
                             return fail(ctx, NPCF_EINVAL, "3PCF bins are not in lexicographic order");
                     items.push_back(make_int4(l, l * (l + 1) / 2, b1 | (nb2 << 16), l * o.n_bins() + first));
                 }
-            }
             ctx->c3nitem = (int)items.size();
             CU(upload(ctx->c3items, items));
             CU(upload(ctx->c3coef, coef));
