@@ -11,12 +11,15 @@
 // of that triple and every b2 < b3 uses it. The register-only kernel (npcf_contract5w.cu)
 // builds it again for every b2 and every item of at most two multiplets. Here a block
 // builds P34 of a group of right triples once per tile of 32 primaries into shared memory
-// ([m12][pair (b3 < b4), b3 >= 2][primary]), and its warps then take items (multiplet,
-// b2): each lane builds P12(b1, b2) for every b1 < b2 in registers and multiplies it with
-// the cached P34 of every pair after b2 into its (b1, b3, b4) sums. Two cache slots
-// alternate: in one phase the warps take, from one work list, the items of group g - 1
-// (reading one slot) and the P34 builds of group g (writing the other), so one block
-// barrier separates the phases. Coupling terms are read through L1 (warp-uniform).
+// ([m12][pair (b3 < b4), b3 >= 2][primary]); its warps then take items (left triple
+// (l1 l2 l12), b2, up to four multiplets of that left triple whose right triples are in the
+// group): each lane builds P12(b1, b2) for every b1 < b2 once in registers and multiplies it
+// with the cached P34 of every pair after b2 of each multiplet into that multiplet's
+// (b1, b3, b4) sums. Two cache slots alternate: in one phase the warps take, from one work
+// list, the P34 builds of group g (writing one slot) and the items of group g - 1 (reading
+// the other), so one block barrier separates the phases. The coupling terms are staged in
+// shared memory where they fit beside the slots (one block of 512 threads per SM), else
+// read through L1 (two blocks of 256 threads per SM).
 #include "npcf_device.h"
 #include "npcf_warp.cuh"
 
