@@ -251,10 +251,9 @@ npcf_status npcf_debug_alm(npcf_ctx* ctx, const int64_t* idx, int64_t k, float* 
  * (1, default, used when no bin holds two shell edges) or compute it from sqrt(r2) and the
  * edges (0); both apply the same exact FP32 rule; key 9 = 5PCF contraction: 0 (default)
  * builds P34 once per block and tile into shared memory where it fits, with the coupling
- * terms in shared memory too where they also fit (one block of 512 threads per SM), else
- * read through L1; 1 takes the register-only kernel, 2 the P34 cache with the terms read
- * through L1, 3 the P34 cache with the terms in shared memory (where they do not fit: the
- * register-only kernel). */
+ * terms in shared memory too where they also fit, else read through L1; 1 takes the
+ * register-only kernel, 2 the P34 cache with the terms read through L1, 3 the P34 cache
+ * with the terms in shared memory (where they do not fit: the register-only kernel). */
 npcf_status npcf_set_tuning(npcf_ctx* ctx, int key, int value);
 
 /* Device time in ms of the stages of the last accumulate call:

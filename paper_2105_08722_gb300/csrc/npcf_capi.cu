@@ -1226,7 +1226,8 @@ npcf_status enqueue_contract(npcf_ctx* ctx, const Plan& P, cudaStream_t s, bool 
         } else if (o.N == 5) {
             if (ctx->c5nitem == 0) continue;
             const bool tabs = ctx->c5c_tabs_fit && (ctx->c5_mode == 0 || ctx->c5_mode == 3);
-            if (ctx->c5c_ok && ctx->c5_mode != 1 && (ctx->c5_mode != 3 || tabs)) {
+            const bool cached = ctx->c5_mode == 0 || ctx->c5_mode == 2 || (ctx->c5_mode == 3 && tabs);
+            if (ctx->c5c_ok && cached) {
                 Contract5CArgs c{};
                 c.alm = ctx->alm.p;
                 c.wp = ctx->wp.p;

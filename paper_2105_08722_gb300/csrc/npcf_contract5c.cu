@@ -19,7 +19,7 @@
 // list, the P34 builds of group g (writing one slot) and the items of group g - 1 (reading
 // the other), so one block barrier separates the phases. The coupling terms are staged in
 // shared memory where they fit beside the slots (one block of 512 threads per SM), else
-// read through L1 (two blocks of 256 threads per SM).
+// read through L1 (two blocks of 256 threads per SM where the slots allow, else one of 512).
 #include "npcf_device.h"
 #include "npcf_warp.cuh"
 
@@ -289,10 +289,9 @@ void launch_nr_c(const Contract5CArgs& a, int nblocks, cudaStream_t s) {
         cudaFuncSetAttribute(k_contract5c<NR, kC5CThreads, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         k_contract5c<NR, kC5CThreads, 2, false><<<nblocks, kC5CThreads, smem, s>>>(a);
-    } else {
-        cudaFuncSetAttribute(k_contract5c<NR, kC5CThreads, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        k_contract5c<NR, kC5CThreads, 1, false><<<nblocks, kC5CThreads, smem, s>>>(a);
+    } else {   // one block per SM: 512 threads
+        cudaFuncSetAttribute(k_contract5c<NR, 512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_contract5c<NR, 512, 1, false><<<nblocks, 512, smem, s>>>(a);
     }
 }
 
